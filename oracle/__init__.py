@@ -1,0 +1,106 @@
+"""CPU oracle for exact frequent subgraph mining under MNI support.
+
+TEST INFRASTRUCTURE ONLY: only the test suite, ``__graft_entry__.smoke()`` and the benchmark's
+CPU-baseline / reference legs may import this package.  The CUDA library never imports it and
+shares no code with it.
+
+``fsm_oracle.c`` is plain C (ESU enumeration of connected vertex sets, every connected edge
+subset in edge-induced mode, brute-force canonical code over all k! permutations, MNI image
+sets over every optimal permutation).  ``brute.py`` is a second, independent oracle for tiny
+graphs that follows the MNI definition literally by enumerating injective maps.
+
+Pattern encoding shared by both oracles' outputs (and by the library's C ABI, which defines
+the same encoding independently):
+  * ``labels[k]``: vertex labels in canonical order;
+  * ``adj``: bit ``i*k + j`` (LSB = bit 0) set for each canonical edge i < j;
+  * patterns sorted ascending by the label sequence, then by the adjacency sequence
+    A(0,1), A(0,2), ..., A(k-2,k-1) compared lexicographically (0 < 1).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "fsm_oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, -O2, no architecture flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            lib.oracle_mine.restype = ctypes.c_void_p
+            lib.oracle_mine.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                                        P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
+            lib.oracle_result_count.restype = ctypes.c_int64
+            lib.oracle_result_count.argtypes = [ctypes.c_void_p]
+            lib.oracle_result_copy.restype = None
+            lib.oracle_result_copy.argtypes = [ctypes.c_void_p, P(ctypes.c_int32), P(ctypes.c_uint64),
+                                               P(ctypes.c_int64), P(ctypes.c_int64)]
+            lib.oracle_free.restype = None
+            lib.oracle_free.argtypes = [ctypes.c_void_p]
+            _lib = lib
+    return _lib
+
+
+MODES = {"edge": 0, "vertex": 1}
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = None) -> dict:
+    """All k-vertex patterns of graph ``g`` with MNI support >= t.
+
+    ``roots=(b, e)`` restricts the enumeration to connected sets whose smallest vertex id is
+    in [b, e) (a bounded sample of the work; supports are then those of the sample).
+    Returns a dict of numpy arrays: labels (P, k) int32, adj (P,) uint64, support (P,) int64,
+    count (P,) int64 (number of embeddings of each pattern)."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    labels = np.ascontiguousarray(g.labels, dtype=np.int32)
+    if labels.size and (labels.min() < 0 or labels.max() > 255):
+        raise ValueError("oracle labels must lie in [0, 255]")
+    b, e = (0, g.n) if roots is None else roots
+    res = lib.oracle_mine(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                          _ptr(labels, ctypes.c_int32), k, MODES[mode], int(t), int(b), int(e))
+    if not res:
+        raise ValueError("oracle_mine rejected its arguments")
+    try:
+        npat = lib.oracle_result_count(res)
+        out = {"labels": np.zeros((npat, k), np.int32), "adj": np.zeros(npat, np.uint64),
+               "support": np.zeros(npat, np.int64), "count": np.zeros(npat, np.int64)}
+        if npat:
+            lib.oracle_result_copy(res, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
+                                   _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64))
+    finally:
+        lib.oracle_free(res)
+    return out
+
+
+def pattern_edges(adj: int, k: int) -> list[tuple[int, int]]:
+    """Canonical edge list (i < j) of an ``adj`` word."""
+    return [(i, j) for i in range(k) for j in range(i + 1, k) if (int(adj) >> (i * k + j)) & 1]

@@ -1,0 +1,454 @@
+/*
+ * Plain CPU oracle for exact frequent subgraph mining (FSM) under MNI support.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg may load this file.  It shares no code with the CUDA library: it computes the
+ * problem from its definitions, slowly and directly.
+ *
+ * What it computes (paper Section 2):
+ *   - Section 2.1: a subgraph G'=(V',E') of G has V' in V, E' in E and inherits labels;
+ *     vertex-induced means E' holds every edge of G among V'; edge-induced embeddings are the
+ *     connected (V',E') with E' any subset of the induced edges (reading of the garbled
+ *     definition: every connected edge subset, the full one included).
+ *   - Definition 1 (isomorphism), read as label-preserving: two labeled graphs share a pattern
+ *     when a bijection preserves both adjacency and vertex labels.
+ *   - Definition 2 (MNI support): sigma(P) = min over pattern vertices c of the number of
+ *     distinct images f(c), f ranging over every isomorphism from P onto an embedding of P.
+ *   - Section 2.2 problem statement: report every pattern with |V_P| = k and sigma >= t.
+ *
+ * Method, step by step (no step of the paper's own exploration is used here):
+ *   1. Every connected k-vertex set of G is listed exactly once with the ESU algorithm
+ *      (Wernicke, "Efficient detection of network motifs", 2006): each set is grown from its
+ *      smallest vertex v, the extension set holding only vertices > v that are exclusive
+ *      neighbours of the newest vertex.
+ *   2. For a set u_0 < ... < u_{k-1}, the embeddings are (V', E') with E' = all induced edges
+ *      (vertex-induced) or every connected spanning subset of them (edge-induced).
+ *   3. Canonical code: for a permutation pi of the k positions, code(pi) is the sequence
+ *      (L(u_pi0), ..., L(u_pi(k-1)), A(pi0,pi1), A(pi0,pi2), ..., A(pi(k-2),pi(k-1))) with A
+ *      the 0/1 adjacency of the embedding and pairs (c1 < c2) in row-major order.  The
+ *      canonical code of the embedding is the lexicographic minimum over all k! permutations.
+ *      Equal codes <=> isomorphic (label-preserving) graphs.
+ *   4. Every permutation attaining the minimum is an isomorphism from the canonical pattern
+ *      onto the embedding (c -> u_pi(c)); for all of them and every canonical position c,
+ *      u_pi(c) joins the image set D[P][c].
+ *   5. sigma(P) = min_c |D[P][c]|; patterns with sigma >= t are returned sorted by code.
+ *
+ * Results are memoised per raw (label tuple, adjacency) key so the k! scan runs once per
+ * distinct raw key.  Image sets are growable open-addressing hash sets of vertex ids.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MAXK 8
+
+/* ------------------------------------------------------------------ small utilities */
+
+static int adjacent(const int32_t *row_ptr, const int32_t *col, int32_t a, int32_t b) {
+    int32_t lo = row_ptr[a], hi = row_ptr[a + 1] - 1;
+    while (lo <= hi) {
+        int32_t mid = lo + (hi - lo) / 2;
+        if (col[mid] == b) return 1;
+        if (col[mid] < b) lo = mid + 1; else hi = mid - 1;
+    }
+    return 0;
+}
+
+static uint64_t mix64(uint64_t x) {
+    x ^= x >> 33; x *= 0xff51afd7ed558ccdULL;
+    x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ULL;
+    x ^= x >> 33; return x;
+}
+
+/* growable hash set of int32 vertex ids (value -1 marks an empty slot) */
+typedef struct { int32_t *slot; int64_t cap, size; } vset_t;
+
+static void vset_init(vset_t *s) { s->slot = NULL; s->cap = 0; s->size = 0; }
+
+static void vset_insert(vset_t *s, int32_t x);
+
+static void vset_grow(vset_t *s) {
+    int64_t ncap = s->cap ? s->cap * 2 : 16;
+    int32_t *old = s->slot; int64_t ocap = s->cap;
+    s->slot = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncap);
+    for (int64_t i = 0; i < ncap; i++) s->slot[i] = -1;
+    s->cap = ncap; s->size = 0;
+    for (int64_t i = 0; i < ocap; i++) if (old[i] >= 0) vset_insert(s, old[i]);
+    free(old);
+}
+
+static void vset_insert(vset_t *s, int32_t x) {
+    if ((s->size + 1) * 2 > s->cap) vset_grow(s);
+    uint64_t h = mix64((uint64_t)(uint32_t)x) & (uint64_t)(s->cap - 1);
+    while (s->slot[h] >= 0) {
+        if (s->slot[h] == x) return;
+        h = (h + 1) & (uint64_t)(s->cap - 1);
+    }
+    s->slot[h] = x; s->size++;
+}
+
+/* ------------------------------------------------------------------ canonical codes */
+
+/* A code is the label sequence plus the adjacency sequence packed into an integer whose most
+ * significant used bit is the first pair (0,1); integer order equals sequence order. */
+typedef struct { int32_t lab[OR_MAXK]; uint32_t adj; } code_t;
+
+static int code_cmp(const code_t *a, const code_t *b, int k) {
+    for (int i = 0; i < k; i++)
+        if (a->lab[i] != b->lab[i]) return a->lab[i] < b->lab[i] ? -1 : 1;
+    if (a->adj != b->adj) return a->adj < b->adj ? -1 : 1;
+    return 0;
+}
+
+typedef struct {
+    int k, npairs, nperm;
+    uint8_t *perms;                 /* nperm x k, all permutations of 0..k-1 */
+    int pi[OR_MAXK * OR_MAXK];      /* pair index of (c1, c2), c1 < c2 */
+} canon_ctx_t;
+
+static void gen_perms(canon_ctx_t *cx) {
+    int k = cx->k, f = 1;
+    for (int i = 2; i <= k; i++) f *= i;
+    cx->nperm = f;
+    cx->perms = (uint8_t *)malloc((size_t)f * (size_t)(k ? k : 1));
+    uint8_t a[OR_MAXK];
+    for (int i = 0; i < k; i++) a[i] = (uint8_t)i;
+    for (int p = 0; p < f; p++) {
+        memcpy(cx->perms + (size_t)p * k, a, (size_t)k);
+        /* next lexicographic permutation */
+        int i = k - 2;
+        while (i >= 0 && a[i] > a[i + 1]) i--;
+        if (i < 0) break;
+        int j = k - 1;
+        while (a[j] < a[i]) j--;
+        uint8_t t = a[i]; a[i] = a[j]; a[j] = t;
+        for (int l = i + 1, r = k - 1; l < r; l++, r--) { t = a[l]; a[l] = a[r]; a[r] = t; }
+    }
+    int q = 0;
+    for (int c1 = 0; c1 < k; c1++)
+        for (int c2 = c1 + 1; c2 < k; c2++) cx->pi[c1 * OR_MAXK + c2] = q++;
+    cx->npairs = q;
+}
+
+/* code of permutation perm applied to (lab, adjrow): position c holds vertex perm[c] */
+static void code_of(const canon_ctx_t *cx, const uint8_t *perm, const int32_t *lab,
+                    const uint32_t *adjrow, code_t *out) {
+    int k = cx->k;
+    for (int c = 0; c < k; c++) out->lab[c] = lab[perm[c]];
+    for (int c = k; c < OR_MAXK; c++) out->lab[c] = 0;
+    uint32_t a = 0;
+    for (int c1 = 0; c1 < k; c1++)
+        for (int c2 = c1 + 1; c2 < k; c2++)
+            a = (a << 1) | ((adjrow[perm[c1]] >> perm[c2]) & 1u);
+    out->adj = a;
+}
+
+/* ------------------------------------------------------------------ pattern registry */
+
+typedef struct {
+    code_t code;
+    int64_t count;                  /* embeddings (V', E') of this pattern */
+    vset_t dom[OR_MAXK];            /* D[P][c] */
+} pattern_t;
+
+typedef struct {
+    uint64_t key_lab; uint32_t key_adj; int used;
+    int32_t pattern;                /* index into patterns */
+    int32_t nopt; int64_t perm_off; /* optimal permutations, k bytes each, in perm pool */
+} memo_t;
+
+typedef struct {
+    int k, mode;
+    const int32_t *row_ptr, *col, *labels;
+    int32_t n;
+    canon_ctx_t cx;
+    pattern_t *pat; int64_t npat, cappat;
+    /* pattern lookup by canonical code: open addressing over indices */
+    int32_t *pat_slot; int64_t pat_cap;
+    memo_t *memo; int64_t memo_cap, memo_size;
+    uint8_t *pool; int64_t pool_size, pool_cap;
+} oracle_t;
+
+static uint64_t code_hash(const code_t *c, int k) {
+    uint64_t h = 0x9e3779b97f4a7c15ULL;
+    for (int i = 0; i < k; i++) h = mix64(h ^ (uint64_t)(uint32_t)c->lab[i]);
+    return mix64(h ^ c->adj);
+}
+
+static int32_t pattern_find_or_add(oracle_t *o, const code_t *c) {
+    if ((o->npat + 1) * 2 > o->pat_cap) {
+        int64_t ncap = o->pat_cap ? o->pat_cap * 2 : 64;
+        free(o->pat_slot);
+        o->pat_slot = (int32_t *)malloc(sizeof(int32_t) * (size_t)ncap);
+        for (int64_t i = 0; i < ncap; i++) o->pat_slot[i] = -1;
+        o->pat_cap = ncap;
+        for (int64_t p = 0; p < o->npat; p++) {
+            uint64_t h = code_hash(&o->pat[p].code, o->k) & (uint64_t)(ncap - 1);
+            while (o->pat_slot[h] >= 0) h = (h + 1) & (uint64_t)(ncap - 1);
+            o->pat_slot[h] = (int32_t)p;
+        }
+    }
+    uint64_t h = code_hash(c, o->k) & (uint64_t)(o->pat_cap - 1);
+    while (o->pat_slot[h] >= 0) {
+        if (code_cmp(&o->pat[o->pat_slot[h]].code, c, o->k) == 0) return o->pat_slot[h];
+        h = (h + 1) & (uint64_t)(o->pat_cap - 1);
+    }
+    if (o->npat == o->cappat) {
+        o->cappat = o->cappat ? o->cappat * 2 : 64;
+        o->pat = (pattern_t *)realloc(o->pat, sizeof(pattern_t) * (size_t)o->cappat);
+    }
+    pattern_t *p = &o->pat[o->npat];
+    p->code = *c; p->count = 0;
+    for (int i = 0; i < OR_MAXK; i++) vset_init(&p->dom[i]);
+    o->pat_slot[h] = (int32_t)o->npat;
+    return (int32_t)o->npat++;
+}
+
+static memo_t *memo_lookup(oracle_t *o, uint64_t klab, uint32_t kadj) {
+    if ((o->memo_size + 1) * 2 > o->memo_cap) {
+        int64_t ncap = o->memo_cap ? o->memo_cap * 2 : 1024;
+        memo_t *old = o->memo; int64_t ocap = o->memo_cap;
+        o->memo = (memo_t *)calloc((size_t)ncap, sizeof(memo_t));
+        o->memo_cap = ncap;
+        for (int64_t i = 0; i < ocap; i++) if (old[i].used) {
+            uint64_t h = mix64(old[i].key_lab ^ mix64(old[i].key_adj)) & (uint64_t)(ncap - 1);
+            while (o->memo[h].used) h = (h + 1) & (uint64_t)(ncap - 1);
+            o->memo[h] = old[i];
+        }
+        free(old);
+    }
+    uint64_t h = mix64(klab ^ mix64(kadj)) & (uint64_t)(o->memo_cap - 1);
+    while (o->memo[h].used) {
+        if (o->memo[h].key_lab == klab && o->memo[h].key_adj == kadj) return &o->memo[h];
+        h = (h + 1) & (uint64_t)(o->memo_cap - 1);
+    }
+    memo_t *m = &o->memo[h];
+    m->used = 1; m->key_lab = klab; m->key_adj = kadj; m->pattern = -1;
+    o->memo_size++;
+    return m;
+}
+
+/* canonicalise one raw labeled graph (lab, adjrow over positions 0..k-1), memoised */
+static memo_t *canonical(oracle_t *o, const int32_t *lab, const uint32_t *adjrow) {
+    int k = o->k;
+    uint64_t klab = 0; uint32_t kadj = 0;
+    for (int i = 0; i < k; i++) klab = (klab << 8) | (uint64_t)(lab[i] & 0xff);
+    /* raw key: the label tuple and the packed upper triangle of the adjacency */
+    for (int c1 = 0; c1 < k; c1++)
+        for (int c2 = c1 + 1; c2 < k; c2++)
+            kadj = (kadj << 1) | ((adjrow[c1] >> c2) & 1u);
+    memo_t *m = memo_lookup(o, klab, kadj);
+    if (m->pattern >= 0) return m;
+    code_t best, cur;
+    int have = 0;
+    for (int p = 0; p < o->cx.nperm; p++) {
+        code_of(&o->cx, o->cx.perms + (size_t)p * k, lab, adjrow, &cur);
+        if (!have || code_cmp(&cur, &best, k) < 0) { best = cur; have = 1; }
+    }
+    int32_t nopt = 0;
+    for (int p = 0; p < o->cx.nperm; p++) {
+        code_of(&o->cx, o->cx.perms + (size_t)p * k, lab, adjrow, &cur);
+        if (code_cmp(&cur, &best, k) == 0) nopt++;
+    }
+    if (o->pool_size + (int64_t)nopt * k > o->pool_cap) {
+        int64_t ncap = o->pool_cap ? o->pool_cap * 2 : 4096;
+        while (ncap < o->pool_size + (int64_t)nopt * k) ncap *= 2;
+        o->pool = (uint8_t *)realloc(o->pool, (size_t)ncap);
+        o->pool_cap = ncap;
+    }
+    m->perm_off = o->pool_size; m->nopt = nopt;
+    for (int p = 0; p < o->cx.nperm; p++) {
+        code_of(&o->cx, o->cx.perms + (size_t)p * k, lab, adjrow, &cur);
+        if (code_cmp(&cur, &best, k) == 0) {
+            memcpy(o->pool + o->pool_size, o->cx.perms + (size_t)p * k, (size_t)k);
+            o->pool_size += k;
+        }
+    }
+    m->pattern = pattern_find_or_add(o, &best);
+    return m;
+}
+
+/* ------------------------------------------------------------------ embeddings of one set */
+
+static int spans_connected(int k, const uint32_t *adjrow) {
+    uint32_t seen = 1u, frontier = 1u;
+    while (frontier) {
+        uint32_t nxt = 0;
+        for (int i = 0; i < k; i++) if (frontier >> i & 1u) nxt |= adjrow[i];
+        nxt &= ~seen;
+        seen |= nxt; frontier = nxt;
+    }
+    return seen == ((1u << k) - 1u);
+}
+
+static void record(oracle_t *o, const int32_t *u, const int32_t *lab, const uint32_t *adjrow) {
+    memo_t *m = canonical(o, lab, adjrow);
+    pattern_t *p = &o->pat[m->pattern];
+    p->count++;
+    const uint8_t *perm = o->pool + m->perm_off;
+    for (int32_t q = 0; q < m->nopt; q++, perm += o->k)
+        for (int c = 0; c < o->k; c++) vset_insert(&p->dom[c], u[perm[c]]);
+}
+
+static void process_set(oracle_t *o, const int32_t *vs) {
+    int k = o->k;
+    int32_t u[OR_MAXK], lab[OR_MAXK];
+    for (int i = 0; i < k; i++) u[i] = vs[i];
+    /* ascending vertex order */
+    for (int i = 1; i < k; i++)
+        for (int j = i; j > 0 && u[j - 1] > u[j]; j--) { int32_t t = u[j]; u[j] = u[j - 1]; u[j - 1] = t; }
+    for (int i = 0; i < k; i++) lab[i] = o->labels[u[i]];
+    int ne = 0, ea[OR_MAXK * OR_MAXK], eb[OR_MAXK * OR_MAXK];
+    uint32_t full[OR_MAXK] = {0};
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++)
+            if (adjacent(o->row_ptr, o->col, u[i], u[j])) {
+                ea[ne] = i; eb[ne] = j; ne++;
+                full[i] |= 1u << j; full[j] |= 1u << i;
+            }
+    if (o->mode == 1 || k == 1) {          /* vertex-induced: the induced edge set only */
+        record(o, u, lab, full);
+        return;
+    }
+    /* edge-induced: every subset of the induced edges that spans V' connectedly */
+    uint64_t nsub = 1ULL << ne;
+    for (uint64_t s = 1; s < nsub; s++) {
+        if (__builtin_popcountll(s) < (unsigned)(k - 1)) continue;   /* a spanning tree needs k-1 edges */
+        uint32_t adjrow[OR_MAXK] = {0};
+        for (int e = 0; e < ne; e++) if (s >> e & 1ULL) {
+            adjrow[ea[e]] |= 1u << eb[e]; adjrow[eb[e]] |= 1u << ea[e];
+        }
+        if (spans_connected(k, adjrow)) record(o, u, lab, adjrow);
+    }
+}
+
+/* ------------------------------------------------------------------ ESU enumeration */
+
+static void esu_extend(oracle_t *o, int32_t *sub, int depth, const int32_t *ext, int64_t next,
+                       int32_t root) {
+    if (depth == o->k) { process_set(o, sub); return; }
+    if (next == 0) return;
+    /* extension array for children: at most next - 1 + deg(w) entries */
+    for (int64_t idx = next - 1; idx >= 0; idx--) {
+        int32_t w = ext[idx];
+        int64_t deg = o->row_ptr[w + 1] - o->row_ptr[w];
+        int32_t *ext2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(idx + deg + 1));
+        int64_t n2 = 0;
+        for (int64_t j = 0; j < idx; j++) ext2[n2++] = ext[j];   /* Vext minus w (and minus the ones already tried) */
+        for (int32_t q = o->row_ptr[w]; q < o->row_ptr[w + 1]; q++) {
+            int32_t x = o->col[q];
+            if (x <= root) continue;
+            int excl = 1;
+            for (int d = 0; d < depth && excl; d++)
+                if (sub[d] == x || adjacent(o->row_ptr, o->col, sub[d], x)) excl = 0;
+            if (excl) ext2[n2++] = x;
+        }
+        sub[depth] = w;
+        esu_extend(o, sub, depth + 1, ext2, n2, root);
+        free(ext2);
+    }
+}
+
+/* ------------------------------------------------------------------ public entry points */
+
+typedef struct {
+    int k; int64_t npat;
+    int32_t *labels;     /* npat x k */
+    uint64_t *adj;       /* bit (i*k + j) set for canonical edge i < j */
+    int64_t *support, *count;
+} oracle_result_t;
+
+static int code_sort_k;
+static const pattern_t *code_sort_base;
+static int idx_cmp(const void *a, const void *b) {
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return code_cmp(&code_sort_base[x].code, &code_sort_base[y].code, code_sort_k);
+}
+
+/*
+ * oracle_mine: every pattern of exactly k vertices with MNI support >= t.
+ *   mode 0 = edge-induced, 1 = vertex-induced.  Only connected sets whose smallest vertex lies
+ *   in [root_begin, root_end) are enumerated (the full graph: 0, n); a partial range gives a
+ *   bounded sample of the work.  Returns NULL on bad arguments.
+ */
+oracle_result_t *oracle_mine(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                             const int32_t *labels, int32_t k, int32_t mode, int64_t t,
+                             int32_t root_begin, int32_t root_end) {
+    if (k < 1 || k > OR_MAXK || n < 0 || (mode != 0 && mode != 1)) return NULL;
+    oracle_t o;
+    memset(&o, 0, sizeof(o));
+    o.k = k; o.mode = mode; o.row_ptr = row_ptr; o.col = col; o.labels = labels; o.n = n;
+    o.cx.k = k;
+    gen_perms(&o.cx);
+    if (root_begin < 0) root_begin = 0;
+    if (root_end > n) root_end = n;
+    int32_t sub[OR_MAXK];
+    for (int32_t v = root_begin; v < root_end; v++) {
+        sub[0] = v;
+        int64_t deg = row_ptr[v + 1] - row_ptr[v];
+        int32_t *ext = (int32_t *)malloc(sizeof(int32_t) * (size_t)(deg + 1));
+        int64_t ne = 0;
+        for (int32_t q = row_ptr[v]; q < row_ptr[v + 1]; q++) if (col[q] > v) ext[ne++] = col[q];
+        esu_extend(&o, sub, 1, ext, ne, v);
+        free(ext);
+    }
+    /* filter and sort */
+    oracle_result_t *r = (oracle_result_t *)calloc(1, sizeof(oracle_result_t));
+    r->k = k;
+    int64_t *keep = (int64_t *)malloc(sizeof(int64_t) * (size_t)(o.npat + 1));
+    int64_t nk = 0;
+    for (int64_t p = 0; p < o.npat; p++) {
+        int64_t sigma = -1;
+        for (int c = 0; c < k; c++) {
+            int64_t s = o.pat[p].dom[c].size;
+            if (sigma < 0 || s < sigma) sigma = s;
+        }
+        if (sigma >= t) keep[nk++] = p;
+    }
+    code_sort_k = k; code_sort_base = o.pat;
+    qsort(keep, (size_t)nk, sizeof(int64_t), idx_cmp);
+    r->npat = nk;
+    r->labels = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nk * k + 1));
+    r->adj = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk + 1));
+    r->support = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
+    r->count = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
+    for (int64_t q = 0; q < nk; q++) {
+        const pattern_t *p = &o.pat[keep[q]];
+        int64_t sigma = -1;
+        for (int c = 0; c < k; c++) {
+            int64_t s = p->dom[c].size;
+            if (sigma < 0 || s < sigma) sigma = s;
+        }
+        for (int c = 0; c < k; c++) r->labels[q * k + c] = p->code.lab[c];
+        /* unpack the row-major adjacency sequence into bit (i*k + j) */
+        uint64_t bits = 0;
+        int np = k * (k - 1) / 2, idx = 0;
+        for (int i = 0; i < k; i++)
+            for (int j = i + 1; j < k; j++, idx++)
+                if ((p->code.adj >> (np - 1 - idx)) & 1u) bits |= 1ULL << (i * k + j);
+        r->adj[q] = bits;
+        r->support[q] = sigma;
+        r->count[q] = p->count;
+    }
+    free(keep);
+    for (int64_t p = 0; p < o.npat; p++)
+        for (int c = 0; c < OR_MAXK; c++) free(o.pat[p].dom[c].slot);
+    free(o.pat); free(o.pat_slot); free(o.memo); free(o.pool); free(o.cx.perms);
+    return r;
+}
+
+int64_t oracle_result_count(const oracle_result_t *r) { return r ? r->npat : -1; }
+
+void oracle_result_copy(const oracle_result_t *r, int32_t *labels, uint64_t *adj,
+                        int64_t *support, int64_t *count) {
+    if (!r) return;
+    memcpy(labels, r->labels, sizeof(int32_t) * (size_t)(r->npat * r->k));
+    memcpy(adj, r->adj, sizeof(uint64_t) * (size_t)r->npat);
+    memcpy(support, r->support, sizeof(int64_t) * (size_t)r->npat);
+    memcpy(count, r->count, sizeof(int64_t) * (size_t)r->npat);
+}
+
+void oracle_free(oracle_result_t *r) {
+    if (!r) return;
+    free(r->labels); free(r->adj); free(r->support); free(r->count); free(r);
+}
