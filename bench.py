@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark: exact frequent subgraph mining (two-vertex exploration) on one GB300.
+
+Workload (default): Chung-Lu power-law graph, 100k vertices, 1.1M undirected edges, degree
+exponent 2.1, 29 vertex labels drawn Zipf(s=1.2), int32 CSR, seed 1 (MiCo-shaped, synthetic);
+exact edge-induced FSM of size k=4 under MNI support at thresholds 300, 1000 and 3000.
+One step = the three fsm_mine calls on the resident graph.
+
+Printed (rank 0, one JSON line): value = embeddings extended per second over the whole job
+(accepted joins of every level / device time), e2e = the same metric through the C ABI from
+host buffers (graph upload, mining, result download inside the timed region), roofline of the
+dominant extension-kernel pass, the CPU oracle on a bounded sample, clocks during the timed
+region.  ``--impl reference`` times the CPU oracle alone on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="cl100k")
+    p.add_argument("--k", type=int, default=4)
+    p.add_argument("--thresholds", default="300,1000,3000")
+    p.add_argument("--cap", type=float, default=None, help="Chung-Lu degree cap (default: sqrt(2m))")
+    p.add_argument("--mode", choices=["edge", "vertex"], default="edge")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def workload_graph(args):
+    import graphgen as gg
+    return gg.workload(args.workload, cap=args.cap if args.cap is not None else "default")
+
+
+def workload_config(args, g):
+    return {"workload": f"{args.workload}: Chung-Lu n={g.n} m={g.m} beta={g.meta.get('beta')} "
+                        f"labels={g.num_labels} {g.meta.get('label_law')}({g.meta.get('zipf_s')}) "
+                        f"seed={g.meta.get('seed')} cap={round(float(g.meta.get('cap')), 1)}",
+            "k": args.k, "thresholds": [int(x) for x in args.thresholds.split(",")], "mode": args.mode,
+            "d_max": int(g.degrees().max()), "graph_hash": g.content_hash(),
+            "l2": "flushed before every timed step (256 MiB write)"}
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle sample
+
+def oracle_sample(g, k: int, target_s: float):
+    """Time the oracle (as it stands, one thread) on the connected k-subgraphs whose smallest
+    vertex id is below R, R grown until a run lasts about target_s seconds."""
+    import oracle
+    oracle.build()
+    R = 16
+    while True:
+        t0 = time.perf_counter()
+        o = oracle.mine(g, k, 1, roots=(0, R))
+        dt = time.perf_counter() - t0
+        if dt >= target_s * 0.6 or R >= g.n:
+            emb = int(o["count"].sum())
+            return {"value": emb / dt, "unit": "embeddings/s", "cores": 1, "kind": "oracle",
+                    "sample": f"all connected {k}-vertex embeddings whose smallest vertex id is < {R} "
+                              f"({R}/{g.n} ESU roots): {emb} embeddings in {dt:.2f} s",
+                    "seconds": dt, "roots": R, "embeddings": emb}
+        grow = target_s / max(dt, 1e-3)
+        R = min(g.n, max(R * 2, int(R * min(grow, 16))))
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def traffic_for(kernel_pass: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    source of the extension kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "extend_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    src = os.path.join(ROOT, "paper_2101_07690_gb300", "csrc", "fsm_extend.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    ent = d.get(kernel_pass)
+    if not ent or d.get("source_sha") != h:
+        return None
+    return ent.get("dram_bytes_per_full_launch")
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2101_07690_gb300 import build, fsm
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    fsm.load()
+    g = workload_graph(args)
+    ths = [int(x) for x in args.thresholds.split(",")]
+    stream = torch.cuda.Stream()
+    G = fsm.Graph.from_graphgen(g, args.mode)
+    G.set_option("stream", stream.cuda_stream)
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step(profile: bool):
+        G.set_option("profile", 1 if profile else 0)
+        tot = {"embeddings": 0, "kernel_launches": 0, "count_ns": 0, "domain_ns": 0, "emit_ns": 0,
+               "count_bytes": 0, "domain_bytes": 0, "emit_bytes": 0, "count_launches": 0,
+               "domain_launches": 0, "emit_launches": 0, "patterns_out": 0, "final_embeddings": 0}
+        for t in ths:
+            r = G.mine(args.k, t, stats=True)
+            s = r["stats"]
+            for key in tot:
+                if key in s:
+                    tot[key] += s[key]
+            tot["patterns_out"] += len(r["support"])
+        return tot
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    times, agg = [], None
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tot = step(True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            agg = tot if agg is None else {k2: agg[k2] + tot[k2] for k2 in agg}
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        e = torch.tensor([float(agg["embeddings"])], device="cuda", dtype=torch.float64)
+        dist.all_reduce(e)
+        emb_all = float(e.item())
+    else:
+        emb_all = float(agg["embeddings"])
+    value = emb_all / (total_ms / 1e3)
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        rp = torch.from_numpy(g.row_ptr).pin_memory()
+        cl = torch.from_numpy(g.col).pin_memory()
+        lb = torch.from_numpy(g.labels).pin_memory()
+        h2d = (rp.numel() + cl.numel() + lb.numel()) * 4
+        d2h, emb_e2e, t_e2e = 0, 0, 0.0
+        for it in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = fsm.fsm_load_graph(rp.data_ptr(), cl.data_ptr(), lb.data_ptr(), g.n, g.num_labels)
+            fsm.fsm_set_option(h, "mode", 0 if args.mode == "edge" else 1)
+            for t in ths:
+                r = fsm.fsm_mine(h, args.k, t)
+                out = fsm.fsm_result_copy(r, args.k)
+                emb_e2e += fsm.fsm_result_stat(r, "embeddings")
+                d2h += sum(a.nbytes for a in out.values())
+                fsm.fsm_free_result(r)
+            fsm.fsm_free_graph(h)
+            t_e2e += time.perf_counter() - t0
+        e2e = {"value": emb_e2e / t_e2e, "unit": "embeddings/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h // args.steps, "ms_per_step": 1e3 * t_e2e / args.steps}
+
+    # roofline of the dominant extension pass (launch durations from CUDA events in the library)
+    passes = {p: (agg[f"{p}_ns"], agg[f"{p}_bytes"], agg[f"{p}_launches"]) for p in ("count", "domain", "emit")}
+    dom = max(passes, key=lambda p: passes[p][0])
+    ns, byts, nl = passes[dom]
+    peak, peak_kind = read_peaks()
+    achieved = (byts / nl) / (ns / nl) if ns > 0 and nl > 0 else 0.0   # bytes per ns == GB/s
+    roofline = {"bound": "hbm", "kernel": f"extend_kernel<L={args.k - 2}, PASS_{dom.upper()}>",
+                "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": traffic_for(dom), "launches": nl, "avg_launch_ms": round(ns / nl / 1e6, 3) if nl else None,
+                "algorithmic_bytes_per_launch": byts / nl if nl else None,
+                "share_of_step": round(ns / 1e6 / total_ms, 3) if total_ms else None,
+                "pass_ms": {p: round(v[0] / 1e6 / args.steps, 2) for p, v in passes.items()}}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(g, args.k, args.cpu_seconds)
+        cpu = {k2: cpu[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+
+    G.close()
+    if rank == 0:
+        line = {"metric": "embeddings extended per second (exact edge-induced FSM, MNI support)",
+                "value": round(value, 1), "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+                "data": "synthetic (seeded Chung-Lu stand-in for the paper's MiCo graph)",
+                "config": dict(workload_config(args, g), parallelism=f"replicas{world}"),
+                "e2e": e2e, "gpu_launches": int(agg["kernel_launches"]),
+                "embeddings_per_step": int(agg["embeddings"] // args.steps),
+                "patterns_per_step": int(agg["patterns_out"] // args.steps),
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    g = workload_graph(args)
+    samples = []
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm state worth priming beyond its first compile
+    cfg = None
+    for _ in range(args.steps):
+        s = oracle_sample(g, args.k, args.cpu_seconds / 2)
+        samples.append(s)
+    value = sum(s["embeddings"] for s in samples) / sum(s["seconds"] for s in samples)
+    ms = 1e3 * sum(s["seconds"] for s in samples) / len(samples)
+    cfg = workload_config(args, g)
+    line = {"impl": "reference", "metric": "embeddings extended per second (exact edge-induced FSM, MNI support)",
+            "value": round(value, 1), "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": dict(cfg, parallelism="cpu"),
+            "cpu_baseline": {"value": round(value, 1), "unit": "embeddings/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[-1]["sample"]},
+            "e2e": {"value": round(value, 1), "unit": "embeddings/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

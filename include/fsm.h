@@ -1,0 +1,154 @@
+/*
+ * fsm.h -- C ABI of the GB300 frequent-subgraph-mining library (two-vertex exploration).
+ *
+ * The library finds every size-k pattern of one labeled, undirected input graph whose MNI
+ * support is at least t (the FSM problem of Section 2.2).  Mining runs level by level
+ * (sizes 1 -> 3 -> 5 -> 7 for odd k, 2 -> 4 -> 6 -> 8 for even k): every embedding of every
+ * frequent size-l pattern is joined with every frequent size-3 subgraph (wedge or triangle)
+ * that shares exactly one vertex with it (two-vertex exploration, Section 4.1, Theorem 1),
+ * duplicates are removed by smallest-vertex-first dissection (Section 4.3, Algorithm 1),
+ * joins whose joining-point triples form an infrequent size-3 pattern are pruned
+ * (Section 4.5), results are grouped by index-based quick pattern (Section 4.4) and each
+ * distinct quick pattern is canonicalised once; MNI support (Definition 2) is aggregated in
+ * per-pattern, per-orbit domain bitmaps.  Every step runs in this library's CUDA kernels on
+ * one GPU; nothing here falls back to the CPU.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: FSM_OK (0) or a negative FSM_E* code; fsm_last_error() then holds a
+ *     thread-local message.  On error, every out-pointer is left NULL / untouched.
+ *   - Pointers passed in are HOST pointers unless the name says otherwise; the library
+ *     copies what it needs and never keeps or frees caller memory.
+ *   - A graph handle owns device memory until fsm_free_graph(); a result handle owns host
+ *     memory until fsm_free_result().  Handles are not thread-safe: one thread per handle.
+ *   - Vertex ids are int32 in [0, n); labels are int32 in [0, num_labels), num_labels <= 64.
+ *   - Pattern encoding (output): labels[k] in canonical order, and adj_bits with bit
+ *     (i*k + j), LSB = bit 0, set for every canonical edge i < j.  The canonical form of a
+ *     labeled graph is the lexicographically smallest (label sequence, adjacency sequence
+ *     A(0,1), A(0,2), ..., A(k-2,k-1)) over all vertex orders; results are sorted ascending by
+ *     that same (label sequence, adjacency sequence) key.
+ */
+#ifndef FSM_H
+#define FSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    FSM_OK = 0,
+    FSM_EINVAL = -1,        /* bad argument or malformed CSR */
+    FSM_ENOMEM = -2,        /* a device or host allocation failed */
+    FSM_ECUDA = -3,         /* a CUDA runtime call or kernel failed */
+    FSM_ETIMEOUT = -4,      /* a bounded device loop gave up (see fsm_last_error) */
+    FSM_EUNSUPPORTED = -5   /* input or request outside the supported range */
+};
+
+typedef struct fsm_graph fsm_graph;
+typedef struct fsm_result fsm_result;
+
+/*
+ * fsm_load_graph -- copy one labeled graph G = (V, E, L) (Section 2.1) to the current CUDA
+ * device and prepare it for mining.
+ *   row_ptr  int32[n+1], row_ptr[0] = 0, nondecreasing; row_ptr[n] = 2|E| = nnz.
+ *   col      int32[nnz]: the neighbours of v are col[row_ptr[v] .. row_ptr[v+1]), sorted
+ *            strictly ascending; every undirected edge appears in both directions; no
+ *            self-loops, no duplicates.
+ *   labels   int32[n]: vertex labels in [0, num_labels).
+ *   n >= 1, 1 <= num_labels <= 64.
+ * The CSR is validated on the device (sortedness, symmetry, self-loops, duplicates, label
+ * range): a malformed graph gives FSM_EINVAL.  nnz >= 2^31 gives FSM_EUNSUPPORTED.
+ * Ownership: the arrays are copied; *out owns device memory until fsm_free_graph().
+ */
+int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *labels,
+                   int32_t n, int32_t num_labels, fsm_graph **out);
+
+/*
+ * fsm_set_option -- set a per-graph option (takes effect on the next fsm_mine call).
+ *   "mode"       0 = edge-induced embeddings (default; the experiments' setting, Section 6.1),
+ *                1 = vertex-induced embeddings (Section 2.1).
+ *   "stream"     a cudaStream_t (cast to int64) that all later work of this graph is issued on;
+ *                0 restores the library's own stream.  The caller keeps ownership.
+ *   "launch"     0 = one launch per frontier batch (default), 1 = persistent work-stealing
+ *                launch over all batches of a level.  Both give identical results.
+ *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
+ *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
+ *   "profile"    1 = time every extension-kernel launch with CUDA events and sum its algorithmic
+ *                bytes (reported by fsm_result_stat); adds one synchronisation per launch.
+ * Unknown keys or out-of-range values give FSM_EINVAL.
+ */
+int fsm_set_option(fsm_graph *g, const char *key, int64_t value);
+
+/*
+ * fsm_mine -- every pattern with exactly k vertices and MNI support >= min_support
+ * (Section 2.2 problem statement; Definition 2).
+ *   1 <= k <= 8, min_support >= 1, sample_rate in (0, 1]; 1.0 means exact mining.  Sampled
+ *   mining (sample_rate < 1) is not available in this build and gives FSM_EUNSUPPORTED.
+ * The supports returned are exact MNI supports; the embedding counts are exact for every
+ * returned pattern.
+ * Ownership: *out is a host-side result owned by the caller until fsm_free_result().
+ */
+int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate,
+             fsm_result **out);
+
+/* Number of patterns in a result (>= 0), or FSM_EINVAL for a NULL result. */
+int64_t fsm_result_count(const fsm_result *r);
+
+/*
+ * fsm_result_get -- pattern i (0 <= i < count) of a result.
+ *   labels_k  int32[k] written with the canonical labels (may be NULL).
+ *   adj_bits  bit (i*k + j) set per canonical edge i < j (may be NULL).
+ *   support   MNI support (may be NULL).
+ */
+int fsm_result_get(const fsm_result *r, int64_t i, int32_t *labels_k, uint64_t *adj_bits,
+                   int64_t *support);
+
+/* Number of embeddings (subgraphs, not maps) of pattern i, counted during mining. */
+int fsm_result_embeddings(const fsm_result *r, int64_t i, int64_t *count);
+
+/*
+ * fsm_result_copy -- all patterns at once: labels int32[count*k] (row-major), adj_bits
+ * uint64[count], support int64[count], embeddings int64[count]; any pointer may be NULL.
+ */
+int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, int64_t *support,
+                    int64_t *embeddings);
+
+/*
+ * fsm_result_stat -- a run counter of the mining call that made r:
+ *   "k", "levels", "candidates" (joins tested), "embeddings" (accepted joins, all levels),
+ *   "final_embeddings" (accepted joins of the last level), "quick_patterns" (distinct index
+ *   based quick patterns, i.e. canonicalisations, all levels), "patterns" (distinct patterns
+ *   of the last level), "live_patterns" (last-level patterns given a domain),
+ *   "frontier_max" (largest stored level), "kernel_launches", "time_ns" (device time of the
+ *   whole call, CUDA events), "final_level_ns" (device time of the last level); with the
+ *   "profile" option also, per extension pass P in {count, domain, emit}: "P_ns" (summed
+ *   launch durations), "P_launches", "P_bytes" (algorithmic bytes: 4 * (d(v) + end pieces of v)
+ *   per (embedding, key position) unit, 4 * (l + 1) per embedding read, and for emit
+ *   4 * (l + 3) per embedding written).
+ */
+int fsm_result_stat(const fsm_result *r, const char *key, int64_t *value);
+
+void fsm_free_result(fsm_result *r);
+void fsm_free_graph(fsm_graph *g);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *fsm_last_error(void);
+
+/*
+ * fsm_debug_dissect -- host build of the library's smallest-vertex-first dissection
+ * (Section 4.3, Algorithm 1, function dissect with n = 3) on one connected subgraph:
+ *   k (4..8) vertices with global ids ids[k] (distinct), adjacency rows adj[k] (bit j of
+ *   adj[i] set when i ~ j).  Writes the 3-vertex part as a bit mask over the k local indices
+ *   (*l_mask) and the shared vertex's local index (*join).  Returns FSM_OK, or
+ *   FSM_EINVAL if the input is not a connected simple graph.  *used_fallback is 1 when the
+ *   greedy rule found no dissection and the exhaustive rule answered instead.  Test hook only.
+ */
+int fsm_debug_dissect(int32_t k, const int32_t *ids, const uint32_t *adj, uint32_t *l_mask,
+                      int32_t *join, int32_t *used_fallback);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSM_H */

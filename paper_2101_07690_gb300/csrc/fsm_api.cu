@@ -1,0 +1,785 @@
+// fsm_api.cu -- the C ABI (include/fsm.h) and the host-side level loop.
+//
+// Level loop (Section 3 workflow, generalised level by level):
+//   size 1   label classes; MNI of a one-vertex pattern is its class size;
+//   size 2   labeled edge patterns with per-orbit domain bitmaps;
+//   size 3   two-vertex extension of every size-1 embedding (each connected size-3 subgraph is
+//            produced once, keyed at its smallest vertex); its frequent patterns are the pieces
+//            of every later join and the table of the joining-point pruning (Section 4.5);
+//   l -> l+2 two-vertex extension of the stored frequent size-l embeddings (odd k from size 3,
+//            even k from size 2), three passes over the same enumeration: count quick patterns,
+//            fill MNI domains of patterns that can still reach the threshold, and (non-final
+//            levels) emit the embeddings of frequent patterns in canonical order.
+// Between passes, each distinct quick pattern is canonicalised once (Section 4.4) and the
+// canonical codes are sorted so pattern ids are deterministic.
+#include "fsm.h"
+#include "fsm_extend.cuh"
+#include "fsm_kernels.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+using namespace fsm;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct FsmError {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string &msg) { throw FsmError{code, msg}; }
+
+void ck(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        fail(FSM_ENOMEM, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    fail(FSM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int set_error(const FsmError &e) {
+    g_last_error = e.msg;
+    return e.code;
+}
+
+std::once_flag g_pool_once[64];
+
+void keep_pool(int dev) {
+    if (dev < 0 || dev >= 64) return;
+    std::call_once(g_pool_once[dev], [dev]() {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+    });
+}
+
+// Stream-ordered device allocations released together.
+struct Arena {
+    cudaStream_t st;
+    std::vector<void *> ptrs;
+    explicit Arena(cudaStream_t s) : st(s) {}
+    template <class T>
+    T *get(int64_t n) {
+        void *p = nullptr;
+        size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
+        bytes = (bytes + 255) & ~(size_t)255;
+        ck(cudaMallocAsync(&p, bytes, st), "device allocation");
+        ptrs.push_back(p);
+        return (T *)p;
+    }
+    void release(void *p) {
+        auto it = std::find(ptrs.begin(), ptrs.end(), p);
+        if (it != ptrs.end()) {
+            cudaFreeAsync(p, st);
+            ptrs.erase(it);
+        }
+    }
+    ~Arena() {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+template <class T>
+T d2h(const T *dptr, cudaStream_t st) {
+    T v{};
+    ck(cudaMemcpyAsync(&v, dptr, sizeof(T), cudaMemcpyDeviceToHost, st), "copy to host");
+    ck(cudaStreamSynchronize(st), "stream synchronize");
+    return v;
+}
+
+} // namespace
+
+struct fsm_graph {
+    int device = 0;
+    int32_t n = 0, NL = 0;
+    int64_t nnz = 0;
+    cudaStream_t own_stream = nullptr, stream = nullptr;
+    int mode = 0, launch = 0, profile = 0;
+    int32_t chunk = 0;
+    int64_t batch = 0;
+    int sms = 0;
+    int32_t *row_ptr = nullptr, *col = nullptr, *labels = nullptr, *rank = nullptr, *cls_size = nullptr,
+            *end_off = nullptr;
+    int64_t *piece_cnt = nullptr;
+    int *err = nullptr;
+    unsigned long long *stats = nullptr;   // [0] tested, [1] accepted, [2..] scratch counters
+    DevGraph dg() const {
+        DevGraph g;
+        g.n = n;
+        g.nnz = nnz;
+        g.row_ptr = row_ptr;
+        g.col = col;
+        g.labels = labels;
+        g.rank = rank;
+        g.piece_cnt = piece_cnt;
+        g.end_off = end_off;
+        return g;
+    }
+};
+
+struct fsm_result {
+    int k = 0;
+    std::vector<int32_t> labels;
+    std::vector<uint64_t> adj;
+    std::vector<int64_t> support, count;
+    std::map<std::string, int64_t> stats;
+};
+
+namespace {
+
+// Frequent patterns of one level and (optionally) its stored embeddings.
+struct LevelSet {
+    int L = 0;
+    int64_t P = 0;                      // frequent patterns
+    uint64_t *lab8 = nullptr, *adj8 = nullptr;
+    unsigned long long *clab = nullptr, *sigma = nullptr, *count = nullptr;
+    uint32_t *cadj = nullptr;
+    int32_t *fv = nullptr, *fpid = nullptr;
+    int64_t N = 0;                      // stored embeddings
+};
+
+struct RunStats {
+    int64_t tested = 0, accepted = 0, qps = 0, patterns = 0, live = 0, frontier_max = 0, levels = 0,
+            final_accepted = 0, launches = 0;
+    // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
+    double pass_ns[3] = {0, 0, 0};
+    int64_t pass_launches[3] = {0, 0, 0}, pass_bytes[3] = {0, 0, 0};
+};
+
+struct Miner {
+    fsm_graph *G;
+    cudaStream_t st;
+    Arena &mem;
+    int64_t t;
+    RunStats &rs;
+
+    int grid_for(int L, int pass) {
+        int bps = 0;
+        cudaError_t e = pass == PASS_COUNT ? occupancy_extend_count(L, &bps)
+                      : pass == PASS_DOMAIN ? occupancy_extend_domain(L, &bps)
+                                            : occupancy_extend_emit(L, &bps);
+        ck(e, "occupancy query");
+        if (bps < 1) bps = 1;
+        return G->sms * bps;
+    }
+
+    // Run one pass of the extension kernel over every batch of the frontier.
+    void run_pass(int pass, const LevelSet &in, ExtArgs A) {
+        const int L = in.L;
+        if (in.N == 0) return;
+        int64_t B = G->batch > 0 ? G->batch : std::max<int64_t>(1024, ((int64_t)1 << 24) / L);
+        B = std::min(B, in.N);
+        const int64_t maxu = B * L;
+        int64_t *cnt = mem.get<int64_t>(maxu);
+        int64_t *base = mem.get<int64_t>(maxu + 1);
+        void *tmp = mem.get<char>((int64_t)scan_temp_bytes(maxu) + 16);
+        unsigned long long *ctr = mem.get<unsigned long long>(1);
+        const int grid = grid_for(L, pass);
+        const int64_t warps = (int64_t)grid * 8;
+        const bool prof = G->profile != 0;
+        unsigned long long *bsum = prof ? mem.get<unsigned long long>(1) : nullptr;
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
+        for (int64_t e0 = 0; e0 < in.N; e0 += B) {
+            const int64_t ne = std::min(B, in.N - e0);
+            ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, e0, ne, L, cnt, st), "unit counts");
+            ck(launch_scan_i64(cnt, base, ne * L, tmp, st), "unit scan");
+            const int64_t total = d2h(base + ne * L, st);
+            if (total == 0) continue;
+            int64_t chunk = G->chunk;
+            if (chunk <= 0) {
+                chunk = 256;
+                while (chunk < 16384 && total / chunk > warps * 64) chunk <<= 1;
+            }
+            A.fv = in.fv;
+            A.fpid = in.fpid;
+            A.fN = in.N;
+            A.e0 = e0;
+            A.ne = ne;
+            A.unit_base = base;
+            A.total = total;
+            A.chunk = (int32_t)chunk;
+            A.nchunks = (total + chunk - 1) / chunk;
+            A.chunk_ctr = ctr;
+            ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
+            if (prof) {
+                ck(cudaMemsetAsync(bsum, 0, sizeof(unsigned long long), st), "memset");
+                ck(launch_unit_bytes(G->row_ptr, G->piece_cnt, in.fv, in.N, e0, ne, L, bsum, st), "unit bytes");
+                rs.pass_bytes[pass] += (int64_t)d2h(bsum, st);
+                cudaEvent_t a, b;
+                ck(cudaEventCreate(&a), "event");
+                ck(cudaEventCreate(&b), "event");
+                evs.emplace_back(a, b);
+                ck(cudaEventRecord(a, st), "event record");
+            }
+            cudaError_t e = pass == PASS_COUNT ? launch_extend_count(L, A, grid, st)
+                          : pass == PASS_DOMAIN ? launch_extend_domain(L, A, grid, st)
+                                                : launch_extend_emit(L, A, grid, st);
+            ck(e, "extension kernel");
+            if (prof) ck(cudaEventRecord(evs.back().second, st), "event record");
+            rs.launches += 1;
+            rs.pass_launches[pass] += 1;
+        }
+        if (prof) {
+            ck(cudaStreamSynchronize(st), "sync");
+            for (auto &ab : evs) {
+                float ms = 0.f;
+                ck(cudaEventElapsedTime(&ms, ab.first, ab.second), "event time");
+                rs.pass_ns[pass] += (double)ms * 1e6;
+                cudaEventDestroy(ab.first);
+                cudaEventDestroy(ab.second);
+            }
+            mem.release(bsum);
+        }
+        mem.release(cnt);
+        mem.release(base);
+        mem.release(tmp);
+        mem.release(ctr);
+    }
+
+    int err_word() { return d2h(G->err, st); }
+
+    // Extend `in` (size L) to size L+2.  piece_freq == nullptr at the size-3 level.
+    LevelSet extend(const LevelSet &in, const uint8_t *piece_freq, bool final) {
+        const int L = in.L, K = L + 2;
+        LevelSet out;
+        out.L = K;
+        ExtArgs A;
+        memset(&A, 0, sizeof(A));
+        A.g = G->dg();
+        A.mode = G->mode;
+        A.pat_adj = in.adj8;
+        A.piece_freq = piece_freq;
+        A.err = G->err;
+        // ---- pass 1: quick patterns and their embedding counts
+        int64_t cap = (int64_t)1 << 16;
+        unsigned long long *keys = nullptr, *qcount = nullptr, *used = nullptr;
+        for (;;) {
+            keys = mem.get<unsigned long long>(cap);
+            qcount = mem.get<unsigned long long>(cap);
+            used = mem.get<unsigned long long>(1);
+            ck(launch_fill_u64(keys, FSM_EMPTY_KEY, cap, st), "fill");
+            ck(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long) * cap, st), "memset");
+            ck(cudaMemsetAsync(used, 0, sizeof(unsigned long long), st), "memset");
+            ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
+            ck(cudaMemsetAsync(G->stats, 0, 2 * sizeof(unsigned long long), st), "memset");
+                        A.qp.keys = keys;
+            A.qp.count = qcount;
+            A.qp.mask = (uint64_t)cap - 1;
+            A.qp.used = used;
+            A.qp.max_used = (unsigned long long)(cap / 2);
+            A.stats = G->stats;
+            run_pass(PASS_COUNT, in, A);
+            const int ew = err_word();
+            if (ew & FSM_ERR_QP_OVERFLOW) {
+                mem.release(keys);
+                mem.release(qcount);
+                mem.release(used);
+                if (cap >= ((int64_t)1 << 31)) fail(FSM_EUNSUPPORTED, "more than 2^30 distinct quick patterns in one level");
+                cap <<= 2;
+                continue;
+            }
+            if (ew) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+            break;
+        }
+        unsigned long long st2[2];
+        ck(cudaMemcpyAsync(st2, G->stats, sizeof(st2), cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaStreamSynchronize(st), "sync");
+        rs.tested += (int64_t)st2[0];
+        rs.accepted += (int64_t)st2[1];
+        if (final) rs.final_accepted = (int64_t)st2[1];
+        // ---- distinct quick patterns -> canonical codes -> pattern ids
+        int64_t *slots = mem.get<int64_t>(cap);
+        unsigned long long *nq_d = mem.get<unsigned long long>(1);
+        ck(cudaMemsetAsync(nq_d, 0, sizeof(unsigned long long), st), "memset");
+        ck(launch_qp_compact(keys, cap, slots, nq_d, st), "compact");
+        const int64_t nq = (int64_t)d2h(nq_d, st);
+        rs.qps += nq;
+        int32_t *qpat = mem.get<int32_t>(cap);
+        uint32_t *qperm = mem.get<uint32_t>(cap);
+        int64_t M = 1;
+        while (M < nq) M <<= 1;
+        CodeRec *recs = mem.get<CodeRec>(M);
+        ck(launch_qp_canon(L, keys, slots, nq, in.lab8, in.adj8, recs, qperm, st), "canonicalise");
+        ck(launch_sort_codes(recs, nq, st), "sort codes");
+        int64_t *flag = mem.get<int64_t>(nq + 1);
+        int64_t *ids = mem.get<int64_t>(nq + 1);
+        void *stmp = mem.get<char>((int64_t)scan_temp_bytes(nq) + 16);
+        unsigned long long *plab = mem.get<unsigned long long>(nq);
+        uint32_t *padj = mem.get<uint32_t>(nq);
+        ck(launch_assign_patterns(recs, nq, slots, flag, ids, stmp, qpat, plab, padj, st), "assign patterns");
+        const int64_t np = nq > 0 ? d2h(ids + nq, st) : 0;
+        mem.release(recs);
+        // ---- orbits, counts, live patterns, domain bitmaps
+        uint64_t *orbit = mem.get<uint64_t>(np);
+        int32_t *minorb = mem.get<int32_t>(np);
+        unsigned long long *pcount = mem.get<unsigned long long>(np);
+        ck(cudaMemsetAsync(pcount, 0, sizeof(unsigned long long) * std::max<int64_t>(np, 1), st), "memset");
+        ck(launch_orbits(K, plab, padj, np, orbit, minorb, st), "orbits");
+        ck(launch_pattern_counts(slots, nq, qpat, qcount, pcount, st), "pattern counts");
+        uint8_t *live = mem.get<uint8_t>(np);
+        int64_t *words = mem.get<int64_t>(np * 8);
+        int64_t *woff = mem.get<int64_t>(np * 8 + 1);
+        int64_t *doff = mem.get<int64_t>(np * 8);
+        void *stmp2 = mem.get<char>((int64_t)scan_temp_bytes(np * 8) + 16);
+        ck(launch_domain_sizes(K, plab, orbit, minorb, pcount, np, t, G->cls_size, live, words, st), "domain sizes");
+        ck(launch_scan_i64(words, woff, np * 8, stmp2, st), "domain scan");
+        ck(launch_domain_offsets(words, woff, np * 8, doff, st), "domain offsets");
+        const int64_t nwords = d2h(woff + np * 8, st);
+        uint32_t *dom = mem.get<uint32_t>(nwords);
+        ck(cudaMemsetAsync(dom, 0, sizeof(uint32_t) * std::max<int64_t>(nwords, 1), st), "memset");
+        rs.patterns = np;
+        {
+            // live pattern count (for statistics)
+            std::vector<uint8_t> hl((size_t)np);
+            if (np) {
+                ck(cudaMemcpyAsync(hl.data(), live, (size_t)np, cudaMemcpyDeviceToHost, st), "copy");
+                ck(cudaStreamSynchronize(st), "sync");
+            }
+            rs.live = std::count(hl.begin(), hl.end(), (uint8_t)1);
+        }
+        // ---- pass 2: MNI domains (Definition 2)
+        A.qp.pattern = qpat;
+        A.qp.perm = qperm;
+        A.live = live;
+        A.orbit = orbit;
+        A.dom_off = doff;
+        A.dom = dom;
+        A.stats = nullptr;
+        if (rs.live > 0) run_pass(PASS_DOMAIN, in, A);
+        unsigned long long *sigma = mem.get<unsigned long long>(np);
+        ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
+        ck(launch_support(K, orbit, live, doff, words, dom, np, sigma, st), "support");
+        int64_t *fflag = mem.get<int64_t>(np + 1);
+        int64_t *fscan = mem.get<int64_t>(np + 1);
+        int32_t *newid = mem.get<int32_t>(np);
+        ck(launch_freq_flags(sigma, np, t, fflag, st), "frequent flags");
+        ck(launch_scan_i64(fflag, fscan, np, stmp2, st), "frequent scan");
+        ck(launch_new_ids(fflag, fscan, np, newid, st), "new ids");
+        const int64_t nf = d2h(fscan + np, st);
+                mem.release(dom);
+        // ---- frequent patterns of size K
+        out.P = nf;
+        out.lab8 = mem.get<uint64_t>(nf);
+        out.adj8 = mem.get<uint64_t>(nf);
+        out.clab = mem.get<unsigned long long>(nf);
+        out.cadj = mem.get<uint32_t>(nf);
+        out.sigma = mem.get<unsigned long long>(nf);
+        out.count = mem.get<unsigned long long>(nf);
+        ck(launch_gather_frequent(K, newid, np, plab, padj, sigma, pcount, out.clab, out.cadj, out.sigma,
+                                  out.count, out.lab8, out.adj8, st), "gather");
+        if (!final && nf > 0) {
+            // ---- pass 3: store the frequent size-K embeddings in canonical order
+            unsigned long long *sum = mem.get<unsigned long long>(1);
+            ck(cudaMemsetAsync(sum, 0, sizeof(unsigned long long), st), "memset");
+            ck(launch_sum_frequent(newid, pcount, np, sum, st), "sum");
+            const int64_t N2 = (int64_t)d2h(sum, st);
+            out.N = N2;
+            out.fv = mem.get<int32_t>(N2 * K);
+            out.fpid = mem.get<int32_t>(N2);
+            unsigned long long *cursor = mem.get<unsigned long long>(1);
+            ck(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st), "memset");
+            A.newid = newid;
+            A.out_v = out.fv;
+            A.out_pid = out.fpid;
+            A.out_N = N2;
+            A.out_cursor = cursor;
+            run_pass(PASS_EMIT, in, A);
+            const int64_t wrote = (int64_t)d2h(cursor, st);
+            if (wrote != N2) fail(FSM_ECUDA, "frontier emission wrote " + std::to_string(wrote) + " of " + std::to_string(N2));
+            if (G->profile) rs.pass_bytes[PASS_EMIT] += N2 * 4 * (K + 1);
+            rs.frontier_max = std::max(rs.frontier_max, N2);
+            mem.release(sum);
+            mem.release(cursor);
+        }
+        const int ew = err_word();
+        if (ew) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+        for (void *p : std::initializer_list<void *>{keys, qcount, used, slots, nq_d, qpat, qperm, flag, ids, stmp, plab,
+                                                     padj, orbit, minorb, pcount, live, words, woff, doff, stmp2, sigma,
+                                                     fflag, fscan, newid})
+            mem.release(p);
+        rs.levels += 1;
+        return out;
+    }
+
+    LevelSet level1(bool with_frontier) {
+        LevelSet s;
+        s.L = 1;
+        const int NL = G->NL;
+        int32_t *lnew = mem.get<int32_t>(NL);
+        s.lab8 = mem.get<uint64_t>(NL);
+        s.adj8 = mem.get<uint64_t>(NL);
+        s.clab = mem.get<unsigned long long>(NL);
+        s.cadj = mem.get<uint32_t>(NL);
+        s.sigma = mem.get<unsigned long long>(NL);
+        s.count = mem.get<unsigned long long>(NL);
+        unsigned long long *nf = mem.get<unsigned long long>(1);
+        ck(launch_level1_tables(NL, G->cls_size, t, lnew, s.lab8, s.adj8, s.clab, s.cadj, s.sigma, s.count, nf, st),
+           "level 1");
+        s.P = (int64_t)d2h(nf, st);
+                if (with_frontier) {
+            int64_t *flag = mem.get<int64_t>(G->n);
+            int64_t *scanned = mem.get<int64_t>(G->n + 1);
+            void *tmp = mem.get<char>((int64_t)scan_temp_bytes(G->n) + 16);
+            // size: number of vertices with a frequent label
+            s.fv = mem.get<int32_t>(G->n);
+            s.fpid = mem.get<int32_t>(G->n);
+            ck(launch_level1_frontier(G->dg(), lnew, flag, scanned, tmp, s.fv, s.fpid, st), "level 1 frontier");
+            s.N = d2h(scanned + G->n, st);
+                        mem.release(flag);
+            mem.release(scanned);
+            mem.release(tmp);
+        }
+        mem.release(lnew);
+        return s;
+    }
+
+    LevelSet level2(bool with_frontier) {
+        LevelSet s;
+        s.L = 2;
+        const int NL = G->NL;
+        const int64_t NP = (int64_t)NL * NL;
+        int64_t *poff = mem.get<int64_t>(NP * 2);
+        int64_t *tw = mem.get<int64_t>(1);
+        ck(launch_level2_offsets(NL, G->cls_size, poff, tw, st), "level 2 offsets");
+        const int64_t words = d2h(tw, st);
+        uint32_t *dom = mem.get<uint32_t>(words);
+        unsigned long long *pc = mem.get<unsigned long long>(NP);
+        unsigned long long *ps = mem.get<unsigned long long>(NP);
+        ck(cudaMemsetAsync(dom, 0, sizeof(uint32_t) * std::max<int64_t>(words, 1), st), "memset");
+        ck(cudaMemsetAsync(pc, 0, sizeof(unsigned long long) * NP, st), "memset");
+        ck(launch_level2_domains(G->dg(), NL, poff, dom, pc, st), "level 2 domains");
+        ck(launch_level2_support(NL, G->cls_size, poff, dom, ps, st), "level 2 support");
+        int32_t *pnew = mem.get<int32_t>(NP);
+        s.lab8 = mem.get<uint64_t>(NP);
+        s.adj8 = mem.get<uint64_t>(NP);
+        s.clab = mem.get<unsigned long long>(NP);
+        s.cadj = mem.get<uint32_t>(NP);
+        s.sigma = mem.get<unsigned long long>(NP);
+        s.count = mem.get<unsigned long long>(NP);
+        unsigned long long *nf = mem.get<unsigned long long>(1);
+        ck(launch_level2_tables(NL, ps, pc, t, pnew, s.lab8, s.adj8, s.clab, s.cadj, s.sigma, s.count, nf, st),
+           "level 2 tables");
+        s.P = (int64_t)d2h(nf, st);
+                if (with_frontier && s.P > 0) {
+            int64_t *flag = mem.get<int64_t>(G->n);
+            int64_t *scanned = mem.get<int64_t>(G->n + 1);
+            void *tmp = mem.get<char>((int64_t)scan_temp_bytes(G->n) + 16);
+            // stored edges = embeddings of the frequent pairs
+            unsigned long long *sum = mem.get<unsigned long long>(1);
+            ck(cudaMemsetAsync(sum, 0, sizeof(unsigned long long), st), "memset");
+            ck(launch_sum_frequent(pnew, pc, NP, sum, st), "sum");
+            s.N = (int64_t)d2h(sum, st);
+            mem.release(sum);
+            s.fv = mem.get<int32_t>(s.N * 2);
+            s.fpid = mem.get<int32_t>(s.N);
+            ck(launch_level2_frontier(G->dg(), NL, pnew, flag, scanned, tmp, s.fv, s.N, s.fpid, st), "level 2 frontier");
+            const int64_t wrote = d2h(scanned + G->n, st);
+            if (wrote != s.N) fail(FSM_ECUDA, "level 2 frontier size mismatch");
+                        mem.release(flag);
+            mem.release(scanned);
+            mem.release(tmp);
+        }
+        mem.release(poff);
+        mem.release(tw);
+        mem.release(dom);
+        mem.release(pc);
+        mem.release(ps);
+        mem.release(pnew);
+        return s;
+    }
+};
+
+void fill_result(fsm_result *r, const LevelSet &s, int k, cudaStream_t st) {
+    const int64_t P = s.P;
+    std::vector<unsigned long long> lab((size_t)P), sig((size_t)P), cnt((size_t)P);
+    std::vector<uint32_t> adj((size_t)P);
+    if (P) {
+        ck(cudaMemcpyAsync(lab.data(), s.clab, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(adj.data(), s.cadj, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(sig.data(), s.sigma, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(cnt.data(), s.count, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaStreamSynchronize(st), "sync");
+    }
+    r->k = k;
+    r->labels.resize((size_t)P * k);
+    r->adj.resize((size_t)P);
+    r->support.resize((size_t)P);
+    r->count.resize((size_t)P);
+    const int np = k * (k - 1) / 2;
+    for (int64_t p = 0; p < P; ++p) {
+        for (int c = 0; c < k; ++c) r->labels[(size_t)p * k + c] = (int32_t)((lab[p] >> (8 * (7 - c))) & 0xff);
+        uint64_t bits = 0;
+        int q = 0;
+        for (int i = 0; i < k; ++i)
+            for (int j = i + 1; j < k; ++j, ++q)
+                if ((adj[p] >> (np - 1 - q)) & 1u) bits |= 1ull << (i * k + j);
+        r->adj[p] = bits;
+        r->support[p] = (int64_t)sig[p];
+        r->count[p] = (int64_t)cnt[p];
+    }
+}
+
+} // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+const char *fsm_last_error(void) { return g_last_error.c_str(); }
+
+int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *labels, int32_t n,
+                   int32_t num_labels, fsm_graph **out) {
+    fsm_graph *g = nullptr;
+    try {
+        if (!out) fail(FSM_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!row_ptr || !labels || n < 1) fail(FSM_EINVAL, "row_ptr/labels must be non-NULL and n >= 1");
+        if (num_labels < 1 || num_labels > 64) fail(FSM_EINVAL, "num_labels must be in [1, 64]");
+        if (row_ptr[0] != 0) fail(FSM_EINVAL, "row_ptr[0] must be 0");
+        for (int32_t v = 0; v < n; ++v)
+            if (row_ptr[v + 1] < row_ptr[v]) fail(FSM_EINVAL, "row_ptr must be nondecreasing");
+        const int64_t nnz = row_ptr[n];
+        if (nnz > 0 && !col) fail(FSM_EINVAL, "col is NULL");
+        if (nnz >= ((int64_t)1 << 31) - 1) fail(FSM_EUNSUPPORTED, "nnz must be below 2^31 - 1");
+        g = new fsm_graph();
+        ck(cudaGetDevice(&g->device), "cudaGetDevice");
+        keep_pool(g->device);
+        ck(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device), "device attribute");
+        ck(cudaStreamCreateWithFlags(&g->own_stream, cudaStreamNonBlocking), "stream create");
+        g->stream = g->own_stream;
+        g->n = n;
+        g->NL = num_labels;
+        g->nnz = nnz;
+        cudaStream_t st = g->stream;
+        auto dalloc = [&](void **p, size_t bytes) { ck(cudaMallocAsync(p, std::max<size_t>(bytes, 16), st), "device allocation"); };
+        dalloc((void **)&g->row_ptr, sizeof(int32_t) * (n + 1));
+        dalloc((void **)&g->col, sizeof(int32_t) * nnz);
+        dalloc((void **)&g->labels, sizeof(int32_t) * n);
+        dalloc((void **)&g->rank, sizeof(int32_t) * n);
+        dalloc((void **)&g->cls_size, sizeof(int32_t) * 64);
+        dalloc((void **)&g->end_off, sizeof(int32_t) * nnz);
+        dalloc((void **)&g->piece_cnt, sizeof(int64_t) * n);
+        dalloc((void **)&g->err, sizeof(int) * 4);
+        dalloc((void **)&g->stats, sizeof(unsigned long long) * 8);
+        ck(cudaMemcpyAsync(g->row_ptr, row_ptr, sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st), "copy");
+        if (nnz) ck(cudaMemcpyAsync(g->col, col, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice, st), "copy");
+        ck(cudaMemcpyAsync(g->labels, labels, sizeof(int32_t) * n, cudaMemcpyHostToDevice, st), "copy");
+        ck(cudaMemsetAsync(g->err, 0, sizeof(int) * 4, st), "memset");
+        ck(cudaMemsetAsync(g->cls_size, 0, sizeof(int32_t) * 64, st), "memset");
+        ck(launch_validate(g->dg(), num_labels, g->err, st), "validate");
+        const int ew = d2h(g->err, st);
+        if (ew) fail(FSM_EINVAL, "malformed CSR: rows must be sorted, symmetric, without self-loops or duplicates, labels in range");
+        ck(launch_prepare(g->dg(), g->piece_cnt, g->end_off, g->rank, g->cls_size, st), "prepare");
+        ck(cudaStreamSynchronize(st), "sync");
+        *out = g;
+        return FSM_OK;
+    } catch (const FsmError &e) {
+        if (g) fsm_free_graph(g);
+        return set_error(e);
+    }
+}
+
+int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
+    try {
+        if (!g || !key) fail(FSM_EINVAL, "graph and key must be non-NULL");
+        std::string k(key);
+        if (k == "mode") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "mode must be 0 (edge-induced) or 1 (vertex-induced)");
+            g->mode = (int)value;
+        } else if (k == "stream") {
+            g->stream = value ? (cudaStream_t)(intptr_t)value : g->own_stream;
+        } else if (k == "profile") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "profile must be 0 or 1");
+            g->profile = (int)value;
+        } else if (k == "launch") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "launch must be 0 or 1");
+            g->launch = (int)value;
+        } else if (k == "chunk") {
+            if (value != 0 && (value < 32 || value > 65536 || (value & (value - 1)))) fail(FSM_EINVAL, "chunk must be 0 or a power of two in [32, 65536]");
+            g->chunk = (int32_t)value;
+        } else if (k == "batch") {
+            if (value != 0 && value < 1024) fail(FSM_EINVAL, "batch must be 0 or >= 1024");
+            g->batch = value;
+        } else {
+            fail(FSM_EINVAL, "unknown option '" + k + "'");
+        }
+        return FSM_OK;
+    } catch (const FsmError &e) {
+        return set_error(e);
+    }
+}
+
+int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, fsm_result **out) {
+    fsm_result *r = nullptr;
+    try {
+        if (!out) fail(FSM_EINVAL, "out is NULL");
+        *out = nullptr;
+        if (!g) fail(FSM_EINVAL, "graph is NULL");
+        if (k < 1 || k > FSM_MAXK) fail(FSM_EINVAL, "k must be in [1, 8]");
+        if (min_support < 1) fail(FSM_EINVAL, "min_support must be >= 1");
+        if (!(sample_rate > 0.0 && sample_rate <= 1.0)) fail(FSM_EINVAL, "sample_rate must be in (0, 1]");
+        if (sample_rate < 1.0) fail(FSM_EUNSUPPORTED, "sampled mining is not available in this build");
+        ck(cudaSetDevice(g->device), "cudaSetDevice");
+        cudaStream_t st = g->stream;
+        cudaEvent_t ev0, ev1, evf;
+        ck(cudaEventCreate(&ev0), "event");
+        ck(cudaEventCreate(&ev1), "event");
+        ck(cudaEventCreate(&evf), "event");
+        const int64_t l0 = launches_so_far();
+        ck(cudaEventRecord(ev0, st), "event record");
+        RunStats rs;
+        r = new fsm_result();
+        {
+            Arena mem(st);
+            Miner m{g, st, mem, min_support, rs};
+            LevelSet res;
+            if (k == 1) {
+                res = m.level1(false);
+                ck(cudaEventRecord(evf, st), "event record");
+            } else if (k == 2) {
+                res = m.level2(false);
+                ck(cudaEventRecord(evf, st), "event record");
+            } else {
+                LevelSet s1 = m.level1(true);
+                const bool odd = (k & 1) != 0;
+                if (k == 3) ck(cudaEventRecord(evf, st), "event record");
+                LevelSet s3 = m.extend(s1, nullptr, k == 3 || !odd);
+                if (k == 3) {
+                    res = s3;
+                } else {
+                    uint8_t *pf = mem.get<uint8_t>(FSM_PIECE_SPACE);
+                    ck(cudaMemsetAsync(pf, 0, FSM_PIECE_SPACE, st), "memset");
+                    ck(launch_piece_table(s3.clab, s3.cadj, s3.P, pf, st), "piece table");
+                    LevelSet cur = odd ? s3 : m.level2(true);
+                    while (cur.L + 2 <= k) {
+                        const bool fin = cur.L + 2 == k;
+                        if (fin) ck(cudaEventRecord(evf, st), "event record");
+                        cur = m.extend(cur, pf, fin);
+                    }
+                    res = cur;
+                }
+            }
+            ck(cudaEventRecord(ev1, st), "event record");
+            fill_result(r, res, k, st);
+        }
+        ck(cudaStreamSynchronize(st), "sync");
+        float ms = 0.f, fms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventElapsedTime(&fms, evf, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        cudaEventDestroy(evf);
+        r->stats["k"] = k;
+        r->stats["levels"] = rs.levels;
+        r->stats["candidates"] = rs.tested;
+        r->stats["embeddings"] = rs.accepted;
+        r->stats["final_embeddings"] = rs.final_accepted;
+        r->stats["quick_patterns"] = rs.qps;
+        r->stats["patterns"] = rs.patterns;
+        r->stats["live_patterns"] = rs.live;
+        r->stats["frontier_max"] = rs.frontier_max;
+        r->stats["kernel_launches"] = (launches_so_far() - l0) + rs.launches;
+        r->stats["time_ns"] = (int64_t)((double)ms * 1e6);
+        r->stats["final_level_ns"] = (int64_t)((double)fms * 1e6);
+        const char *pn[3] = {"count", "domain", "emit"};
+        for (int p = 0; p < 3; ++p) {
+            r->stats[std::string(pn[p]) + "_ns"] = (int64_t)rs.pass_ns[p];
+            r->stats[std::string(pn[p]) + "_launches"] = rs.pass_launches[p];
+            r->stats[std::string(pn[p]) + "_bytes"] = rs.pass_bytes[p];
+        }
+        *out = r;
+        return FSM_OK;
+    } catch (const FsmError &e) {
+        delete r;
+        return set_error(e);
+    }
+}
+
+int64_t fsm_result_count(const fsm_result *r) {
+    if (!r) { g_last_error = "result is NULL"; return FSM_EINVAL; }
+    return (int64_t)r->support.size();
+}
+
+int fsm_result_get(const fsm_result *r, int64_t i, int32_t *labels_k, uint64_t *adj_bits, int64_t *support) {
+    if (!r || i < 0 || i >= (int64_t)r->support.size()) { g_last_error = "bad result or index"; return FSM_EINVAL; }
+    if (labels_k) std::memcpy(labels_k, r->labels.data() + (size_t)i * r->k, sizeof(int32_t) * r->k);
+    if (adj_bits) *adj_bits = r->adj[(size_t)i];
+    if (support) *support = r->support[(size_t)i];
+    return FSM_OK;
+}
+
+int fsm_result_embeddings(const fsm_result *r, int64_t i, int64_t *count) {
+    if (!r || !count || i < 0 || i >= (int64_t)r->count.size()) { g_last_error = "bad result or index"; return FSM_EINVAL; }
+    *count = r->count[(size_t)i];
+    return FSM_OK;
+}
+
+int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, int64_t *support, int64_t *embeddings) {
+    if (!r) { g_last_error = "result is NULL"; return FSM_EINVAL; }
+    const size_t P = r->support.size();
+    if (labels && P) std::memcpy(labels, r->labels.data(), sizeof(int32_t) * P * r->k);
+    if (adj_bits && P) std::memcpy(adj_bits, r->adj.data(), sizeof(uint64_t) * P);
+    if (support && P) std::memcpy(support, r->support.data(), sizeof(int64_t) * P);
+    if (embeddings && P) std::memcpy(embeddings, r->count.data(), sizeof(int64_t) * P);
+    return FSM_OK;
+}
+
+int fsm_result_stat(const fsm_result *r, const char *key, int64_t *value) {
+    if (!r || !key || !value) { g_last_error = "NULL argument"; return FSM_EINVAL; }
+    auto it = r->stats.find(key);
+    if (it == r->stats.end()) { g_last_error = std::string("unknown stat '") + key + "'"; return FSM_EINVAL; }
+    *value = it->second;
+    return FSM_OK;
+}
+
+void fsm_free_result(fsm_result *r) { delete r; }
+
+void fsm_free_graph(fsm_graph *g) {
+    if (!g) return;
+    cudaStream_t st = g->stream ? g->stream : g->own_stream;
+    void *ps[] = {g->row_ptr, g->col, g->labels, g->rank, g->cls_size, g->end_off, g->piece_cnt, g->err, g->stats};
+    for (void *p : ps)
+        if (p) cudaFreeAsync(p, st);
+    if (st) cudaStreamSynchronize(st);
+    if (g->own_stream) cudaStreamDestroy(g->own_stream);
+    delete g;
+}
+
+int fsm_debug_dissect(int32_t k, const int32_t *ids, const uint32_t *adj, uint32_t *l_mask, int32_t *join,
+                      int32_t *used_fallback) {
+    if (k < 3 || k > FSM_MAXK || !ids || !adj || !l_mask || !join || !used_fallback) {
+        g_last_error = "k must be in [3, 8] and pointers non-NULL";
+        return FSM_EINVAL;
+    }
+    const uint32_t all = (1u << k) - 1u;
+    for (int i = 0; i < k; ++i) {
+        if ((adj[i] & ~all) || (adj[i] >> i & 1u)) { g_last_error = "adjacency out of range or self-loop"; return FSM_EINVAL; }
+        for (int j = 0; j < k; ++j)
+            if (((adj[i] >> j) & 1u) != ((adj[j] >> i) & 1u)) { g_last_error = "adjacency not symmetric"; return FSM_EINVAL; }
+        for (int j = i + 1; j < k; ++j)
+            if (ids[i] == ids[j]) { g_last_error = "ids not distinct"; return FSM_EINVAL; }
+    }
+    if (!mask_connected(all, adj, k)) { g_last_error = "graph not connected"; return FSM_EINVAL; }
+    uint32_t lm = 0;
+    int jn = -1;
+    const bool greedy = dissect3(k, ids, adj, lm, jn);
+    if (lm == 0) { g_last_error = "no dissection exists"; return FSM_EINVAL; }
+    *l_mask = lm;
+    *join = jn;
+    *used_fallback = greedy ? 0 : 1;
+    return FSM_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,377 @@
+// fsm_extend.cuh -- the two-vertex extension kernel (one level l -> l+2).
+//
+// Work: every (frontier embedding s, key position i) "unit" owns the pieces keyed at v = s[i]:
+//   centre pieces  {v, a, b}, a < b both in N(v): the wedge a-v-b, and the triangle if a ~ b;
+//   end pieces     {v, a, b}, a in N(v), b in N(a) \ {v}: the wedge v-a-b centred at a.
+// Together these are every connected size-3 subgraph containing v (edge-induced); in
+// vertex-induced mode a closed triple yields only its triangle.  Joining s with a piece t on v
+// is Section 4.1's two-vertex exploration, equivalent to the hash join of Section 4.2 on the
+// column holding v; the piece list is generated from the CSR instead of being stored.
+//
+// Per join: require s and t to share only v (Algorithm 1's first test); read the cross
+// adjacencies between s \ {v} and t \ {v}; for each subset of them (edge-induced) or all of them
+// (vertex-induced) prune when a joining-point triple {v, s[p], t[q]} is connected with an
+// infrequent size-3 pattern (Section 4.5), keep the join only when smallest-vertex-first
+// dissection returns exactly (t, s) (Algorithm 1), and form its index-based quick pattern key
+// (Section 4.4).  The pass template parameter says what an accepted join does:
+//   PASS_COUNT   insert the key into the quick-pattern table and count it;
+//   PASS_DOMAIN  set the MNI domain bits of its pattern's orbits (Definition 2);
+//   PASS_EMIT    write it, permuted into canonical order, to the next frontier.
+//
+// Scheduling: the pieces of a batch of units form one index space [0, total) (exclusive prefix
+// `unit_base`); warps take fixed-size chunks of it from an atomic counter, so hub vertices
+// with millions of pieces are split across many warps and light units share a warp.
+#pragma once
+#include "fsm_device.cuh"
+
+namespace fsm {
+
+enum { PASS_COUNT = 0, PASS_DOMAIN = 1, PASS_EMIT = 2 };
+
+struct QPTab {
+    unsigned long long *keys;      // [cap], FSM_EMPTY_KEY when free
+    unsigned long long *count;     // [cap] accepted joins per key
+    int32_t *pattern;              // [cap] pattern id of the key (after canonicalisation)
+    uint32_t *perm;                // [cap] local vertex h -> canonical position, 3 bits each
+    uint64_t mask;                 // cap - 1 (cap a power of two)
+    unsigned long long *used;      // occupied slots
+    unsigned long long max_used;   // overflow threshold (load factor 1/2)
+};
+
+struct ExtArgs {
+    DevGraph g;
+    int mode;                      // 0 edge-induced, 1 vertex-induced
+    // frontier batch: embeddings [e0, e0 + ne) of an SoA array with stride fN
+    const int32_t *fv;
+    const int32_t *fpid;
+    int64_t fN, e0, ne;
+    const int64_t *unit_base;      // [ne*L + 1] exclusive prefix of pieces per unit
+    int64_t total;                 // pieces in this batch
+    int64_t nchunks;
+    int32_t chunk;                 // pieces per chunk
+    unsigned long long *chunk_ctr;
+    // size-l pattern table (frequent patterns of the level being extended)
+    const uint64_t *pat_adj;       // [P] 8 adjacency rows (one byte each) over canonical positions
+    // frequent size-3 patterns, by piece index; NULL at level 1 (nothing is known yet)
+    const uint8_t *piece_freq;
+    QPTab qp;
+    // domains (PASS_DOMAIN)
+    const uint8_t *live;           // [P'] pattern has domains
+    const uint64_t *orbit;         // [P'] 8 bytes: orbit representative per canonical position
+    const int64_t *dom_off;        // [P'*8] word offset per orbit representative
+    uint32_t *dom;
+    // emission (PASS_EMIT)
+    const int32_t *newid;          // [P'] id among frequent patterns, -1 otherwise
+    int32_t *out_v;                // SoA [K][out_N]
+    int32_t *out_pid;
+    int64_t out_N;
+    unsigned long long *out_cursor;
+    unsigned long long *stats;     // [0] joins tested, [1] joins accepted
+    int *err;
+};
+
+__device__ __forceinline__ int64_t last_le(const int64_t *base, int64_t lo, int64_t hi, int64_t x) {
+    // largest u in [lo, hi] with base[u] <= x (base[lo] <= x assumed)
+    while (lo < hi) {
+        int64_t mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t qp_insert(const QPTab &t, uint64_t key, int *err) {
+    uint64_t h = mix64(key) & t.mask;
+    for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+        unsigned long long cur = __ldcg(t.keys + h);
+        if (cur == key) return (int64_t)h;
+        if (cur == FSM_EMPTY_KEY) {
+            unsigned long long old = atomicCAS(t.keys + h, FSM_EMPTY_KEY, key);
+            if (old == FSM_EMPTY_KEY) {
+                unsigned long long u = atomicAdd(t.used, 1ull);
+                if (u >= t.max_used) atomicOr(err, FSM_ERR_QP_OVERFLOW);
+                return (int64_t)h;
+            }
+            if (old == key) return (int64_t)h;
+        }
+        h = (h + 1) & t.mask;
+    }
+    atomicOr(err, FSM_ERR_QP_OVERFLOW);
+    return -1;
+}
+
+__device__ __forceinline__ int64_t qp_find(const QPTab &t, uint64_t key) {
+    uint64_t h = mix64(key) & t.mask;
+    for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+        unsigned long long cur = __ldg(t.keys + h);
+        if (cur == key) return (int64_t)h;
+        if (cur == FSM_EMPTY_KEY) return -1;
+        h = (h + 1) & t.mask;
+    }
+    return -1;
+}
+
+template <int L>
+__device__ __forceinline__ bool in_s(const int32_t (&S)[L], int32_t x) {
+    bool r = false;
+#pragma unroll
+    for (int p = 0; p < L; ++p) r |= (S[p] == x);
+    return r;
+}
+
+struct Tally { unsigned long long tested, accepted; };
+
+// One accepted join: act according to PASS.
+template <int L, int PASS>
+__device__ __forceinline__ void accept(const ExtArgs &A, uint64_t key, const int32_t (&gid)[L + 2]) {
+    constexpr int K = L + 2;
+    if (PASS == PASS_COUNT) {
+        const unsigned act = __activemask();
+        const unsigned grp = __match_any_sync(act, key);
+        const int lane = threadIdx.x & 31;
+        if (lane == __ffs(grp) - 1) {
+            int64_t slot = qp_insert(A.qp, key, A.err);
+            if (slot >= 0) atomicAdd(A.qp.count + slot, (unsigned long long)__popc(grp));
+        }
+        return;
+    }
+    int64_t slot = qp_find(A.qp, key);
+    if (slot < 0) { atomicOr(A.err, FSM_ERR_QP_MISSING); return; }
+    const int32_t P = __ldg(A.qp.pattern + slot);
+    const uint32_t perm = __ldg(A.qp.perm + slot);
+    if (PASS == PASS_DOMAIN) {
+        if (!__ldg(A.live + P)) return;
+        const uint64_t orb = __ldg(A.orbit + P);
+#pragma unroll
+        for (int h = 0; h < K; ++h) {
+            const int c = (perm >> (3 * h)) & 7;
+            const int o = (int)(orb >> (8 * c)) & 0xff;
+            const int64_t off = __ldg(A.dom_off + (int64_t)P * 8 + o);
+            const int32_t r = __ldg(A.g.rank + gid[h]);
+            uint32_t *w = A.dom + off + (r >> 5);
+            const uint32_t bit = 1u << (r & 31);
+            if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+        }
+    } else {  // PASS_EMIT
+        const int32_t nid = __ldg(A.newid + P);
+        if (nid < 0) return;
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(act) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(A.out_cursor, (unsigned long long)__popc(act));
+        base = __shfl_sync(act, base, leader);
+        const int64_t pos = (int64_t)base + __popc(act & ((1u << lane) - 1u));
+        if (pos >= A.out_N) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
+#pragma unroll
+        for (int h = 0; h < K; ++h) {
+            const int c = (perm >> (3 * h)) & 7;
+            A.out_v[(int64_t)c * A.out_N + pos] = gid[h];
+        }
+        A.out_pid[pos] = nid;
+    }
+}
+
+// Join s (vertices S, pattern pid, key position i) with one piece.  Piece vertices pv[0..2]
+// are in the piece's own order, pl their labels; shape is PIECE_WEDGE (centre pv[0]) or
+// PIECE_TRI.
+template <int L, int PASS>
+__device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
+                                           uint64_t srows, int32_t pid, int i, int shape,
+                                           const int32_t (&pv)[3], const int (&pl)[3], Tally &tl) {
+    constexpr int K = L + 2;
+    const uint32_t pidx = piece_index(shape, pl[0], pl[1], pl[2]);
+    if (A.piece_freq && !__ldg(A.piece_freq + pidx)) return;
+    const int32_t v = S[i];
+    const int jpos = pv[0] == v ? 0 : (pv[1] == v ? 1 : 2);
+    const int q0 = jpos == 0 ? 1 : 0;
+    const int q1 = jpos == 2 ? 1 : 2;
+    const int32_t x0 = pv[q0], x1 = pv[q1];
+    const int lx0 = pl[q0], lx1 = pl[q1];
+    uint32_t tj0, tj1, txx;
+    piece_join_edges(shape, jpos, tj0, tj1, txx);
+
+    // cross adjacency between s \ {v} and {x0, x1}
+    uint32_t avail = 0;
+#pragma unroll
+    for (int p = 0; p < L; ++p) {
+        if (p == i) continue;
+        const int pp = p < i ? p : p - 1;
+        if (is_adj(A.g, S[p], x0)) avail |= 1u << (2 * pp);
+        if (is_adj(A.g, S[p], x1)) avail |= 1u << (2 * pp + 1);
+    }
+    const uint32_t srow_i = (uint32_t)(srows >> (8 * i)) & 0xffu;
+
+    int32_t gid[K];
+#pragma unroll
+    for (int h = 0; h < L; ++h) gid[h] = S[h];
+    gid[L] = x0;
+    gid[L + 1] = x1;
+
+    uint32_t sub = avail;
+    for (;;) {
+        ++tl.tested;
+        bool keep = true;
+        if (L >= 2 && A.piece_freq) {
+            // joining-point pruning: every connected triple {v, s[p], t[q]} must be frequent
+#pragma unroll
+            for (int p = 0; p < L; ++p) {
+                if (p == i) continue;
+                const int pp = p < i ? p : p - 1;
+                const uint32_t e1 = (srow_i >> p) & 1u;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const uint32_t e2 = q ? tj1 : tj0;
+                    const uint32_t e3 = (sub >> (2 * pp + q)) & 1u;
+                    if (e1 + e2 + e3 < 2) continue;
+                    const int lx = q ? lx1 : lx0;
+                    uint32_t idx;
+                    if (e1 && e2 && e3) idx = tri_index(SL[i], SL[p], lx);
+                    else if (e1 && e2) idx = wedge_index(SL[i], SL[p], lx);
+                    else if (e1 && e3) idx = wedge_index(SL[p], SL[i], lx);
+                    else idx = wedge_index(lx, SL[i], SL[p]);
+                    if (!__ldg(A.piece_freq + idx)) keep = false;
+                }
+            }
+        }
+        if (keep && L >= 2) {
+            // smallest-vertex-first dissection must return exactly (t, s)
+            uint32_t adjK[K];
+            join_graph(L, srows, i, tj0, tj1, txx, sub, adjK);
+            uint32_t lm = 0;
+            int jn = -1;
+            dissect3(K, gid, adjK, lm, jn);
+            keep = (lm == ((1u << i) | (1u << L) | (1u << (L + 1)))) && jn == i;
+        }
+        if (keep) {
+            ++tl.accepted;
+            accept<L, PASS>(A, make_key((uint32_t)pid, pidx, i, jpos, sub), gid);
+        }
+        if (A.mode == 1 || sub == 0) break;
+        sub = (sub - 1) & avail;
+    }
+}
+
+template <int L, int PASS>
+__device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
+                                         uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl) {
+    const DevGraph &g = A.g;
+    const int32_t v = S[i];
+    const int32_t rp = __ldg(g.row_ptr + v);
+    const int32_t d = __ldg(g.row_ptr + v + 1) - rp;
+    const int64_t nc = (int64_t)d * (d - 1) / 2;
+    int32_t pv[3];
+    int pl[3];
+    if (lq < nc) {
+        // centre pair (x < y) with lq = y(y-1)/2 + x
+        int32_t y = (int32_t)((1.0f + sqrtf(1.0f + 8.0f * (float)lq)) * 0.5f);
+        while ((int64_t)y * (y - 1) / 2 > lq) --y;
+        while ((int64_t)(y + 1) * y / 2 <= lq) ++y;
+        const int32_t x = (int32_t)(lq - (int64_t)y * (y - 1) / 2);
+        const int32_t a = __ldg(g.col + rp + x), b = __ldg(g.col + rp + y);
+        if (L == 1 && a < v) return;                 // size-3 subgraphs keyed at their smallest vertex
+        if (in_s<L>(S, a) || in_s<L>(S, b)) return;
+        const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
+        const bool tri = is_adj(g, a, b);
+        if (A.mode == 0 || !tri) {
+            pv[0] = v; pl[0] = SL[i];
+            if (lab_id_less(la, a, lb, b)) { pv[1] = a; pl[1] = la; pv[2] = b; pl[2] = lb; }
+            else { pv[1] = b; pl[1] = lb; pv[2] = a; pl[2] = la; }
+            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl);
+        }
+        if (tri) {
+            int32_t t0 = v, t1 = a, t2 = b;
+            int m0 = SL[i], m1 = la, m2 = lb, tl_;
+            int32_t tv;
+            if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
+            if (lab_id_less(m2, t2, m1, t1)) { tv = t1; t1 = t2; t2 = tv; tl_ = m1; m1 = m2; m2 = tl_; }
+            if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
+            pv[0] = t0; pv[1] = t1; pv[2] = t2;
+            pl[0] = m0; pl[1] = m1; pl[2] = m2;
+            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_TRI, pv, pl, tl);
+        }
+    } else {
+        const int64_t lq2 = lq - nc;
+        int32_t lo = 0, hi = d - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if ((int64_t)__ldg(g.end_off + rp + mid) <= lq2) lo = mid; else hi = mid - 1;
+        }
+        const int32_t a = __ldg(g.col + rp + lo);
+        const int32_t b = __ldg(g.col + __ldg(g.row_ptr + a) + (int32_t)(lq2 - __ldg(g.end_off + rp + lo)));
+        if (b == v) return;
+        if (L == 1 && (a < v || b < v)) return;
+        if (in_s<L>(S, a) || in_s<L>(S, b)) return;
+        if (A.mode == 1 && is_adj(g, v, b)) return;  // the induced triple is the triangle (centre branch)
+        const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
+        pv[0] = a; pl[0] = la;
+        if (lab_id_less(SL[i], v, lb, b)) { pv[1] = v; pl[1] = SL[i]; pv[2] = b; pl[2] = lb; }
+        else { pv[1] = b; pl[1] = lb; pv[2] = v; pl[2] = SL[i]; }
+        join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl);
+    }
+}
+
+template <int L, int PASS>
+__global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nunits = A.ne * L;
+    Tally tl{0ull, 0ull};
+    for (;;) {
+        unsigned long long c = 0;
+        if (lane == 0) c = atomicAdd(A.chunk_ctr, 1ull);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        if (c >= (unsigned long long)A.nchunks) break;
+        const int64_t q0 = (int64_t)c * A.chunk;
+        const int64_t q1 = min(q0 + (int64_t)A.chunk, A.total);
+        int64_t ulo = 0, uhi = 0;
+        if (lane == 0) {
+            ulo = last_le(A.unit_base, 0, nunits - 1, q0);
+            uhi = last_le(A.unit_base, ulo, nunits - 1, q1 - 1);
+        }
+        ulo = __shfl_sync(0xffffffffu, ulo, 0);
+        uhi = __shfl_sync(0xffffffffu, uhi, 0);
+        int64_t cur = -1, ub = 0;
+        int32_t S[L];
+        int SL[L];
+        int32_t pid = 0;
+        int i = 0;
+        uint64_t srows = 0;
+        for (int64_t q = q0 + lane; q < q1; q += 32) {
+            const int64_t u = (ulo == uhi) ? ulo : last_le(A.unit_base, ulo, uhi, q);
+            if (u != cur) {
+                cur = u;
+                const int64_t e = A.e0 + u / L;
+                i = (int)(u % L);
+#pragma unroll
+                for (int p = 0; p < L; ++p) {
+                    S[p] = __ldg(A.fv + (int64_t)p * A.fN + e);
+                    SL[p] = __ldg(A.g.labels + S[p]);
+                }
+                pid = __ldg(A.fpid + e);
+                srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
+                ub = __ldg(A.unit_base + u);
+            }
+            do_piece<L, PASS>(A, S, SL, srows, pid, i, q - ub, tl);
+        }
+    }
+    // per-warp totals, one atomic per warp
+    unsigned long long t0 = tl.tested, t1 = tl.accepted;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+        t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+    }
+    if (lane == 0 && A.stats) {
+        atomicAdd(A.stats + 0, t0);
+        atomicAdd(A.stats + 1, t1);
+    }
+}
+
+// Host launchers, one translation unit per pass.
+cudaError_t launch_extend_count(int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t launch_extend_domain(int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t launch_extend_emit(int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t occupancy_extend_count(int L, int *blocks_per_sm);
+cudaError_t occupancy_extend_domain(int L, int *blocks_per_sm);
+cudaError_t occupancy_extend_emit(int L, int *blocks_per_sm);
+
+} // namespace fsm

@@ -1,0 +1,31 @@
+// fsm_extend_domain.cu -- instantiations of the extension kernel for PASS_DOMAIN.
+#include "fsm_extend.cuh"
+
+namespace fsm {
+
+cudaError_t launch_extend_domain(int L, const ExtArgs &A, int grid, cudaStream_t st) {
+    switch (L) {
+    case 1: extend_kernel<1, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
+    case 2: extend_kernel<2, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
+    case 3: extend_kernel<3, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
+    case 4: extend_kernel<4, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
+    case 5: extend_kernel<5, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
+    case 6: extend_kernel<6, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t occupancy_extend_domain(int L, int *blocks_per_sm) {
+    switch (L) {
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<1, PASS_DOMAIN>, 256, 0);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<2, PASS_DOMAIN>, 256, 0);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<3, PASS_DOMAIN>, 256, 0);
+    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<4, PASS_DOMAIN>, 256, 0);
+    case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<5, PASS_DOMAIN>, 256, 0);
+    case 6: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<6, PASS_DOMAIN>, 256, 0);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+} // namespace fsm

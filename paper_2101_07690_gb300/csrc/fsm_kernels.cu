@@ -1,0 +1,912 @@
+// fsm_kernels.cu -- graph preparation, scans, quick-pattern bookkeeping, canonicalisation,
+// orbits, MNI domains and supports, and the size-1 / size-2 base levels.
+#include "fsm_kernels.cuh"
+
+#include <climits>
+
+#include <atomic>
+
+namespace fsm {
+
+static std::atomic<int64_t> g_launches{0};
+int64_t launches_so_far() { return g_launches.load(); }
+void note_launches(int64_t n) { g_launches.fetch_add(n); }
+#define LAUNCHED(n) note_launches(n)
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int blocks_for(int64_t n, int threads = kThreads) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 64) b = 152 * 64;   // grid-stride beyond this
+    return (int)b;
+}
+
+__device__ __forceinline__ int64_t gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t gstride() { return (int64_t)gridDim.x * blockDim.x; }
+
+// ------------------------------------------------------------------ graph preparation
+
+__global__ void validate_kernel(DevGraph g, int32_t num_labels, int *err) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) {
+        const int32_t rb = g.row_ptr[v], re = g.row_ptr[v + 1];
+        const int32_t lab = g.labels[v];
+        bool bad = rb > re || rb < 0 || (int64_t)re > g.nnz || lab < 0 || lab >= num_labels;
+        if (!bad) {
+            for (int32_t j = rb; j < re && !bad; ++j) {
+                const int32_t w = g.col[j];
+                if (w < 0 || w >= g.n || w == (int32_t)v || (j > rb && g.col[j - 1] >= w)) { bad = true; break; }
+                // symmetry: v must appear in N(w)
+                int32_t lo = g.row_ptr[w], hi = g.row_ptr[w + 1];
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi) >> 1;
+                    if (g.col[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
+                }
+                if (lo >= g.row_ptr[w + 1] || g.col[lo] != (int32_t)v) bad = true;
+            }
+        }
+        if (bad) atomicOr(err, FSM_ERR_CSR);
+    }
+}
+
+__global__ void prepare_kernel(DevGraph g, int64_t *piece_cnt, int32_t *end_off, int32_t *rank,
+                               int32_t *cls_size) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) {
+        const int32_t rb = g.row_ptr[v], re = g.row_ptr[v + 1];
+        const int64_t d = re - rb;
+        int64_t run = 0;
+        for (int32_t j = rb; j < re; ++j) {
+            end_off[j] = (int32_t)run;
+            const int32_t a = g.col[j];
+            run += g.row_ptr[a + 1] - g.row_ptr[a];
+        }
+        piece_cnt[v] = d * (d - 1) / 2 + run;
+        rank[v] = atomicAdd(cls_size + g.labels[v], 1);
+    }
+}
+
+// ------------------------------------------------------------------ scan (exclusive, int64)
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int64_t kScanTile = (int64_t)kScanThreads * kScanItems;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t *warp_tot, int64_t &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) warp_tot[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0;
+        int64_t ti = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        warp_tot[lane] = ti - t;          // exclusive prefix of warp totals
+        if (lane == 31) warp_tot[32] = ti;
+    }
+    __syncthreads();
+    const int64_t res = warp_tot[wid] + incl - x;
+    total = warp_tot[32];
+    __syncthreads();
+    return res;
+}
+
+// out[i] = exclusive prefix within the tile + base[tile] (base may be NULL)
+__global__ void __launch_bounds__(kScanThreads) scan_tile_kernel(const int64_t *in, int64_t *out, int64_t n,
+                                                                 const int64_t *base, int64_t *tile_sum,
+                                                                 bool write_total) {
+    __shared__ int64_t warp_tot[33];
+    const int64_t t0 = (int64_t)blockIdx.x * kScanTile;
+    const int64_t i0 = t0 + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = (i0 + k < n) ? in[i0 + k] : 0;
+        s += v[k];
+    }
+    int64_t total;
+    int64_t ex = block_exclusive_scan(s, warp_tot, total);
+    if (out) {
+        const int64_t b = base ? base[blockIdx.x] : 0;
+        int64_t run = b + ex;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (i0 + k < n) out[i0 + k] = run;
+            run += v[k];
+        }
+        if (write_total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) out[n] = b + total;
+    }
+    if (tile_sum && threadIdx.x == 0) tile_sum[blockIdx.x] = total;
+}
+
+} // namespace
+
+size_t scan_temp_bytes(int64_t n) {
+    if (n <= kScanTile) return 0;
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    return (size_t)(2 * nb + 1) * sizeof(int64_t) + scan_temp_bytes(nb);
+}
+
+cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *temp, cudaStream_t st) {
+    if (n <= 0) {
+        return cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+    }
+    if (n <= kScanTile) {
+        LAUNCHED(1);
+        scan_tile_kernel<<<1, kScanThreads, 0, st>>>(in, out, n, nullptr, nullptr, true);
+        return cudaGetLastError();
+    }
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    int64_t *sums = (int64_t *)temp;
+    int64_t *sums_x = sums + nb;
+    void *rest = sums_x + nb + 1;
+    LAUNCHED(1);
+    scan_tile_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, nullptr, n, nullptr, sums, false);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_scan_i64(sums, sums_x, nb, rest, st);
+    if (e != cudaSuccess) return e;
+    LAUNCHED(1);
+    scan_tile_kernel<<<(unsigned)nb, kScanThreads, 0, st>>>(in, out, n, sums_x, nullptr, true);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const DevGraph &g, int32_t num_labels, int *err, cudaStream_t st) {
+    LAUNCHED(1);
+    validate_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, num_labels, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prepare(const DevGraph &g, int64_t *piece_cnt, int32_t *end_off, int32_t *rank,
+                           int32_t *cls_size, cudaStream_t st) {
+    LAUNCHED(1);
+    prepare_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, piece_cnt, end_off, rank, cls_size);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ unit counts
+
+namespace {
+__global__ void unit_counts_kernel(const int64_t *piece_cnt, const int32_t *fv, int64_t fN, int64_t e0,
+                                   int64_t ne, int L, int64_t *cnt) {
+    const int64_t nu = ne * L;
+    for (int64_t u = gtid(); u < nu; u += gstride()) {
+        const int64_t e = e0 + u / L;
+        const int p = (int)(u % L);
+        cnt[u] = piece_cnt[fv[(int64_t)p * fN + e]];
+    }
+}
+
+__global__ void fill_u64_kernel(unsigned long long *p, unsigned long long v, int64_t n) {
+    for (int64_t i = gtid(); i < n; i += gstride()) p[i] = v;
+}
+
+__global__ void qp_compact_kernel(const unsigned long long *keys, int64_t cap, int64_t *slots,
+                                  unsigned long long *n_out) {
+    for (int64_t s = gtid(); s < cap; s += gstride()) {
+        if (keys[s] != FSM_EMPTY_KEY) {
+            const unsigned long long q = atomicAdd(n_out, 1ull);
+            slots[q] = s;
+        }
+    }
+}
+} // namespace
+
+cudaError_t launch_unit_counts(const int64_t *piece_cnt, const int32_t *fv, int64_t fN, int64_t e0,
+                               int64_t ne, int L, int64_t *cnt, cudaStream_t st) {
+    LAUNCHED(1);
+    unit_counts_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(piece_cnt, fv, fN, e0, ne, L, cnt);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void unit_bytes_kernel(const int32_t *row_ptr, const int64_t *piece_cnt, const int32_t *fv, int64_t fN,
+                                  int64_t e0, int64_t ne, int L, unsigned long long *sum) {
+    const int64_t nu = ne * L;
+    unsigned long long s = 0;
+    for (int64_t u = gtid(); u < nu; u += gstride()) {
+        const int64_t e = e0 + u / L;
+        const int32_t v = fv[(int64_t)(u % L) * fN + e];
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        const int64_t ends = piece_cnt[v] - d * (d - 1) / 2;
+        s += 4ull * (unsigned long long)(d + ends);
+        if (u % L == 0) s += 4ull * (unsigned long long)(L + 1);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(sum, s);
+}
+} // namespace
+
+cudaError_t launch_unit_bytes(const int32_t *row_ptr, const int64_t *piece_cnt, const int32_t *fv, int64_t fN,
+                              int64_t e0, int64_t ne, int L, unsigned long long *sum, cudaStream_t st) {
+    LAUNCHED(1);
+    unit_bytes_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(row_ptr, piece_cnt, fv, fN, e0, ne, L, sum);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t st) {
+    LAUNCHED(1);
+    fill_u64_kernel<<<blocks_for(n), kThreads, 0, st>>>(p, v, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qp_compact(const unsigned long long *keys, int64_t cap, int64_t *slots,
+                              unsigned long long *n_out, cudaStream_t st) {
+    LAUNCHED(1);
+    qp_compact_kernel<<<blocks_for(cap), kThreads, 0, st>>>(keys, cap, slots, n_out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ canonical codes
+
+namespace {
+
+__device__ __forceinline__ bool next_perm(int *a, int n) {
+    int i = n - 2;
+    while (i >= 0 && a[i] >= a[i + 1]) --i;
+    if (i < 0) {
+        for (int l = 0, r = n - 1; l < r; ++l, --r) { int t = a[l]; a[l] = a[r]; a[r] = t; }
+        return false;
+    }
+    int j = n - 1;
+    while (a[j] <= a[i]) --j;
+    int t = a[i]; a[i] = a[j]; a[j] = t;
+    for (int l = i + 1, r = n - 1; l < r; ++l, --r) { t = a[l]; a[l] = a[r]; a[r] = t; }
+    return true;
+}
+
+// Advance perm to the next permutation that keeps every position's label (positions with equal
+// labels form contiguous segments seg_start[c]..); false after the last one.
+__device__ __forceinline__ bool next_label_perm(int K, const int *seg_start, int *perm) {
+    int c = K - 1;
+    while (c >= 0) {
+        const int s = seg_start[c];
+        if (c - s + 1 >= 2 && next_perm(perm + s, c - s + 1)) return true;
+        c = s - 1;
+    }
+    return false;
+}
+
+__device__ __forceinline__ uint32_t adj_code(int K, const uint32_t *adj, const int *perm) {
+    uint32_t code = 0;
+    for (int c1 = 0; c1 < K; ++c1) {
+        const uint32_t row = adj[perm[c1]];
+        for (int c2 = c1 + 1; c2 < K; ++c2) code = (code << 1) | ((row >> perm[c2]) & 1u);
+    }
+    return code;
+}
+
+// Canonical code of a labeled K-vertex graph: the smallest (label sequence, adjacency
+// sequence) over all vertex orders.  The smallest label sequence is the sorted one, so only
+// label-preserving orders of the sorted positions are enumerated.  inv[h] = canonical
+// position of vertex h in the first optimal order.
+__device__ void canonicalise(int K, const int *lab, const uint32_t *adj, unsigned long long &clab,
+                             uint32_t &cadj, uint32_t &inv) {
+    int perm[FSM_MAXK], seg[FSM_MAXK], best[FSM_MAXK];
+    for (int h = 0; h < K; ++h) perm[h] = h;
+    for (int a = 1; a < K; ++a)          // insertion sort by label (stable)
+        for (int b = a; b > 0 && lab[perm[b - 1]] > lab[perm[b]]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
+    for (int c = 0; c < K; ++c) seg[c] = (c > 0 && lab[perm[c]] == lab[perm[c - 1]]) ? seg[c - 1] : c;
+    // within each segment start from ascending vertex index (next_perm enumerates from there)
+    for (int c = 0; c < K; ++c)
+        for (int b = c; b > seg[c] && perm[b - 1] > perm[b]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
+    uint32_t bc = 0xffffffffu;
+    do {
+        const uint32_t code = adj_code(K, adj, perm);
+        if (code < bc) {
+            bc = code;
+            for (int c = 0; c < K; ++c) best[c] = perm[c];
+        }
+    } while (next_label_perm(K, seg, perm));
+    unsigned long long l = 0;
+    for (int c = 0; c < K; ++c) l |= (unsigned long long)(lab[best[c]] & 0xff) << (8 * (7 - c));
+    uint32_t iv = 0;
+    for (int c = 0; c < K; ++c) iv |= (uint32_t)c << (3 * best[c]);
+    clab = l;
+    cadj = bc;
+    inv = iv;
+}
+
+__global__ void qp_canon_kernel(int L, const unsigned long long *keys, const int64_t *slots, int64_t nq,
+                                const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
+                                uint32_t *perm_out) {
+    const int K = L + 2;
+    for (int64_t q = gtid(); q < nq; q += gstride()) {
+        const int64_t slot = slots[q];
+        uint32_t pid, pidx, cross;
+        int i, jpos;
+        split_key(keys[slot], pid, pidx, i, jpos, cross);
+        const uint64_t lab8 = pat_lab8[pid], srows = pat_adj8[pid];
+        const int shape = (int)(pidx >> 18);
+        const int pl[3] = {(int)(pidx >> 12) & 63, (int)(pidx >> 6) & 63, (int)pidx & 63};
+        const int q0 = jpos == 0 ? 1 : 0;
+        const int q1 = jpos == 2 ? 1 : 2;
+        int labH[FSM_MAXK];
+        for (int h = 0; h < L; ++h) labH[h] = (int)(lab8 >> (8 * h)) & 0xff;
+        labH[L] = pl[q0];
+        labH[L + 1] = pl[q1];
+        uint32_t tj0, tj1, txx, adjH[FSM_MAXK];
+        piece_join_edges(shape, jpos, tj0, tj1, txx);
+        join_graph(L, srows, i, tj0, tj1, txx, cross, adjH);
+        unsigned long long cl;
+        uint32_t ca, inv;
+        canonicalise(K, labH, adjH, cl, ca, inv);
+        recs[q].lab = cl;
+        recs[q].adj = ca;
+        recs[q].idx = (uint32_t)q;
+        perm_out[slot] = inv;
+    }
+}
+
+__device__ __forceinline__ bool rec_less(const CodeRec &a, const CodeRec &b) {
+    if (a.lab != b.lab) return a.lab < b.lab;
+    if (a.adj != b.adj) return a.adj < b.adj;
+    return a.idx < b.idx;
+}
+
+__global__ void bitonic_step_kernel(CodeRec *r, int64_t M, int64_t j, int64_t k) {
+    for (int64_t t = gtid(); t < M; t += gstride()) {
+        const int64_t p = t ^ j;
+        if (p <= t) continue;
+        const bool up = (t & k) == 0;
+        CodeRec a = r[t], b = r[p];
+        if (up ? rec_less(b, a) : rec_less(a, b)) { r[t] = b; r[p] = a; }
+    }
+}
+
+__global__ void pad_recs_kernel(CodeRec *r, int64_t n, int64_t M) {
+    for (int64_t t = n + gtid(); t < M; t += gstride()) {
+        r[t].lab = ~0ull; r[t].adj = ~0u; r[t].idx = ~0u;
+    }
+}
+
+__global__ void boundary_flags_kernel(const CodeRec *r, int64_t n, int64_t *flag) {
+    for (int64_t t = gtid(); t < n; t += gstride())
+        flag[t] = (t == 0 || r[t].lab != r[t - 1].lab || r[t].adj != r[t - 1].adj) ? 1 : 0;
+}
+
+__global__ void assign_kernel(const CodeRec *r, int64_t n, const int64_t *slots, const int64_t *flag,
+                              const int64_t *ids, int32_t *qp_pattern, unsigned long long *pat_lab,
+                              uint32_t *pat_adj) {
+    for (int64_t t = gtid(); t < n; t += gstride()) {
+        const int64_t pid = ids[t] + flag[t] - 1;
+        qp_pattern[slots[r[t].idx]] = (int32_t)pid;
+        if (flag[t]) { pat_lab[pid] = r[t].lab; pat_adj[pid] = r[t].adj; }
+    }
+}
+
+__device__ __forceinline__ void decode_code(int K, unsigned long long clab, uint32_t cadj, int *lab, uint32_t *adj) {
+    const int np = K * (K - 1) / 2;
+    for (int c = 0; c < K; ++c) { lab[c] = (int)(clab >> (8 * (7 - c))) & 0xff; adj[c] = 0; }
+    int q = 0;
+    for (int c1 = 0; c1 < K; ++c1)
+        for (int c2 = c1 + 1; c2 < K; ++c2, ++q)
+            if ((cadj >> (np - 1 - q)) & 1u) { adj[c1] |= 1u << c2; adj[c2] |= 1u << c1; }
+}
+
+__global__ void orbits_kernel(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+                              uint64_t *orbit, int32_t *min_orbit) {
+    for (int64_t P = gtid(); P < np; P += gstride()) {
+        int lab[FSM_MAXK], perm[FSM_MAXK], seg[FSM_MAXK], rep[FSM_MAXK];
+        uint32_t adj[FSM_MAXK];
+        decode_code(K, pat_lab[P], pat_adj[P], lab, adj);
+        const uint32_t code = pat_adj[P];
+        for (int c = 0; c < K; ++c) {
+            perm[c] = c;
+            rep[c] = c;
+            seg[c] = (c > 0 && lab[c] == lab[c - 1]) ? seg[c - 1] : c;
+        }
+        // automorphisms are the label-preserving orders with the same adjacency sequence
+        do {
+            if (adj_code(K, adj, perm) == code)
+                for (int c = 0; c < K; ++c) if (perm[c] < rep[c]) rep[c] = perm[c];
+        } while (next_label_perm(K, seg, perm));
+        uint64_t o = 0;
+        int mn = K;
+        for (int c = 0; c < K; ++c) {
+            o |= (uint64_t)rep[c] << (8 * c);
+            if (rep[c] == c) {
+                int sz = 0;
+                for (int x = 0; x < K; ++x) sz += rep[x] == c;
+                if (sz < mn) mn = sz;
+            }
+        }
+        orbit[P] = o;
+        min_orbit[P] = mn;
+    }
+}
+
+__global__ void pattern_counts_kernel(const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                                      const unsigned long long *qp_count, unsigned long long *pat_count) {
+    for (int64_t q = gtid(); q < nq; q += gstride()) {
+        const int64_t s = slots[q];
+        atomicAdd(pat_count + qp_pattern[s], qp_count[s]);
+    }
+}
+
+__global__ void domain_sizes_kernel(int K, const unsigned long long *pat_lab, const uint64_t *orbit,
+                                    const int32_t *min_orbit, const unsigned long long *pat_count, int64_t np,
+                                    int64_t t, const int32_t *cls_size, uint8_t *live, int64_t *words) {
+    for (int64_t P = gtid(); P < np; P += gstride()) {
+        const bool lv = (unsigned long long)min_orbit[P] * pat_count[P] >= (unsigned long long)t;
+        live[P] = lv ? 1 : 0;
+        for (int c = 0; c < 8; ++c) {
+            int64_t w = 0;
+            if (lv && c < K && (int)((orbit[P] >> (8 * c)) & 0xff) == c) {
+                const int lab = (int)(pat_lab[P] >> (8 * (7 - c))) & 0xff;
+                w = ((int64_t)cls_size[lab] + 31) / 32;
+            }
+            words[P * 8 + c] = w;
+        }
+    }
+}
+
+__global__ void domain_offsets_kernel(const int64_t *words, const int64_t *scanned, int64_t n8, int64_t *off) {
+    for (int64_t x = gtid(); x < n8; x += gstride()) off[x] = words[x] > 0 ? scanned[x] : -1;
+}
+
+// one warp per (pattern, orbit representative)
+__global__ void support_kernel(int K, const uint64_t *orbit, const uint8_t *live, const int64_t *dom_off,
+                               const int64_t *words, const uint32_t *dom, int64_t np,
+                               unsigned long long *sigma) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = np * 8;
+    for (int64_t w = gtid() >> 5; w < nw; w += gstride() >> 5) {
+        const int64_t P = w >> 3;
+        const int c = (int)(w & 7);
+        if (!live[P] || c >= K || (int)((orbit[P] >> (8 * c)) & 0xff) != c) continue;
+        const uint32_t *b = dom + dom_off[w];
+        const int64_t n = words[w];
+        unsigned long long s = 0;
+        for (int64_t x = lane; x < n; x += 32) s += __popc(b[x]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) atomicMin(sigma + P, s);
+    }
+}
+
+__global__ void freq_flags_kernel(const unsigned long long *sigma, int64_t np, int64_t t, int64_t *flag) {
+    for (int64_t P = gtid(); P < np; P += gstride())
+        flag[P] = (sigma[P] != ~0ull && sigma[P] >= (unsigned long long)t) ? 1 : 0;
+}
+
+__global__ void new_ids_kernel(const int64_t *flag, const int64_t *scanned, int64_t np, int32_t *newid) {
+    for (int64_t P = gtid(); P < np; P += gstride()) newid[P] = flag[P] ? (int32_t)scanned[P] : -1;
+}
+
+__global__ void gather_frequent_kernel(int K, const int32_t *newid, int64_t np, const unsigned long long *pat_lab,
+                                       const uint32_t *pat_adj, const unsigned long long *sigma,
+                                       const unsigned long long *pat_count, unsigned long long *o_lab,
+                                       uint32_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
+                                       uint64_t *o_lab8, uint64_t *o_adj8) {
+    for (int64_t P = gtid(); P < np; P += gstride()) {
+        const int32_t id = newid[P];
+        if (id < 0) continue;
+        o_lab[id] = pat_lab[P];
+        o_adj[id] = pat_adj[P];
+        o_sigma[id] = sigma[P];
+        o_count[id] = pat_count[P];
+        if (o_lab8) {
+            int lab[FSM_MAXK];
+            uint32_t adj[FSM_MAXK];
+            decode_code(K, pat_lab[P], pat_adj[P], lab, adj);
+            uint64_t l8 = 0, a8 = 0;
+            for (int c = 0; c < K; ++c) {
+                l8 |= (uint64_t)(lab[c] & 0xff) << (8 * c);
+                a8 |= (uint64_t)(adj[c] & 0xff) << (8 * c);
+            }
+            o_lab8[id] = l8;
+            o_adj8[id] = a8;
+        }
+    }
+}
+
+__global__ void sum_frequent_kernel(const int32_t *newid, const unsigned long long *pat_count, int64_t np,
+                                    unsigned long long *sum) {
+    unsigned long long s = 0;
+    for (int64_t P = gtid(); P < np; P += gstride())
+        if (newid[P] >= 0) s += pat_count[P];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(sum, s);
+}
+
+} // namespace
+
+cudaError_t launch_qp_canon(int L, const unsigned long long *keys, const int64_t *slots, int64_t nq,
+                            const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
+                            uint32_t *perm, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    qp_canon_kernel<<<blocks_for(nq, 128), 128, 0, st>>>(L, keys, slots, nq, pat_lab8, pat_adj8, recs, perm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_codes(CodeRec *recs, int64_t n, cudaStream_t st) {
+    if (n <= 1) return cudaSuccess;
+    int64_t M = 1;
+    while (M < n) M <<= 1;
+    LAUNCHED(1);
+    pad_recs_kernel<<<blocks_for(M - n + 1), kThreads, 0, st>>>(recs, n, M);
+    for (int64_t k = 2; k <= M; k <<= 1)
+        for (int64_t j = k >> 1; j > 0; j >>= 1) {
+            LAUNCHED(1);
+            bitonic_step_kernel<<<blocks_for(M), kThreads, 0, st>>>(recs, M, j, k);
+        }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assign_patterns(const CodeRec *recs, int64_t n, const int64_t *slots, int64_t *flag,
+                                   int64_t *ids, void *scan_tmp, int32_t *qp_pattern,
+                                   unsigned long long *pat_lab, uint32_t *pat_adj, cudaStream_t st) {
+    if (n <= 0) return cudaMemsetAsync(ids, 0, sizeof(int64_t), st);
+    LAUNCHED(1);
+    boundary_flags_kernel<<<blocks_for(n), kThreads, 0, st>>>(recs, n, flag);
+    cudaError_t e = launch_scan_i64(flag, ids, n, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    LAUNCHED(1);
+    assign_kernel<<<blocks_for(n), kThreads, 0, st>>>(recs, n, slots, flag, ids, qp_pattern, pat_lab, pat_adj);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orbits(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+                          uint64_t *orbit, int32_t *min_orbit, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    orbits_kernel<<<blocks_for(np, 128), 128, 0, st>>>(K, pat_lab, pat_adj, np, orbit, min_orbit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pattern_counts(const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                                  const unsigned long long *qp_count, unsigned long long *pat_count,
+                                  cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    pattern_counts_kernel<<<blocks_for(nq), kThreads, 0, st>>>(slots, nq, qp_pattern, qp_count, pat_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_sizes(int K, const unsigned long long *pat_lab, const uint64_t *orbit,
+                                const int32_t *min_orbit, const unsigned long long *pat_count,
+                                int64_t np, int64_t t, const int32_t *cls_size, uint8_t *live,
+                                int64_t *words, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    domain_sizes_kernel<<<blocks_for(np), kThreads, 0, st>>>(K, pat_lab, orbit, min_orbit, pat_count, np, t,
+                                                           cls_size, live, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_domain_offsets(const int64_t *words, const int64_t *scanned, int64_t n8, int64_t *off,
+                                  cudaStream_t st) {
+    if (n8 <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    domain_offsets_kernel<<<blocks_for(n8), kThreads, 0, st>>>(words, scanned, n8, off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_support(int K, const uint64_t *orbit, const uint8_t *live, const int64_t *dom_off,
+                           const int64_t *words, const uint32_t *dom, int64_t np,
+                           unsigned long long *sigma, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    support_kernel<<<blocks_for(np * 8 * 32), kThreads, 0, st>>>(K, orbit, live, dom_off, words, dom, np, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_freq_flags(const unsigned long long *sigma, int64_t np, int64_t t, int64_t *flag,
+                              cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    freq_flags_kernel<<<blocks_for(np), kThreads, 0, st>>>(sigma, np, t, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_new_ids(const int64_t *flag, const int64_t *scanned, int64_t np, int32_t *newid,
+                           cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    new_ids_kernel<<<blocks_for(np), kThreads, 0, st>>>(flag, scanned, np, newid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_frequent(int K, const int32_t *newid, int64_t np, const unsigned long long *pat_lab,
+                                   const uint32_t *pat_adj, const unsigned long long *sigma,
+                                   const unsigned long long *pat_count, unsigned long long *o_lab,
+                                   uint32_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
+                                   uint64_t *o_lab8, uint64_t *o_adj8, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    gather_frequent_kernel<<<blocks_for(np), kThreads, 0, st>>>(K, newid, np, pat_lab, pat_adj, sigma, pat_count,
+                                                              o_lab, o_adj, o_sigma, o_count, o_lab8, o_adj8);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sum_frequent(const int32_t *newid, const unsigned long long *pat_count, int64_t np,
+                                unsigned long long *sum, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    sum_frequent_kernel<<<blocks_for(np), kThreads, 0, st>>>(newid, pat_count, np, sum);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ base levels
+
+namespace {
+
+__global__ void level1_flags_kernel(const DevGraph g, const int32_t *label_newid, int64_t *flag) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) flag[v] = label_newid[g.labels[v]] >= 0 ? 1 : 0;
+}
+
+__global__ void level1_write_kernel(const DevGraph g, const int32_t *label_newid, const int64_t *flag,
+                                    const int64_t *scanned, int32_t *fv, int32_t *fpid) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) {
+        if (!flag[v]) continue;
+        const int64_t pos = scanned[v];
+        fv[pos] = (int32_t)v;
+        fpid[pos] = label_newid[g.labels[v]];
+    }
+}
+
+__global__ void level2_offsets_kernel(int32_t NL, const int32_t *cls_size, int64_t *pair_off, int64_t *total) {
+    if (gtid() != 0) return;
+    int64_t run = 0;
+    for (int lo = 0; lo < NL; ++lo)
+        for (int hi = 0; hi < NL; ++hi) {
+            const int64_t x = ((int64_t)lo * NL + hi) * 2;
+            if (hi < lo) { pair_off[x] = -1; pair_off[x + 1] = -1; continue; }
+            pair_off[x] = run;
+            run += ((int64_t)cls_size[lo] + 31) / 32;
+            if (hi > lo) { pair_off[x + 1] = run; run += ((int64_t)cls_size[hi] + 31) / 32; }
+            else pair_off[x + 1] = -1;
+        }
+    *total = run;
+}
+
+__device__ __forceinline__ void set_bit(uint32_t *dom, int64_t off, int32_t r) {
+    uint32_t *w = dom + off + (r >> 5);
+    const uint32_t bit = 1u << (r & 31);
+    if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+}
+
+__global__ void level2_domains_kernel(const DevGraph g, int32_t NL, const int64_t *pair_off, uint32_t *dom,
+                                      unsigned long long *pair_count) {
+    for (int64_t u = gtid(); u < g.n; u += gstride()) {
+        const int lu = g.labels[u];
+        const int32_t ru = g.rank[u];
+        for (int32_t j = g.row_ptr[u]; j < g.row_ptr[u + 1]; ++j) {
+            const int32_t w = g.col[j];
+            if (w < u) continue;
+            const int lw = g.labels[w];
+            const int lo = lu < lw ? lu : lw, hi = lu < lw ? lw : lu;
+            const int64_t x = ((int64_t)lo * NL + hi) * 2;
+            atomicAdd(pair_count + (x >> 1), 1ull);
+            if (lo == hi) {
+                set_bit(dom, pair_off[x], ru);
+                set_bit(dom, pair_off[x], g.rank[w]);
+            } else if (lu < lw) {
+                set_bit(dom, pair_off[x], ru);
+                set_bit(dom, pair_off[x + 1], g.rank[w]);
+            } else {
+                set_bit(dom, pair_off[x], g.rank[w]);
+                set_bit(dom, pair_off[x + 1], ru);
+            }
+        }
+    }
+}
+
+// one warp per label pair (lo <= hi)
+__global__ void level2_support_kernel(int32_t NL, const int32_t *cls_size, const int64_t *pair_off,
+                                      const uint32_t *dom, unsigned long long *sigma) {
+    const int lane = threadIdx.x & 31;
+    const int64_t np = (int64_t)NL * NL;
+    for (int64_t w = gtid() >> 5; w < np; w += gstride() >> 5) {
+        const int lo = (int)(w / NL), hi = (int)(w % NL);
+        if (hi < lo) { if (lane == 0) sigma[w] = 0; continue; }
+        unsigned long long s0 = 0, s1 = 0;
+        const int64_t n0 = ((int64_t)cls_size[lo] + 31) / 32;
+        for (int64_t x = lane; x < n0; x += 32) s0 += __popc(dom[pair_off[w * 2] + x]);
+        if (hi > lo) {
+            const int64_t n1 = ((int64_t)cls_size[hi] + 31) / 32;
+            for (int64_t x = lane; x < n1; x += 32) s1 += __popc(dom[pair_off[w * 2 + 1] + x]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        if (lane == 0) sigma[w] = (hi > lo) ? (s0 < s1 ? s0 : s1) : s0;
+    }
+}
+
+__global__ void level2_flags_kernel(const DevGraph g, int32_t NL, const int32_t *pair_newid, int64_t *flag) {
+    for (int64_t u = gtid(); u < g.n; u += gstride()) {
+        const int lu = g.labels[u];
+        int64_t c = 0;
+        for (int32_t j = g.row_ptr[u]; j < g.row_ptr[u + 1]; ++j) {
+            const int32_t w = g.col[j];
+            if (w < u) continue;
+            const int lw = g.labels[w];
+            const int lo = lu < lw ? lu : lw, hi = lu < lw ? lw : lu;
+            c += pair_newid[lo * NL + hi] >= 0;
+        }
+        flag[u] = c;
+    }
+}
+
+__global__ void level2_write_kernel(const DevGraph g, int32_t NL, const int32_t *pair_newid,
+                                    const int64_t *scanned, int32_t *fv, int64_t fN, int32_t *fpid) {
+    for (int64_t u = gtid(); u < g.n; u += gstride()) {
+        const int lu = g.labels[u];
+        int64_t pos = scanned[u];
+        for (int32_t j = g.row_ptr[u]; j < g.row_ptr[u + 1]; ++j) {
+            const int32_t w = g.col[j];
+            if (w < u) continue;
+            const int lw = g.labels[w];
+            const int lo = lu < lw ? lu : lw, hi = lu < lw ? lw : lu;
+            const int32_t id = pair_newid[lo * NL + hi];
+            if (id < 0) continue;
+            // canonical order: smaller label first; equal labels: smaller id first (u < w)
+            const bool u_first = lu <= lw;
+            fv[pos] = u_first ? (int32_t)u : w;
+            fv[fN + pos] = u_first ? w : (int32_t)u;
+            fpid[pos] = id;
+            ++pos;
+        }
+    }
+}
+
+__global__ void piece_table_kernel(const unsigned long long *lab, const uint32_t *adj, int64_t n, uint8_t *pf) {
+    for (int64_t P = gtid(); P < n; P += gstride()) {
+        const int l0 = (int)(lab[P] >> 56) & 0xff, l1 = (int)(lab[P] >> 48) & 0xff, l2 = (int)(lab[P] >> 40) & 0xff;
+        const uint32_t a01 = (adj[P] >> 2) & 1u, a02 = (adj[P] >> 1) & 1u, a12 = adj[P] & 1u;
+        uint32_t idx;
+        if (a01 && a02 && a12) idx = tri_index(l0, l1, l2);
+        else if (a01 && a02) idx = wedge_index(l0, l1, l2);
+        else if (a01 && a12) idx = wedge_index(l1, l0, l2);
+        else idx = wedge_index(l2, l0, l1);
+        pf[idx] = 1;
+    }
+}
+
+} // namespace
+
+cudaError_t launch_level1_frontier(const DevGraph &g, const int32_t *label_newid, int64_t *flag,
+                                   int64_t *scanned, void *scan_tmp, int32_t *fv, int32_t *fpid,
+                                   cudaStream_t st) {
+    LAUNCHED(1);
+    level1_flags_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, label_newid, flag);
+    cudaError_t e = launch_scan_i64(flag, scanned, g.n, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    LAUNCHED(1);
+    level1_write_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, label_newid, flag, scanned, fv, fpid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level2_offsets(int32_t NL, const int32_t *cls_size, int64_t *pair_off,
+                                  int64_t *total_words, cudaStream_t st) {
+    LAUNCHED(1);
+    level2_offsets_kernel<<<1, 32, 0, st>>>(NL, cls_size, pair_off, total_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level2_domains(const DevGraph &g, int32_t NL, const int64_t *pair_off,
+                                  uint32_t *dom, unsigned long long *pair_count, cudaStream_t st) {
+    LAUNCHED(1);
+    level2_domains_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, NL, pair_off, dom, pair_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level2_support(int32_t NL, const int32_t *cls_size, const int64_t *pair_off,
+                                  const uint32_t *dom, unsigned long long *sigma, cudaStream_t st) {
+    LAUNCHED(1);
+    level2_support_kernel<<<blocks_for((int64_t)NL * NL * 32), kThreads, 0, st>>>(NL, cls_size, pair_off, dom, sigma);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level2_frontier(const DevGraph &g, int32_t NL, const int32_t *pair_newid,
+                                   int64_t *flag, int64_t *scanned, void *scan_tmp, int32_t *fv,
+                                   int64_t fN, int32_t *fpid, cudaStream_t st) {
+    LAUNCHED(1);
+    level2_flags_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, NL, pair_newid, flag);
+    cudaError_t e = launch_scan_i64(flag, scanned, g.n, scan_tmp, st);
+    if (e != cudaSuccess) return e;
+    LAUNCHED(1);
+    level2_write_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, NL, pair_newid, scanned, fv, fN, fpid);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void level1_tables_kernel(int32_t NL, const int32_t *cls_size, int64_t t, int32_t *label_newid,
+                                     uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                     unsigned long long *sigma, unsigned long long *count,
+                                     unsigned long long *n_freq) {
+    if (gtid() != 0) return;
+    int32_t id = 0;
+    for (int l = 0; l < NL; ++l) {
+        // size-1 pattern of label l: every vertex of the class is an image (Definition 2)
+        const int64_t s = cls_size[l];
+        if (s >= t && s > 0) {
+            label_newid[l] = id;
+            lab8[id] = (uint64_t)l;
+            adj8[id] = 0;
+            clab[id] = (unsigned long long)l << 56;
+            cadj[id] = 0;
+            sigma[id] = (unsigned long long)s;
+            count[id] = (unsigned long long)s;
+            ++id;
+        } else {
+            label_newid[l] = -1;
+        }
+    }
+    *n_freq = (unsigned long long)id;
+}
+
+__global__ void level2_tables_kernel(int32_t NL, const unsigned long long *pair_sigma,
+                                     const unsigned long long *pair_count, int64_t t, int32_t *pair_newid,
+                                     uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                     unsigned long long *sigma, unsigned long long *count,
+                                     unsigned long long *n_freq) {
+    if (gtid() != 0) return;
+    int32_t id = 0;
+    for (int lo = 0; lo < NL; ++lo)
+        for (int hi = 0; hi < NL; ++hi) {
+            const int64_t x = (int64_t)lo * NL + hi;
+            if (hi >= lo && pair_count[x] > 0 && pair_sigma[x] >= (unsigned long long)t) {
+                pair_newid[x] = id;
+                lab8[id] = (uint64_t)lo | ((uint64_t)hi << 8);
+                adj8[id] = 0x0102ull;                  // row 0 = {1}, row 1 = {0}
+                clab[id] = ((unsigned long long)lo << 56) | ((unsigned long long)hi << 48);
+                cadj[id] = 1u;
+                sigma[id] = pair_sigma[x];
+                count[id] = pair_count[x];
+                ++id;
+            } else {
+                pair_newid[x] = -1;
+            }
+        }
+    *n_freq = (unsigned long long)id;
+}
+} // namespace
+
+cudaError_t launch_level1_tables(int32_t NL, const int32_t *cls_size, int64_t t, int32_t *label_newid,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 unsigned long long *sigma, unsigned long long *count,
+                                 unsigned long long *n_freq, cudaStream_t st) {
+    LAUNCHED(1);
+    level1_tables_kernel<<<1, 32, 0, st>>>(NL, cls_size, t, label_newid, lab8, adj8, clab, cadj, sigma, count, n_freq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_level2_tables(int32_t NL, const unsigned long long *pair_sigma,
+                                 const unsigned long long *pair_count, int64_t t, int32_t *pair_newid,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 unsigned long long *sigma, unsigned long long *count,
+                                 unsigned long long *n_freq, cudaStream_t st) {
+    LAUNCHED(1);
+    level2_tables_kernel<<<1, 32, 0, st>>>(NL, pair_sigma, pair_count, t, pair_newid, lab8, adj8, clab, cadj,
+                                           sigma, count, n_freq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
+                               uint8_t *piece_freq, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    piece_table_kernel<<<blocks_for(n), kThreads, 0, st>>>(lab, adj, n, piece_freq);
+    return cudaGetLastError();
+}
+
+} // namespace fsm

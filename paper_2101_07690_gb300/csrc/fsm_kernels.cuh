@@ -1,0 +1,124 @@
+// fsm_kernels.cuh -- host-callable launchers for every kernel outside the extension kernel.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include "fsm_device.cuh"
+
+namespace fsm {
+
+// One pattern's canonical code: labels in canonical order packed big-endian (byte 7 = first
+// position) and the adjacency sequence A(0,1), A(0,2), ..., A(k-2,k-1) with A(0,1) as the most
+// significant of the k(k-1)/2 used bits.  Integer order on (lab, adj) is the lexicographic
+// order of the code.  idx carries a payload through sorting.
+struct CodeRec {
+    unsigned long long lab;
+    uint32_t adj;
+    uint32_t idx;
+};
+
+// ---- graph preparation
+cudaError_t launch_validate(const DevGraph &g, int32_t num_labels, int *err, cudaStream_t st);
+cudaError_t launch_prepare(const DevGraph &g, int64_t *piece_cnt, int32_t *end_off, int32_t *rank,
+                           int32_t *cls_size, cudaStream_t st);
+
+// ---- scans (exclusive, out has n+1 entries, out[n] = total)
+size_t scan_temp_bytes(int64_t n);
+cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *temp, cudaStream_t st);
+
+// ---- per-batch unit piece counts: cnt[u] = piece_cnt[fv[(u % L) * fN + e0 + u / L]]
+cudaError_t launch_unit_counts(const int64_t *piece_cnt, const int32_t *fv, int64_t fN, int64_t e0,
+                               int64_t ne, int L, int64_t *cnt, cudaStream_t st);
+
+// algorithmic bytes of one batch of units, added to *sum: per unit 4 * (d(v) + end pieces of v)
+// (the key list and every end list read once) plus 4 * (L + 1) per embedding (vertices + id)
+cudaError_t launch_unit_bytes(const int32_t *row_ptr, const int64_t *piece_cnt, const int32_t *fv, int64_t fN,
+                              int64_t e0, int64_t ne, int L, unsigned long long *sum, cudaStream_t st);
+
+// ---- quick-pattern table
+cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t st);
+cudaError_t launch_qp_compact(const unsigned long long *keys, int64_t cap, int64_t *slots,
+                              unsigned long long *n_out, cudaStream_t st);
+// canonical code of each distinct key; writes recs[q] (idx = q) and perm[slot]
+cudaError_t launch_qp_canon(int L, const unsigned long long *keys, const int64_t *slots, int64_t nq,
+                            const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
+                            uint32_t *perm, cudaStream_t st);
+// sort recs[0..n) ascending by (lab, adj, idx); recs must have room for next_pow2(n) entries
+cudaError_t launch_sort_codes(CodeRec *recs, int64_t n, cudaStream_t st);
+// after sorting: pattern ids.  flags/ids scratch of n+1 entries.  Writes qp_pattern[slot],
+// pattern codes pat_lab/pat_adj, and *n_pat.
+cudaError_t launch_assign_patterns(const CodeRec *recs, int64_t n, const int64_t *slots, int64_t *flag,
+                                   int64_t *ids, void *scan_tmp, int32_t *qp_pattern,
+                                   unsigned long long *pat_lab, uint32_t *pat_adj, cudaStream_t st);
+// per pattern: orbit representatives (8 bytes), smallest orbit size
+cudaError_t launch_orbits(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+                          uint64_t *orbit, int32_t *min_orbit, cudaStream_t st);
+// pattern embedding counts: pat_count[pattern[slot]] += count[slot]
+cudaError_t launch_pattern_counts(const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                                  const unsigned long long *qp_count, unsigned long long *pat_count,
+                                  cudaStream_t st);
+// live patterns (count * smallest orbit >= t) and the words of each orbit bitmap
+cudaError_t launch_domain_sizes(int K, const unsigned long long *pat_lab, const uint64_t *orbit,
+                                const int32_t *min_orbit, const unsigned long long *pat_count,
+                                int64_t np, int64_t t, const int32_t *cls_size, uint8_t *live,
+                                int64_t *words, cudaStream_t st);
+// offsets from the scanned sizes (-1 where no bitmap)
+cudaError_t launch_domain_offsets(const int64_t *words, const int64_t *scanned, int64_t n8, int64_t *off,
+                                  cudaStream_t st);
+// MNI support: sigma[P] = min over orbit bitmaps of popcount (0 for non-live patterns)
+cudaError_t launch_support(int K, const uint64_t *orbit, const uint8_t *live, const int64_t *dom_off,
+                           const int64_t *words, const uint32_t *dom, int64_t np,
+                           unsigned long long *sigma, cudaStream_t st);
+// frequent flags (sigma >= t) as int64 0/1 for scanning, and the new ids afterwards
+cudaError_t launch_freq_flags(const unsigned long long *sigma, int64_t np, int64_t t, int64_t *flag,
+                              cudaStream_t st);
+cudaError_t launch_new_ids(const int64_t *flag, const int64_t *scanned, int64_t np, int32_t *newid,
+                           cudaStream_t st);
+// gather frequent patterns: codes, sigma, counts -> compact arrays; also level tables (lab8/adj8)
+cudaError_t launch_gather_frequent(int K, const int32_t *newid, int64_t np, const unsigned long long *pat_lab,
+                                   const uint32_t *pat_adj, const unsigned long long *sigma,
+                                   const unsigned long long *pat_count, unsigned long long *o_lab,
+                                   uint32_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
+                                   uint64_t *o_lab8, uint64_t *o_adj8, cudaStream_t st);
+// sum of counts of frequent patterns (the next frontier's size)
+cudaError_t launch_sum_frequent(const int32_t *newid, const unsigned long long *pat_count, int64_t np,
+                                unsigned long long *sum, cudaStream_t st);
+
+// ---- base levels
+// level 1: frequent labels (cls_size >= t): flag per label
+// level 1 frontier: vertices whose label is frequent (deterministic compaction)
+cudaError_t launch_level1_frontier(const DevGraph &g, const int32_t *label_newid, int64_t *flag,
+                                   int64_t *scanned, void *scan_tmp, int32_t *fv, int32_t *fpid,
+                                   cudaStream_t st);
+// level 2: edge patterns over label pairs (lo <= hi) indexed lo*NL + hi
+cudaError_t launch_level2_domains(const DevGraph &g, int32_t NL, const int64_t *pair_off,
+                                  uint32_t *dom, unsigned long long *pair_count, cudaStream_t st);
+cudaError_t launch_level2_offsets(int32_t NL, const int32_t *cls_size, int64_t *pair_off,
+                                  int64_t *total_words, cudaStream_t st);
+cudaError_t launch_level2_support(int32_t NL, const int32_t *cls_size, const int64_t *pair_off,
+                                  const uint32_t *dom, unsigned long long *sigma, cudaStream_t st);
+// level 2 frontier: every edge of a frequent pair in canonical order
+cudaError_t launch_level2_frontier(const DevGraph &g, int32_t NL, const int32_t *pair_newid,
+                                   int64_t *flag, int64_t *scanned, void *scan_tmp, int32_t *fv,
+                                   int64_t fN, int32_t *fpid, cudaStream_t st);
+
+// size-1 and size-2 pattern tables (single-block kernels over the <= 64 labels / label pairs):
+// frequent ids in code order, level tables, codes, supports, counts; *n_freq = frequent count
+cudaError_t launch_level1_tables(int32_t NL, const int32_t *cls_size, int64_t t, int32_t *label_newid,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 unsigned long long *sigma, unsigned long long *count,
+                                 unsigned long long *n_freq, cudaStream_t st);
+cudaError_t launch_level2_tables(int32_t NL, const unsigned long long *pair_sigma,
+                                 const unsigned long long *pair_count, int64_t t, int32_t *pair_newid,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 unsigned long long *sigma, unsigned long long *count,
+                                 unsigned long long *n_freq, cudaStream_t st);
+
+// number of kernels launched by this process so far
+int64_t launches_so_far();
+void note_launches(int64_t n);
+
+// ---- pieces: mark the frequent size-3 patterns by piece index
+cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
+                               uint8_t *piece_freq, cudaStream_t st);
+
+} // namespace fsm

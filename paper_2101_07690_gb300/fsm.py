@@ -1,0 +1,219 @@
+"""Python binding of the C ABI in include/fsm.h (argument marshalling only).
+
+Every function keeps the C name and forwards to ``_build/libfsm.so``; all mining work runs in
+the library's CUDA kernels.  A missing library raises ``ImportError`` -- there is no other
+implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfsm.so")
+
+FSM_OK = 0
+FSM_EINVAL = -1
+FSM_ENOMEM = -2
+FSM_ECUDA = -3
+FSM_ETIMEOUT = -4
+FSM_EUNSUPPORTED = -5
+_NAMES = {FSM_EINVAL: "FSM_EINVAL", FSM_ENOMEM: "FSM_ENOMEM", FSM_ECUDA: "FSM_ECUDA",
+          FSM_ETIMEOUT: "FSM_ETIMEOUT", FSM_EUNSUPPORTED: "FSM_EUNSUPPORTED"}
+
+# every entry point that include/fsm.h declares
+EXPORTS = ["fsm_load_graph", "fsm_set_option", "fsm_mine", "fsm_result_count", "fsm_result_get",
+           "fsm_result_embeddings", "fsm_result_copy", "fsm_result_stat", "fsm_free_result",
+           "fsm_free_graph", "fsm_last_error", "fsm_debug_dissect"]
+
+
+class FsmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libfsm.so (built by ``paper_2101_07690_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libfsm.so not built at {p}; run paper_2101_07690_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    P = ctypes.POINTER
+    vp, i32, i64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64
+    sig = {
+        "fsm_load_graph": (ctypes.c_int, [P(i32), P(i32), P(i32), i32, i32, P(vp)]),
+        "fsm_set_option": (ctypes.c_int, [vp, ctypes.c_char_p, i64]),
+        "fsm_mine": (ctypes.c_int, [vp, i32, i64, ctypes.c_double, P(vp)]),
+        "fsm_result_count": (i64, [vp]),
+        "fsm_result_get": (ctypes.c_int, [vp, i64, P(i32), P(u64), P(i64)]),
+        "fsm_result_embeddings": (ctypes.c_int, [vp, i64, P(i64)]),
+        "fsm_result_copy": (ctypes.c_int, [vp, P(i32), P(u64), P(i64), P(i64)]),
+        "fsm_result_stat": (ctypes.c_int, [vp, ctypes.c_char_p, P(i64)]),
+        "fsm_free_result": (None, [vp]),
+        "fsm_free_graph": (None, [vp]),
+        "fsm_last_error": (ctypes.c_char_p, []),
+        "fsm_debug_dissect": (ctypes.c_int, [i32, P(i32), P(ctypes.c_uint32), P(ctypes.c_uint32), P(i32), P(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != FSM_OK:
+        raise FsmError(rc, fsm_last_error())
+    return rc
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def fsm_last_error() -> str:
+    return (load().fsm_last_error() or b"").decode()
+
+
+def fsm_load_graph(row_ptr, col, labels, n: int, num_labels: int) -> int:
+    """Copy a CSR graph to the current device; returns the graph handle.  Arrays may be numpy
+    arrays or raw host addresses (ints) of int32 buffers."""
+    lib = load()
+    keep = []
+
+    def arg(a):
+        if isinstance(a, int):
+            return ctypes.cast(a, ctypes.POINTER(ctypes.c_int32))
+        arr = _i32(a)
+        keep.append(arr)
+        return _ptr(arr, ctypes.c_int32)
+
+    h = ctypes.c_void_p()
+    _check(lib.fsm_load_graph(arg(row_ptr), arg(col), arg(labels), int(n), int(num_labels), ctypes.byref(h)))
+    return h.value
+
+
+def fsm_set_option(g: int, key: str, value: int) -> None:
+    _check(load().fsm_set_option(g, key.encode(), int(value)))
+
+
+def fsm_mine(g: int, k: int, min_support: int, sample_rate: float = 1.0) -> int:
+    r = ctypes.c_void_p()
+    _check(load().fsm_mine(g, int(k), int(min_support), float(sample_rate), ctypes.byref(r)))
+    return r.value
+
+
+def fsm_result_count(r: int) -> int:
+    n = load().fsm_result_count(r)
+    if n < 0:
+        raise FsmError(int(n), fsm_last_error())
+    return int(n)
+
+
+def fsm_result_get(r: int, i: int, k: int):
+    labels = np.zeros(k, np.int32)
+    adj = ctypes.c_uint64()
+    sup = ctypes.c_int64()
+    _check(load().fsm_result_get(r, int(i), _ptr(labels, ctypes.c_int32), ctypes.byref(adj), ctypes.byref(sup)))
+    return labels, int(adj.value), int(sup.value)
+
+
+def fsm_result_embeddings(r: int, i: int) -> int:
+    c = ctypes.c_int64()
+    _check(load().fsm_result_embeddings(r, int(i), ctypes.byref(c)))
+    return int(c.value)
+
+
+def fsm_result_copy(r: int, k: int) -> dict:
+    n = fsm_result_count(r)
+    out = {"labels": np.zeros((n, k), np.int32), "adj": np.zeros(n, np.uint64),
+           "support": np.zeros(n, np.int64), "count": np.zeros(n, np.int64)}
+    _check(load().fsm_result_copy(r, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
+                                  _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64)))
+    return out
+
+
+def fsm_result_stat(r: int, key: str) -> int:
+    v = ctypes.c_int64()
+    _check(load().fsm_result_stat(r, key.encode(), ctypes.byref(v)))
+    return int(v.value)
+
+
+def fsm_free_result(r: int) -> None:
+    if r:
+        load().fsm_free_result(r)
+
+
+def fsm_free_graph(g: int) -> None:
+    if g:
+        load().fsm_free_graph(g)
+
+
+def fsm_debug_dissect(ids, adj_rows):
+    """Host build of the dissection rule: returns (l_mask, join, used_fallback)."""
+    ids = _i32(ids)
+    rows = np.ascontiguousarray(adj_rows, dtype=np.uint32)
+    lm, jn, fb = ctypes.c_uint32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().fsm_debug_dissect(len(ids), _ptr(ids, ctypes.c_int32), _ptr(rows, ctypes.c_uint32),
+                                    ctypes.byref(lm), ctypes.byref(jn), ctypes.byref(fb)))
+    return int(lm.value), int(jn.value), int(fb.value)
+
+
+STATS = ["k", "levels", "candidates", "embeddings", "final_embeddings", "quick_patterns", "patterns",
+         "live_patterns", "frontier_max", "kernel_launches", "time_ns", "final_level_ns",
+         "count_ns", "domain_ns", "emit_ns", "count_launches", "domain_launches", "emit_launches",
+         "count_bytes", "domain_bytes", "emit_bytes"]
+
+
+class Graph:
+    """Owning wrapper of a graph handle."""
+
+    def __init__(self, row_ptr, col, labels, num_labels: int, mode: str = "edge"):
+        self.n = int(len(labels))
+        self.handle = fsm_load_graph(row_ptr, col, labels, self.n, int(num_labels))
+        self.set_mode(mode)
+
+    @classmethod
+    def from_graphgen(cls, g, mode: str = "edge"):
+        return cls(g.row_ptr, g.col, g.labels, g.num_labels, mode)
+
+    def set_mode(self, mode: str):
+        fsm_set_option(self.handle, "mode", {"edge": 0, "vertex": 1}[mode])
+
+    def set_option(self, key: str, value: int):
+        fsm_set_option(self.handle, key, value)
+
+    def mine(self, k: int, t: int, sample_rate: float = 1.0, stats: bool = False):
+        r = fsm_mine(self.handle, k, t, sample_rate)
+        try:
+            out = fsm_result_copy(r, k)
+            if stats:
+                out["stats"] = {s: fsm_result_stat(r, s) for s in STATS}
+        finally:
+            fsm_free_result(r)
+        return out
+
+    def close(self):
+        if self.handle:
+            fsm_free_graph(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

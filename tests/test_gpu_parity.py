@@ -1,0 +1,160 @@
+"""GPU parity: the CUDA library against the CPU oracle, bit-exact (same patterns, same MNI
+supports, same embedding counts), through the C ABI."""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_07690_gb300 import build, fsm as f
+    build.build()
+    f.load()
+    return f
+
+
+def _same(got, exp, ctx=""):
+    assert got["labels"].shape == exp["labels"].shape, f"{ctx}: {got['labels'].shape[0]} patterns vs oracle {exp['labels'].shape[0]}"
+    for key in ("labels", "adj", "support", "count"):
+        if not np.array_equal(got[key], exp[key]):
+            bad = np.nonzero(np.any(np.atleast_2d(got[key] != exp[key]).reshape(len(got["support"]), -1), axis=1))[0][:5]
+            raise AssertionError(f"{ctx}: {key} differs at rows {bad.tolist()}: "
+                                 f"got {got[key][bad].tolist()} expected {exp[key][bad].tolist()}")
+
+
+def check(fsm, g, k, t, mode="edge", options=None):
+    G = fsm.Graph.from_graphgen(g, mode)
+    for key, val in (options or {}).items():
+        G.set_option(key, val)
+    got = G.mine(k, t)
+    G.close()
+    exp = oracle.mine(g, k, t, mode)
+    _same(got, exp, f"k={k} t={t} mode={mode} n={g.n}")
+    return got
+
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_random(fsm, mode, seed):
+    g = gg.random_small(10, 0.35, 1 + seed % 3, seed)
+    for k in range(1, 7):
+        check(fsm, g, k, 1, mode)
+
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+def test_closed_forms(fsm, mode):
+    for k in range(1, 7):
+        check(fsm, gg.complete(7), k, 1, mode)
+        check(fsm, gg.path(12), k, 1, mode)
+        check(fsm, gg.cycle(9), k, 1, mode)
+        check(fsm, gg.star(7), k, 1, mode)
+    check(fsm, gg.complete_bipartite(3, 5), 2, 1, mode)
+    check(fsm, gg.spider(3, 2), 7, 1, mode)
+
+
+def test_complete_graph_pattern_counts(fsm):
+    # edge-induced K_7 at k = 6: all 112 connected 6-vertex graphs, each with sigma = 7
+    got = check(fsm, gg.complete(7), 6, 1, "edge")
+    assert len(got["support"]) == 112 and np.all(got["support"] == 7)
+
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+def test_er1000_config(fsm, mode):
+    """Erdos-Renyi n=1000, average degree 6, 4 uniform labels, threshold 30 (k <= 3), plus k=4."""
+    g = gg.workload("er1000")
+    for k in (1, 2, 3, 4):
+        check(fsm, g, k, 30, mode)
+
+
+@pytest.mark.parametrize("k", [5, 6, 7, 8])
+def test_large_k_sparse(fsm, k):
+    g = gg.erdos_renyi(40, 2.5, seed=k, num_labels=2)
+    for mode in ("edge", "vertex"):
+        check(fsm, g, k, 1, mode)
+        check(fsm, g, k, 3, mode)
+
+
+@pytest.mark.parametrize("t", [2, 6, 20])
+def test_chung_lu_scaled(fsm, t):
+    """Shape of the 100k-vertex Chung-Lu workload (beta 2.1, 29 Zipf labels) at 1/50 scale."""
+    g = gg.workload("cl100k", scale=0.02, cap=60)
+    for k in (3, 4):
+        check(fsm, g, k, t)
+
+
+def test_chunking_and_batching_do_not_change_results(fsm):
+    g = gg.workload("cl100k", scale=0.02, cap=60)
+    ref = check(fsm, g, 4, 6)
+    for opts in ({"chunk": 32}, {"chunk": 65536}, {"batch": 1024}, {"batch": 1024, "chunk": 64}):
+        G = fsm.Graph.from_graphgen(g)
+        for key, val in opts.items():
+            G.set_option(key, val)
+        got = G.mine(4, 6)
+        G.close()
+        _same(got, ref, str(opts))
+
+
+def test_deterministic_and_reusable_handle(fsm):
+    g = gg.workload("er1000")
+    G = fsm.Graph.from_graphgen(g)
+    a = G.mine(4, 10)
+    b = G.mine(4, 10)
+    c = G.mine(3, 30)
+    G.close()
+    for key in a:
+        assert np.array_equal(a[key], b[key])
+    _same(c, oracle.mine(g, 3, 30), "after reuse")
+
+
+def test_vertex_renaming(fsm):
+    g = gg.workload("cl100k", scale=0.01, cap=40)
+    h = gg.relabel_vertices(g, np.random.default_rng(3).permutation(g.n))
+    Gg, Gh = fsm.Graph.from_graphgen(g), fsm.Graph.from_graphgen(h)
+    a, b = Gg.mine(4, 3), Gh.mine(4, 3)
+    Gg.close()
+    Gh.close()
+    for key in a:
+        assert np.array_equal(a[key], b[key])
+
+
+def test_errors(fsm):
+    g = gg.path(5)
+    G = fsm.Graph.from_graphgen(g)
+    with pytest.raises(fsm.FsmError) as e:
+        G.mine(9, 1)
+    assert e.value.code == fsm.FSM_EINVAL
+    with pytest.raises(fsm.FsmError) as e:
+        G.mine(3, 0)
+    assert e.value.code == fsm.FSM_EINVAL
+    with pytest.raises(fsm.FsmError) as e:
+        G.mine(3, 1, sample_rate=0.5)
+    assert e.value.code == fsm.FSM_EUNSUPPORTED
+    with pytest.raises(fsm.FsmError):
+        G.set_option("mode", 2)
+    G.close()
+    # asymmetric CSR
+    with pytest.raises(fsm.FsmError) as e:
+        fsm.fsm_load_graph(np.array([0, 1, 1], np.int32), np.array([1], np.int32), np.zeros(2, np.int32), 2, 1)
+    assert e.value.code == fsm.FSM_EINVAL
+    # unsorted row
+    with pytest.raises(fsm.FsmError) as e:
+        fsm.fsm_load_graph(np.array([0, 2, 3, 4], np.int32), np.array([2, 1, 0, 0], np.int32), np.zeros(3, np.int32), 3, 1)
+    assert e.value.code == fsm.FSM_EINVAL
+
+
+def test_stats(fsm):
+    g = gg.workload("er1000")
+    G = fsm.Graph.from_graphgen(g)
+    r = G.mine(4, 30, stats=True)
+    G.close()
+    s = r["stats"]
+    assert s["levels"] == 2 and s["kernel_launches"] > 0 and s["time_ns"] > 0
+    # every returned embedding was accepted in the last level
+    assert s["final_embeddings"] >= int(r["count"].sum())
