@@ -173,9 +173,9 @@ def run_ours(args, rank, world, local_rank):
 
     def step(profile: bool):
         G.set_option("profile", 1 if profile else 0)
-        tot = {"embeddings": 0, "kernel_launches": 0, "count_ns": 0, "domain_ns": 0, "emit_ns": 0,
-               "count_bytes": 0, "domain_bytes": 0, "emit_bytes": 0, "count_launches": 0,
-               "domain_launches": 0, "emit_launches": 0, "patterns_out": 0, "final_embeddings": 0}
+        tot = {"embeddings": 0, "kernel_launches": 0, "patterns_out": 0, "final_embeddings": 0}
+        tot.update({f"{p}_{f}_l{l}": 0 for p in ("count", "domain", "emit") for f in ("ns", "launches", "bytes")
+                    for l in range(1, 7)})
         for t in ths:
             r = G.mine(args.k, t, stats=True)
             s = r["stats"]
@@ -244,18 +244,19 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": d2h // args.steps, "ms_per_step": 1e3 * t_e2e / args.steps}
 
     # roofline of the dominant extension pass (launch durations from CUDA events in the library)
-    passes = {p: (agg[f"{p}_ns"], agg[f"{p}_bytes"], agg[f"{p}_launches"]) for p in ("count", "domain", "emit")}
-    dom = max(passes, key=lambda p: passes[p][0])
+    passes = {(p, l): (agg[f"{p}_ns_l{l}"], agg[f"{p}_bytes_l{l}"], agg[f"{p}_launches_l{l}"])
+              for p in ("count", "domain", "emit") for l in range(1, 7)}
+    dom = max(passes, key=lambda q: passes[q][0])
     ns, byts, nl = passes[dom]
     peak, peak_kind = read_peaks()
     achieved = (byts / nl) / (ns / nl) if ns > 0 and nl > 0 else 0.0   # bytes per ns == GB/s
-    roofline = {"bound": "hbm", "kernel": f"extend_kernel<L={args.k - 2}, PASS_{dom.upper()}>",
+    roofline = {"bound": "hbm", "kernel": f"extend_kernel<{dom[1]}, PASS_{dom[0].upper()}>",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
-                "traffic": traffic_for(dom), "launches": nl, "avg_launch_ms": round(ns / nl / 1e6, 3) if nl else None,
+                "traffic": traffic_for(f"{dom[0]}_l{dom[1]}"), "launches": nl, "avg_launch_ms": round(ns / nl / 1e6, 3) if nl else None,
                 "algorithmic_bytes_per_launch": byts / nl if nl else None,
                 "share_of_step": round(ns / 1e6 / total_ms, 3) if total_ms else None,
-                "pass_ms": {p: round(v[0] / 1e6 / args.steps, 2) for p, v in passes.items()}}
+                "pass_ms": {f"{p}_l{l}": round(v[0] / 1e6 / args.steps, 2) for (p, l), v in passes.items() if v[2]}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

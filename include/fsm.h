@@ -125,7 +125,8 @@ int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, in
  *   "profile" option also, per extension pass P in {count, domain, emit}: "P_ns" (summed
  *   launch durations), "P_launches", "P_bytes" (algorithmic bytes: 4 * (d(v) + end pieces of v)
  *   per (embedding, key position) unit, 4 * (l + 1) per embedding read, and for emit
- *   4 * (l + 3) per embedding written).
+ *   4 * (l + 3) per embedding written), and the same per extended level size l as
+ *   "P_ns_l<l>", "P_launches_l<l>", "P_bytes_l<l>" (l = 1..6).
  */
 int fsm_result_stat(const fsm_result *r, const char *key, int64_t *value);
 

@@ -154,8 +154,8 @@ struct RunStats {
     int64_t tested = 0, accepted = 0, qps = 0, patterns = 0, live = 0, frontier_max = 0, levels = 0,
             final_accepted = 0, launches = 0;
     // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
-    double pass_ns[3] = {0, 0, 0};
-    int64_t pass_launches[3] = {0, 0, 0}, pass_bytes[3] = {0, 0, 0};
+    double pass_ns[FSM_MAXL + 1][3] = {};
+    int64_t pass_launches[FSM_MAXL + 1][3] = {}, pass_bytes[FSM_MAXL + 1][3] = {};
 };
 
 struct Miner {
@@ -216,7 +216,7 @@ struct Miner {
             if (prof) {
                 ck(cudaMemsetAsync(bsum, 0, sizeof(unsigned long long), st), "memset");
                 ck(launch_unit_bytes(G->row_ptr, G->piece_cnt, in.fv, in.N, e0, ne, L, bsum, st), "unit bytes");
-                rs.pass_bytes[pass] += (int64_t)d2h(bsum, st);
+                rs.pass_bytes[L][pass] += (int64_t)d2h(bsum, st);
                 cudaEvent_t a, b;
                 ck(cudaEventCreate(&a), "event");
                 ck(cudaEventCreate(&b), "event");
@@ -229,14 +229,14 @@ struct Miner {
             ck(e, "extension kernel");
             if (prof) ck(cudaEventRecord(evs.back().second, st), "event record");
             rs.launches += 1;
-            rs.pass_launches[pass] += 1;
+            rs.pass_launches[L][pass] += 1;
         }
         if (prof) {
             ck(cudaStreamSynchronize(st), "sync");
             for (auto &ab : evs) {
                 float ms = 0.f;
                 ck(cudaEventElapsedTime(&ms, ab.first, ab.second), "event time");
-                rs.pass_ns[pass] += (double)ms * 1e6;
+                rs.pass_ns[L][pass] += (double)ms * 1e6;
                 cudaEventDestroy(ab.first);
                 cudaEventDestroy(ab.second);
             }
@@ -398,7 +398,7 @@ struct Miner {
             run_pass(PASS_EMIT, in, A);
             const int64_t wrote = (int64_t)d2h(cursor, st);
             if (wrote != N2) fail(FSM_ECUDA, "frontier emission wrote " + std::to_string(wrote) + " of " + std::to_string(N2));
-            if (G->profile) rs.pass_bytes[PASS_EMIT] += N2 * 4 * (K + 1);
+            if (G->profile) rs.pass_bytes[L][PASS_EMIT] += N2 * 4 * (K + 1);
             rs.frontier_max = std::max(rs.frontier_max, N2);
             mem.release(sum);
             mem.release(cursor);
@@ -695,9 +695,20 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["final_level_ns"] = (int64_t)((double)fms * 1e6);
         const char *pn[3] = {"count", "domain", "emit"};
         for (int p = 0; p < 3; ++p) {
-            r->stats[std::string(pn[p]) + "_ns"] = (int64_t)rs.pass_ns[p];
-            r->stats[std::string(pn[p]) + "_launches"] = rs.pass_launches[p];
-            r->stats[std::string(pn[p]) + "_bytes"] = rs.pass_bytes[p];
+            double ns = 0;
+            int64_t nl = 0, nb = 0;
+            for (int L = 1; L <= FSM_MAXL; ++L) {
+                const std::string sfx = "_l" + std::to_string(L);
+                r->stats[std::string(pn[p]) + "_ns" + sfx] = (int64_t)rs.pass_ns[L][p];
+                r->stats[std::string(pn[p]) + "_launches" + sfx] = rs.pass_launches[L][p];
+                r->stats[std::string(pn[p]) + "_bytes" + sfx] = rs.pass_bytes[L][p];
+                ns += rs.pass_ns[L][p];
+                nl += rs.pass_launches[L][p];
+                nb += rs.pass_bytes[L][p];
+            }
+            r->stats[std::string(pn[p]) + "_ns"] = (int64_t)ns;
+            r->stats[std::string(pn[p]) + "_launches"] = nl;
+            r->stats[std::string(pn[p]) + "_bytes"] = nb;
         }
         *out = r;
         return FSM_OK;

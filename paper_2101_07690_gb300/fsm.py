@@ -176,7 +176,9 @@ def fsm_debug_dissect(ids, adj_rows):
 STATS = ["k", "levels", "candidates", "embeddings", "final_embeddings", "quick_patterns", "patterns",
          "live_patterns", "frontier_max", "kernel_launches", "time_ns", "final_level_ns",
          "count_ns", "domain_ns", "emit_ns", "count_launches", "domain_launches", "emit_launches",
-         "count_bytes", "domain_bytes", "emit_bytes"]
+         "count_bytes", "domain_bytes", "emit_bytes"] + [
+             f"{p}_{f}_l{l}" for p in ("count", "domain", "emit") for f in ("ns", "launches", "bytes")
+             for l in range(1, 7)]
 
 
 class Graph:
