@@ -113,23 +113,24 @@ class Clocks:
 # ----------------------------------------------------------------------------- CPU oracle sample
 
 def oracle_sample(g, k: int, target_s: float):
-    """Time the oracle (as it stands, one thread) on the connected k-subgraphs whose smallest
-    vertex id is below R, R grown until a run lasts about target_s seconds."""
+    """Time the oracle (as it stands, one thread) on a bounded sample of the workload: ESU from
+    the lowest vertex ids upward, stopped after E embeddings, E sized from a short calibration
+    run so the timed run lasts about target_s seconds."""
     import oracle
     oracle.build()
-    R = 16
-    while True:
-        t0 = time.perf_counter()
-        o = oracle.mine(g, k, 1, roots=(0, R))
-        dt = time.perf_counter() - t0
-        if dt >= target_s * 0.6 or R >= g.n:
-            emb = int(o["count"].sum())
-            return {"value": emb / dt, "unit": "embeddings/s", "cores": 1, "kind": "oracle",
-                    "sample": f"all connected {k}-vertex embeddings whose smallest vertex id is < {R} "
-                              f"({R}/{g.n} ESU roots): {emb} embeddings in {dt:.2f} s",
-                    "seconds": dt, "roots": R, "embeddings": emb}
-        grow = target_s / max(dt, 1e-3)
-        R = min(g.n, max(R * 2, int(R * min(grow, 16))))
+    E = 20000
+    t0 = time.perf_counter()
+    oracle.mine(g, k, 1, max_embeddings=E)
+    rate = E / max(time.perf_counter() - t0, 1e-3)
+    E = max(E, int(rate * target_s))
+    t0 = time.perf_counter()
+    o = oracle.mine(g, k, 1, max_embeddings=E)
+    dt = time.perf_counter() - t0
+    emb = int(o["count"].sum())
+    return {"value": emb / dt, "unit": "embeddings/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {emb} connected {k}-vertex embeddings in ESU order from the lowest vertex "
+                      f"ids of the same graph (edge-induced, every pattern); {dt:.2f} s on one host core",
+            "seconds": dt, "embeddings": emb}
 
 
 def read_peaks():

@@ -52,7 +52,7 @@ def _load():
             lib.oracle_mine.restype = ctypes.c_void_p
             lib.oracle_mine.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
                                         P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32,
-                                        ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
+                                        ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
             lib.oracle_result_count.restype = ctypes.c_int64
             lib.oracle_result_count.argtypes = [ctypes.c_void_p]
             lib.oracle_result_copy.restype = None
@@ -71,11 +71,14 @@ def _ptr(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
-def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = None) -> dict:
+def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = None,
+         max_embeddings: int = 0) -> dict:
     """All k-vertex patterns of graph ``g`` with MNI support >= t.
 
     ``roots=(b, e)`` restricts the enumeration to connected sets whose smallest vertex id is
-    in [b, e) (a bounded sample of the work; supports are then those of the sample).
+    in [b, e); ``max_embeddings > 0`` stops after that many embeddings (roots taken in
+    ascending order).  Both give a bounded sample of the work, whose supports are those of the
+    sample.
     Returns a dict of numpy arrays: labels (P, k) int32, adj (P,) uint64, support (P,) int64,
     count (P,) int64 (number of embeddings of each pattern)."""
     lib = _load()
@@ -86,7 +89,8 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
         raise ValueError("oracle labels must lie in [0, 255]")
     b, e = (0, g.n) if roots is None else roots
     res = lib.oracle_mine(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
-                          _ptr(labels, ctypes.c_int32), k, MODES[mode], int(t), int(b), int(e))
+                          _ptr(labels, ctypes.c_int32), k, MODES[mode], int(t), int(b), int(e),
+                          int(max_embeddings))
     if not res:
         raise ValueError("oracle_mine rejected its arguments")
     try:

@@ -161,6 +161,8 @@ typedef struct {
     int k, mode;
     const int32_t *row_ptr, *col, *labels;
     int32_t n;
+    int64_t budget, seen;           /* stop after `budget` embeddings (<= 0: no limit) */
+    int stop;
     canon_ctx_t cx;
     pattern_t *pat; int64_t npat, cappat;
     /* pattern lookup by canonical code: open addressing over indices */
@@ -282,6 +284,8 @@ static int spans_connected(int k, const uint32_t *adjrow) {
 }
 
 static void record(oracle_t *o, const int32_t *u, const int32_t *lab, const uint32_t *adjrow) {
+    if (o->stop) return;
+    if (o->budget > 0 && ++o->seen >= o->budget) o->stop = 1;
     memo_t *m = canonical(o, lab, adjrow);
     pattern_t *p = &o->pat[m->pattern];
     p->count++;
@@ -326,10 +330,11 @@ static void process_set(oracle_t *o, const int32_t *vs) {
 
 static void esu_extend(oracle_t *o, int32_t *sub, int depth, const int32_t *ext, int64_t next,
                        int32_t root) {
+    if (o->stop) return;
     if (depth == o->k) { process_set(o, sub); return; }
     if (next == 0) return;
     /* extension array for children: at most next - 1 + deg(w) entries */
-    for (int64_t idx = next - 1; idx >= 0; idx--) {
+    for (int64_t idx = next - 1; idx >= 0 && !o->stop; idx--) {
         int32_t w = ext[idx];
         int64_t deg = o->row_ptr[w + 1] - o->row_ptr[w];
         int32_t *ext2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(idx + deg + 1));
@@ -369,21 +374,23 @@ static int idx_cmp(const void *a, const void *b) {
  * oracle_mine: every pattern of exactly k vertices with MNI support >= t.
  *   mode 0 = edge-induced, 1 = vertex-induced.  Only connected sets whose smallest vertex lies
  *   in [root_begin, root_end) are enumerated (the full graph: 0, n); a partial range gives a
- *   bounded sample of the work.  Returns NULL on bad arguments.
+ *   bounded sample of the work, and so does max_embeddings > 0, which stops the enumeration
+ *   (roots in ascending order) after that many embeddings.  Returns NULL on bad arguments.
  */
 oracle_result_t *oracle_mine(int32_t n, const int32_t *row_ptr, const int32_t *col,
                              const int32_t *labels, int32_t k, int32_t mode, int64_t t,
-                             int32_t root_begin, int32_t root_end) {
+                             int32_t root_begin, int32_t root_end, int64_t max_embeddings) {
     if (k < 1 || k > OR_MAXK || n < 0 || (mode != 0 && mode != 1)) return NULL;
     oracle_t o;
     memset(&o, 0, sizeof(o));
     o.k = k; o.mode = mode; o.row_ptr = row_ptr; o.col = col; o.labels = labels; o.n = n;
+    o.budget = max_embeddings;
     o.cx.k = k;
     gen_perms(&o.cx);
     if (root_begin < 0) root_begin = 0;
     if (root_end > n) root_end = n;
     int32_t sub[OR_MAXK];
-    for (int32_t v = root_begin; v < root_end; v++) {
+    for (int32_t v = root_begin; v < root_end && !o.stop; v++) {
         sub[0] = v;
         int64_t deg = row_ptr[v + 1] - row_ptr[v];
         int32_t *ext = (int32_t *)malloc(sizeof(int32_t) * (size_t)(deg + 1));

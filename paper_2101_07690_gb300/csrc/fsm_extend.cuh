@@ -120,18 +120,43 @@ __device__ __forceinline__ bool in_s(const int32_t (&S)[L], int32_t x) {
 
 struct Tally { unsigned long long tested, accepted; };
 
+// Per-block aggregation of quick-pattern counts (PASS_COUNT).  Hot keys (the dominant label
+// patterns) would otherwise serialise on one global counter; each block sums them in shared
+// memory and flushes once when the persistent loop ends.
+#define FSM_SMEM_SLOTS 1024
+#define FSM_SMEM_PROBES 16
+struct CountCache {
+    unsigned long long key[FSM_SMEM_SLOTS];
+    unsigned long long cnt[FSM_SMEM_SLOTS];
+};
+
+__device__ __forceinline__ void count_key(const ExtArgs &A, CountCache *cc, uint64_t key, unsigned n) {
+    uint32_t h = (uint32_t)mix64(key) & (FSM_SMEM_SLOTS - 1);
+    for (int probe = 0; probe < FSM_SMEM_PROBES; ++probe) {
+        unsigned long long cur = cc->key[h];
+        if (cur == FSM_EMPTY_KEY) cur = atomicCAS(cc->key + h, FSM_EMPTY_KEY, key);
+        if (cur == FSM_EMPTY_KEY || cur == key) {
+            atomicAdd(cc->cnt + h, (unsigned long long)n);
+            return;
+        }
+        h = (h + 1) & (FSM_SMEM_SLOTS - 1);
+    }
+    int64_t slot = qp_insert(A.qp, key, A.err);
+    if (slot >= 0) atomicAdd(A.qp.count + slot, (unsigned long long)n);
+}
+
 // One accepted join: act according to PASS.
+struct DomCache { uint32_t *w; uint32_t bits; };
+
 template <int L, int PASS>
-__device__ __forceinline__ void accept(const ExtArgs &A, uint64_t key, const int32_t (&gid)[L + 2]) {
+__device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCache &dc, uint64_t key,
+                                       const int32_t (&gid)[L + 2]) {
     constexpr int K = L + 2;
     if (PASS == PASS_COUNT) {
         const unsigned act = __activemask();
         const unsigned grp = __match_any_sync(act, key);
         const int lane = threadIdx.x & 31;
-        if (lane == __ffs(grp) - 1) {
-            int64_t slot = qp_insert(A.qp, key, A.err);
-            if (slot >= 0) atomicAdd(A.qp.count + slot, (unsigned long long)__popc(grp));
-        }
+        if (lane == __ffs(grp) - 1) count_key(A, cc, key, __popc(grp));
         return;
     }
     int64_t slot = qp_find(A.qp, key);
@@ -149,7 +174,10 @@ __device__ __forceinline__ void accept(const ExtArgs &A, uint64_t key, const int
             const int32_t r = __ldg(A.g.rank + gid[h]);
             uint32_t *w = A.dom + off + (r >> 5);
             const uint32_t bit = 1u << (r & 31);
+            if (w == dc.w && (dc.bits & bit)) continue;   // this lane set it already
             if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+            if (w != dc.w) { dc.w = w; dc.bits = 0; }
+            dc.bits |= bit;
         }
     } else {  // PASS_EMIT
         const int32_t nid = __ldg(A.newid + P);
@@ -177,7 +205,8 @@ __device__ __forceinline__ void accept(const ExtArgs &A, uint64_t key, const int
 template <int L, int PASS>
 __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                            uint64_t srows, int32_t pid, int i, int shape,
-                                           const int32_t (&pv)[3], const int (&pl)[3], Tally &tl) {
+                                           const int32_t (&pv)[3], const int (&pl)[3], Tally &tl,
+                                           CountCache *cc, DomCache &dc) {
     constexpr int K = L + 2;
     const uint32_t pidx = piece_index(shape, pl[0], pl[1], pl[2]);
     if (A.piece_freq && !__ldg(A.piece_freq + pidx)) return;
@@ -244,7 +273,7 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
         }
         if (keep) {
             ++tl.accepted;
-            accept<L, PASS>(A, make_key((uint32_t)pid, pidx, i, jpos, sub), gid);
+            accept<L, PASS>(A, cc, dc, make_key((uint32_t)pid, pidx, i, jpos, sub), gid);
         }
         if (A.mode == 1 || sub == 0) break;
         sub = (sub - 1) & avail;
@@ -253,7 +282,8 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
 
 template <int L, int PASS>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
-                                         uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl) {
+                                         uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
+                                         CountCache *cc, DomCache &dc) {
     const DevGraph &g = A.g;
     const int32_t v = S[i];
     const int32_t rp = __ldg(g.row_ptr + v);
@@ -276,7 +306,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             pv[0] = v; pl[0] = SL[i];
             if (lab_id_less(la, a, lb, b)) { pv[1] = a; pl[1] = la; pv[2] = b; pl[2] = lb; }
             else { pv[1] = b; pl[1] = lb; pv[2] = a; pl[2] = la; }
-            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl);
+            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
         }
         if (tri) {
             int32_t t0 = v, t1 = a, t2 = b;
@@ -287,7 +317,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
             pv[0] = t0; pv[1] = t1; pv[2] = t2;
             pl[0] = m0; pl[1] = m1; pl[2] = m2;
-            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_TRI, pv, pl, tl);
+            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_TRI, pv, pl, tl, cc, dc);
         }
     } else {
         const int64_t lq2 = lq - nc;
@@ -306,7 +336,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         pv[0] = a; pl[0] = la;
         if (lab_id_less(SL[i], v, lb, b)) { pv[1] = v; pl[1] = SL[i]; pv[2] = b; pl[2] = lb; }
         else { pv[1] = b; pl[1] = lb; pv[2] = v; pl[2] = SL[i]; }
-        join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl);
+        join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
     }
 }
 
@@ -315,6 +345,16 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t nunits = A.ne * L;
     Tally tl{0ull, 0ull};
+    DomCache dc{nullptr, 0u};
+    extern __shared__ unsigned long long dyn_smem[];   // CountCache in PASS_COUNT launches
+    CountCache *cc = PASS == PASS_COUNT ? reinterpret_cast<CountCache *>(dyn_smem) : nullptr;
+    if (PASS == PASS_COUNT) {
+        for (int x = threadIdx.x; x < FSM_SMEM_SLOTS; x += blockDim.x) {
+            cc->key[x] = FSM_EMPTY_KEY;
+            cc->cnt[x] = 0ull;
+        }
+        __syncthreads();
+    }
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) c = atomicAdd(A.chunk_ctr, 1ull);
@@ -350,7 +390,16 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
                 ub = __ldg(A.unit_base + u);
             }
-            do_piece<L, PASS>(A, S, SL, srows, pid, i, q - ub, tl);
+            do_piece<L, PASS>(A, S, SL, srows, pid, i, q - ub, tl, cc, dc);
+        }
+    }
+    if (PASS == PASS_COUNT) {
+        __syncthreads();
+        for (int x = threadIdx.x; x < FSM_SMEM_SLOTS; x += blockDim.x) {
+            const unsigned long long key = cc->key[x];
+            if (key == FSM_EMPTY_KEY) continue;
+            int64_t slot = qp_insert(A.qp, key, A.err);
+            if (slot >= 0) atomicAdd(A.qp.count + slot, cc->cnt[x]);
         }
     }
     // per-warp totals, one atomic per warp
