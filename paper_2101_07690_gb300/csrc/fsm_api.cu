@@ -110,6 +110,7 @@ struct fsm_graph {
     int32_t chunk = 0;
     int64_t batch = 0;
     int sms = 0;
+    int64_t qp_hint[FSM_MAXL + 1] = {};   // distinct quick patterns seen at each level last time
     int32_t *row_ptr = nullptr, *col = nullptr, *labels = nullptr, *rank = nullptr, *cls_size = nullptr,
             *end_off = nullptr;
     int64_t *piece_cnt = nullptr;
@@ -175,13 +176,39 @@ struct Miner {
         return G->sms * bps;
     }
 
-    // Run one pass of the extension kernel over every batch of the frontier.
-    void run_pass(int pass, const LevelSet &in, ExtArgs A) {
+    // Profiling records: one event pair per timed region, read after the call's last sync.
+    struct ProfEv { cudaEvent_t a, b; int L, pass; };
+    std::vector<ProfEv> prof_ev;
+    unsigned long long *prof_bytes = nullptr;   // [(FSM_MAXL + 1) * 3] algorithmic bytes, device
+
+    struct Range { int64_t e0, ne; };
+
+    // Run one pass of the extension kernel over the frontier.
+    //   launch 0: batches of at most `batch` embeddings, each sized on the host;
+    //   launch 1: one persistent work-stealing launch over the whole frontier (sizes stay on the
+    //             device), captured with its prefix kernels into a CUDA graph;
+    //   launch 2: one launch per frontier pattern (the frontier grouped by pattern id), all
+    //             captured into one CUDA graph.
+    void run_pass(int pass, const LevelSet &in, ExtArgs A, const std::vector<int64_t> &pat_off) {
         const int L = in.L;
         if (in.N == 0) return;
         int64_t B = G->batch > 0 ? G->batch : std::max<int64_t>(1024, ((int64_t)1 << 24) / L);
-        B = std::min(B, in.N);
-        const int64_t maxu = B * L;
+        std::vector<Range> ranges;
+        bool device_total = false;
+        if (G->launch == 2 && (int64_t)pat_off.size() == in.P + 1) {
+            for (int64_t p = 0; p < in.P; ++p)
+                for (int64_t e0 = pat_off[p]; e0 < pat_off[p + 1]; e0 += B)
+                    ranges.push_back({e0, std::min(B, pat_off[p + 1] - e0)});
+            device_total = true;
+        } else if (G->launch == 1 && in.N * L <= ((int64_t)1 << 27)) {
+            ranges.push_back({0, in.N});
+            device_total = true;
+        } else {
+            for (int64_t e0 = 0; e0 < in.N; e0 += B) ranges.push_back({e0, std::min(B, in.N - e0)});
+        }
+        int64_t maxne = 0;
+        for (auto &r : ranges) maxne = std::max(maxne, r.ne);
+        const int64_t maxu = maxne * L;
         int64_t *cnt = mem.get<int64_t>(maxu);
         int64_t *base = mem.get<int64_t>(maxu + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(maxu) + 16);
@@ -189,58 +216,77 @@ struct Miner {
         const int grid = grid_for(L, pass);
         const int64_t warps = (int64_t)grid * 8;
         const bool prof = G->profile != 0;
-        unsigned long long *bsum = prof ? mem.get<unsigned long long>(1) : nullptr;
-        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> evs;
-        for (int64_t e0 = 0; e0 < in.N; e0 += B) {
-            const int64_t ne = std::min(B, in.N - e0);
-            ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, e0, ne, L, cnt, st), "unit counts");
-            ck(launch_scan_i64(cnt, base, ne * L, tmp, st), "unit scan");
-            const int64_t total = d2h(base + ne * L, st);
-            if (total == 0) continue;
-            int64_t chunk = G->chunk;
-            if (chunk <= 0) {
-                chunk = 256;
-                while (chunk < 16384 && total / chunk > warps * 64) chunk <<= 1;
-            }
-            A.fv = in.fv;
-            A.fpid = in.fpid;
-            A.fN = in.N;
-            A.e0 = e0;
-            A.ne = ne;
-            A.unit_base = base;
-            A.total = total;
-            A.chunk = (int32_t)chunk;
-            A.nchunks = (total + chunk - 1) / chunk;
-            A.chunk_ctr = ctr;
-            ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
-            if (prof) {
-                ck(cudaMemsetAsync(bsum, 0, sizeof(unsigned long long), st), "memset");
-                ck(launch_unit_bytes(G->row_ptr, G->piece_cnt, in.fv, in.N, e0, ne, L, bsum, st), "unit bytes");
-                rs.pass_bytes[L][pass] += (int64_t)d2h(bsum, st);
-                cudaEvent_t a, b;
-                ck(cudaEventCreate(&a), "event");
-                ck(cudaEventCreate(&b), "event");
-                evs.emplace_back(a, b);
-                ck(cudaEventRecord(a, st), "event record");
-            }
+        A.fv = in.fv;
+        A.fpid = in.fpid;
+        A.fN = in.N;
+        A.unit_base = base;
+        A.chunk_ctr = ctr;
+        auto launch_ext = [&]() {
             cudaError_t e = pass == PASS_COUNT ? launch_extend_count(L, A, grid, st)
                           : pass == PASS_DOMAIN ? launch_extend_domain(L, A, grid, st)
                                                 : launch_extend_emit(L, A, grid, st);
             ck(e, "extension kernel");
-            if (prof) ck(cudaEventRecord(evs.back().second, st), "event record");
             rs.launches += 1;
             rs.pass_launches[L][pass] += 1;
-        }
-        if (prof) {
-            ck(cudaStreamSynchronize(st), "sync");
-            for (auto &ab : evs) {
-                float ms = 0.f;
-                ck(cudaEventElapsedTime(&ms, ab.first, ab.second), "event time");
-                rs.pass_ns[L][pass] += (double)ms * 1e6;
-                cudaEventDestroy(ab.first);
-                cudaEventDestroy(ab.second);
+        };
+        auto bytes = [&](const Range &r) {
+            if (prof) ck(launch_unit_bytes(G->row_ptr, G->piece_cnt, in.fv, in.N, r.e0, r.ne, L,
+                                           prof_bytes + L * 3 + pass, st), "unit bytes");
+        };
+        auto new_ev = [&]() {
+            ProfEv ev{nullptr, nullptr, L, pass};
+            ck(cudaEventCreate(&ev.a), "event");
+            ck(cudaEventCreate(&ev.b), "event");
+            prof_ev.push_back(ev);
+            return prof_ev.size() - 1;
+        };
+        if (device_total) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+            for (const Range &r : ranges) {
+                ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
+                ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
+                bytes(r);
+                ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
+                A.e0 = r.e0;
+                A.ne = r.ne;
+                A.total = -1;
+                A.nchunks = 0;
+                A.chunk = G->chunk;
+                launch_ext();
             }
-            mem.release(bsum);
+            ck(cudaStreamEndCapture(st, &graph), "end capture");
+            ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+            size_t ei = prof ? new_ev() : 0;
+            if (prof) ck(cudaEventRecord(prof_ev[ei].a, st), "event record");
+            ck(cudaGraphLaunch(exec, st), "graph launch");
+            if (prof) ck(cudaEventRecord(prof_ev[ei].b, st), "event record");
+            ck(cudaGraphExecDestroy(exec), "graph destroy");
+            ck(cudaGraphDestroy(graph), "graph destroy");
+        } else {
+            for (const Range &r : ranges) {
+                ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
+                ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
+                const int64_t total = d2h(base + r.ne * L, st);
+                if (total == 0) continue;
+                bytes(r);
+                int64_t chunk = G->chunk;
+                if (chunk <= 0) {
+                    chunk = 256;
+                    while (chunk < 16384 && total / chunk > warps * 64) chunk <<= 1;
+                }
+                A.e0 = r.e0;
+                A.ne = r.ne;
+                A.total = total;
+                A.chunk = (int32_t)chunk;
+                A.nchunks = (total + chunk - 1) / chunk;
+                ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
+                size_t ei = prof ? new_ev() : 0;
+                if (prof) ck(cudaEventRecord(prof_ev[ei].a, st), "event record");
+                launch_ext();
+                if (prof) ck(cudaEventRecord(prof_ev[ei].b, st), "event record");
+            }
         }
         mem.release(cnt);
         mem.release(base);
@@ -248,10 +294,36 @@ struct Miner {
         mem.release(ctr);
     }
 
+    // Frontier grouped by pattern id (launch mode 2): returns host offsets, P+1 entries.
+    std::vector<int64_t> group_by_pattern(LevelSet &in) {
+        std::vector<int64_t> off;
+        if (G->launch != 2 || in.N == 0 || in.P == 0) return off;
+        int64_t *cnt = mem.get<int64_t>(in.P);
+        int64_t *doff = mem.get<int64_t>(in.P + 1);
+        void *tmp = mem.get<char>((int64_t)scan_temp_bytes(in.P) + 16);
+        unsigned long long *cur = mem.get<unsigned long long>(in.P);
+        ck(launch_u64_to_i64(in.count, cnt, in.P, st), "counts");
+        ck(launch_scan_i64(cnt, doff, in.P, tmp, st), "pattern offsets");
+        ck(cudaMemsetAsync(cur, 0, sizeof(unsigned long long) * in.P, st), "memset");
+        int32_t *nv = mem.get<int32_t>(in.N * in.L);
+        int32_t *np = mem.get<int32_t>(in.N);
+        ck(launch_group_by_pattern(in.fv, in.fpid, in.N, in.L, doff, cur, nv, np, st), "group by pattern");
+        off.resize((size_t)in.P + 1);
+        ck(cudaMemcpyAsync(off.data(), doff, sizeof(int64_t) * (in.P + 1), cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaStreamSynchronize(st), "sync");
+        if (off[(size_t)in.P] != in.N) fail(FSM_ECUDA, "frontier pattern counts do not add up");
+        in.fv = nv;
+        in.fpid = np;
+        for (void *p : {(void *)cnt, (void *)doff, tmp, (void *)cur}) mem.release(p);
+        return off;
+    }
+
     int err_word() { return d2h(G->err, st); }
 
     // Extend `in` (size L) to size L+2.  piece_freq == nullptr at the size-3 level.
-    LevelSet extend(const LevelSet &in, const uint8_t *piece_freq, bool final) {
+    LevelSet extend(const LevelSet &in_level, const uint8_t *piece_freq, bool final) {
+        LevelSet in = in_level;
+        const std::vector<int64_t> pat_off = group_by_pattern(in);
         const int L = in.L, K = L + 2;
         LevelSet out;
         out.L = K;
@@ -263,7 +335,8 @@ struct Miner {
         A.piece_freq = piece_freq;
         A.err = G->err;
         // ---- pass 1: quick patterns and their embedding counts
-        int64_t cap = (int64_t)1 << 16;
+        int64_t cap = (int64_t)1 << 20;
+        while (cap < 4 * G->qp_hint[L] && cap < ((int64_t)1 << 30)) cap <<= 1;
         unsigned long long *keys = nullptr, *qcount = nullptr, *used = nullptr;
         for (;;) {
             keys = mem.get<unsigned long long>(cap);
@@ -280,7 +353,7 @@ struct Miner {
             A.qp.used = used;
             A.qp.max_used = (unsigned long long)(cap / 2);
             A.stats = G->stats;
-            run_pass(PASS_COUNT, in, A);
+            run_pass(PASS_COUNT, in, A, pat_off);
             const int ew = err_word();
             if (ew & FSM_ERR_QP_OVERFLOW) {
                 mem.release(keys);
@@ -306,6 +379,7 @@ struct Miner {
         ck(launch_qp_compact(keys, cap, slots, nq_d, st), "compact");
         const int64_t nq = (int64_t)d2h(nq_d, st);
         rs.qps += nq;
+        G->qp_hint[L] = std::max(G->qp_hint[L], nq);
         int32_t *qpat = mem.get<int32_t>(cap);
         uint32_t *qperm = mem.get<uint32_t>(cap);
         int64_t M = 1;
@@ -357,7 +431,7 @@ struct Miner {
         A.dom_off = doff;
         A.dom = dom;
         A.stats = nullptr;
-        if (rs.live > 0) run_pass(PASS_DOMAIN, in, A);
+        if (rs.live > 0) run_pass(PASS_DOMAIN, in, A, pat_off);
         unsigned long long *sigma = mem.get<unsigned long long>(np);
         ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
         ck(launch_support(K, orbit, live, doff, words, dom, np, sigma, st), "support");
@@ -395,10 +469,10 @@ struct Miner {
             A.out_pid = out.fpid;
             A.out_N = N2;
             A.out_cursor = cursor;
-            run_pass(PASS_EMIT, in, A);
+            run_pass(PASS_EMIT, in, A, pat_off);
             const int64_t wrote = (int64_t)d2h(cursor, st);
             if (wrote != N2) fail(FSM_ECUDA, "frontier emission wrote " + std::to_string(wrote) + " of " + std::to_string(N2));
-            if (G->profile) rs.pass_bytes[L][PASS_EMIT] += N2 * 4 * (K + 1);
+            if (G->profile) rs.pass_bytes[L][PASS_EMIT] += N2 * 4 * (K + 1);   // output written
             rs.frontier_max = std::max(rs.frontier_max, N2);
             mem.release(sum);
             mem.release(cursor);
@@ -644,6 +718,10 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         {
             Arena mem(st);
             Miner m{g, st, mem, min_support, rs};
+            if (g->profile) {
+                m.prof_bytes = mem.get<unsigned long long>((FSM_MAXL + 1) * 3);
+                ck(cudaMemsetAsync(m.prof_bytes, 0, sizeof(unsigned long long) * (FSM_MAXL + 1) * 3, st), "memset");
+            }
             LevelSet res;
             if (k == 1) {
                 res = m.level1(false);
@@ -673,6 +751,22 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
             }
             ck(cudaEventRecord(ev1, st), "event record");
             fill_result(r, res, k, st);
+            if (g->profile) {
+                unsigned long long pb[(FSM_MAXL + 1) * 3];
+                ck(cudaMemcpyAsync(pb, m.prof_bytes, sizeof(pb), cudaMemcpyDeviceToHost, st), "copy");
+                ck(cudaStreamSynchronize(st), "sync");
+                for (int L = 0; L <= FSM_MAXL; ++L)
+                    for (int p = 0; p < 3; ++p) rs.pass_bytes[L][p] += (int64_t)pb[L * 3 + p];
+                for (auto &ev : m.prof_ev) {
+                    float ems = 0.f;
+                    ck(cudaEventElapsedTime(&ems, ev.a, ev.b), "event time");
+                    rs.pass_ns[ev.L][ev.pass] += (double)ems * 1e6;
+                }
+            }
+            for (auto &ev : m.prof_ev) {
+                cudaEventDestroy(ev.a);
+                cudaEventDestroy(ev.b);
+            }
         }
         ck(cudaStreamSynchronize(st), "sync");
         float ms = 0.f, fms = 0.f;

@@ -46,9 +46,9 @@ struct ExtArgs {
     const int32_t *fpid;
     int64_t fN, e0, ne;
     const int64_t *unit_base;      // [ne*L + 1] exclusive prefix of pieces per unit
-    int64_t total;                 // pieces in this batch
-    int64_t nchunks;
-    int32_t chunk;                 // pieces per chunk
+    int64_t total;                 // pieces in this batch; < 0: read unit_base[ne*L] on the device
+    int64_t nchunks;               // ignored when total < 0
+    int32_t chunk;                 // pieces per chunk; <= 0 with total < 0: sized on the device
     unsigned long long *chunk_ctr;
     // size-l pattern table (frequent patterns of the level being extended)
     const uint64_t *pat_adj;       // [P] 8 adjacency rows (one byte each) over canonical positions
@@ -79,9 +79,13 @@ __device__ __forceinline__ int64_t last_le(const int64_t *base, int64_t lo, int6
     return lo;
 }
 
+// Linear probing stops after FSM_MAX_PROBES slots: at load <= 1/2 a run that long means the
+// table is too small, so the pass is flagged, abandoned and repeated with a larger table.
+#define FSM_MAX_PROBES 256
+
 __device__ __forceinline__ int64_t qp_insert(const QPTab &t, uint64_t key, int *err) {
     uint64_t h = mix64(key) & t.mask;
-    for (uint64_t probe = 0; probe <= t.mask; ++probe) {
+    for (uint64_t probe = 0; probe <= t.mask && probe < FSM_MAX_PROBES; ++probe) {
         unsigned long long cur = __ldcg(t.keys + h);
         if (cur == key) return (int64_t)h;
         if (cur == FSM_EMPTY_KEY) {
@@ -355,13 +359,28 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
         }
         __syncthreads();
     }
+    int64_t total = A.total, nchunks = A.nchunks, chunk = A.chunk;
+    if (total < 0) {
+        // device-resident size: no host round trip between the prefix sum and this launch
+        total = __ldg(A.unit_base + nunits);
+        if (chunk <= 0) {
+            const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+            chunk = 256;
+            while (chunk < 16384 && total / chunk > warps * 64) chunk <<= 1;
+        }
+        nchunks = (total + chunk - 1) / chunk;
+    }
     for (;;) {
         unsigned long long c = 0;
-        if (lane == 0) c = atomicAdd(A.chunk_ctr, 1ull);
+        if (lane == 0) {
+            // an overflowing count pass is repeated with a larger table: stop early
+            if (PASS == PASS_COUNT && (*(volatile int *)A.err & FSM_ERR_QP_OVERFLOW)) c = ~0ull;
+            else c = atomicAdd(A.chunk_ctr, 1ull);
+        }
         c = __shfl_sync(0xffffffffu, c, 0);
-        if (c >= (unsigned long long)A.nchunks) break;
-        const int64_t q0 = (int64_t)c * A.chunk;
-        const int64_t q1 = min(q0 + (int64_t)A.chunk, A.total);
+        if (c >= (unsigned long long)nchunks) break;
+        const int64_t q0 = (int64_t)c * chunk;
+        const int64_t q1 = min(q0 + chunk, total);
         int64_t ulo = 0, uhi = 0;
         if (lane == 0) {
             ulo = last_le(A.unit_base, 0, nunits - 1, q0);

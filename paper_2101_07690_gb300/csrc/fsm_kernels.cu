@@ -236,6 +236,36 @@ cudaError_t launch_unit_bytes(const int32_t *row_ptr, const int64_t *piece_cnt, 
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void group_kernel(const int32_t *fv, const int32_t *fpid, int64_t N, int L, const int64_t *off,
+                             unsigned long long *cursor, int32_t *out_v, int32_t *out_pid) {
+    for (int64_t e = gtid(); e < N; e += gstride()) {
+        const int32_t p = fpid[e];
+        const int64_t pos = off[p] + (int64_t)atomicAdd(cursor + p, 1ull);
+        for (int c = 0; c < L; ++c) out_v[(int64_t)c * N + pos] = fv[(int64_t)c * N + e];
+        out_pid[pos] = p;
+    }
+}
+__global__ void u64_to_i64_kernel(const unsigned long long *in, int64_t *out, int64_t n) {
+    for (int64_t i = gtid(); i < n; i += gstride()) out[i] = (int64_t)in[i];
+}
+} // namespace
+
+cudaError_t launch_group_by_pattern(const int32_t *fv, const int32_t *fpid, int64_t N, int L, const int64_t *off,
+                                    unsigned long long *cursor, int32_t *out_v, int32_t *out_pid, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    group_kernel<<<blocks_for(N), kThreads, 0, st>>>(fv, fpid, N, L, off, cursor, out_v, out_pid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_u64_to_i64(const unsigned long long *in, int64_t *out, int64_t n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    u64_to_i64_kernel<<<blocks_for(n), kThreads, 0, st>>>(in, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t st) {
     LAUNCHED(1);
     fill_u64_kernel<<<blocks_for(n), kThreads, 0, st>>>(p, v, n);

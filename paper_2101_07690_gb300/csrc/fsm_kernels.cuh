@@ -34,6 +34,12 @@ cudaError_t launch_unit_counts(const int64_t *piece_cnt, const int32_t *fv, int6
 cudaError_t launch_unit_bytes(const int32_t *row_ptr, const int64_t *piece_cnt, const int32_t *fv, int64_t fN,
                               int64_t e0, int64_t ne, int L, unsigned long long *sum, cudaStream_t st);
 
+// Group a stored frontier by pattern id: offsets = exclusive prefix of counts[P] (P+1 entries),
+// then every embedding is copied to off[pid] + (arrival order within its pattern).
+cudaError_t launch_group_by_pattern(const int32_t *fv, const int32_t *fpid, int64_t N, int L, const int64_t *off,
+                                    unsigned long long *cursor, int32_t *out_v, int32_t *out_pid, cudaStream_t st);
+cudaError_t launch_u64_to_i64(const unsigned long long *in, int64_t *out, int64_t n, cudaStream_t st);
+
 // ---- quick-pattern table
 cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t n, cudaStream_t st);
 cudaError_t launch_qp_compact(const unsigned long long *keys, int64_t cap, int64_t *slots,

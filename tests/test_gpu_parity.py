@@ -173,3 +173,30 @@ def test_stats(fsm):
     assert s["levels"] == 2 and s["kernel_launches"] > 0 and s["time_ns"] > 0
     # every returned embedding was accepted in the last level
     assert s["final_embeddings"] >= int(r["count"].sum())
+
+
+@pytest.mark.parametrize("launch", [0, 1, 2])
+def test_launch_modes_identical(fsm, launch):
+    """Batched, persistent (one work-stealing launch per pass, CUDA-graph captured) and
+    per-pattern launches give the oracle's result."""
+    cases = [(gg.workload("er1000"), 4, 10), (gg.workload("er1000"), 5, 10),
+             (gg.workload("cl100k", scale=0.005, cap=30), 4, 6),
+             (gg.erdos_renyi(40, 2.5, seed=7, num_labels=2), 7, 2)]
+    for g, k, t in cases:
+        opts = {"launch": launch}
+        check(fsm, g, k, t, "edge", opts)
+        check(fsm, g, k, t, "edge", dict(opts, batch=1024, chunk=64))
+        check(fsm, g, k, t, "vertex", opts)
+
+
+def test_profile_option_counts_launches(fsm):
+    g = gg.workload("er1000")
+    G = fsm.Graph.from_graphgen(g)
+    G.set_option("profile", 1)
+    for launch in (0, 1, 2):
+        G.set_option("launch", launch)
+        r = G.mine(5, 10, stats=True)
+        s = r["stats"]
+        assert s["count_launches_l3"] >= 1 and s["count_ns_l3"] > 0 and s["count_bytes_l3"] > 0
+        assert s["domain_launches_l1"] >= 1 and s["emit_launches_l1"] >= 1
+    G.close()
