@@ -39,7 +39,8 @@ def parse_args():
     p.add_argument("--workload", default="cl100k")
     p.add_argument("--k", type=int, default=4)
     p.add_argument("--thresholds", default="300,1000,3000")
-    p.add_argument("--cap", type=float, default=None, help="Chung-Lu degree cap (default: sqrt(2m))")
+    p.add_argument("--cap", type=float, default=300.0,
+                   help="Chung-Lu expected-degree cap (default 300; 0 = the structural cutoff sqrt(2m))")
     p.add_argument("--mode", choices=["edge", "vertex"], default="edge")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -49,7 +50,7 @@ def parse_args():
 
 def workload_graph(args):
     import graphgen as gg
-    return gg.workload(args.workload, cap=args.cap if args.cap is not None else "default")
+    return gg.workload(args.workload, cap=args.cap if args.cap else None)
 
 
 def workload_config(args, g):

@@ -70,8 +70,15 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                1 = vertex-induced embeddings (Section 2.1).
  *   "stream"     a cudaStream_t (cast to int64) that all later work of this graph is issued on;
  *                0 restores the library's own stream.  The caller keeps ownership.
- *   "launch"     0 = one launch per frontier batch (default), 1 = persistent work-stealing
- *                launch over all batches of a level.  Both give identical results.
+ *   "launch"     0 = one launch per frontier batch of at most "batch" embeddings, sized on
+ *                the host (default); 1 = one persistent work-stealing launch per pass over the
+ *                whole frontier, all sizes kept on the device, captured with its prefix kernels
+ *                in a CUDA graph (falls back to 0 above 2^27 units); 2 = one launch per frontier
+ *                pattern (the frontier grouped by pattern id), captured in one CUDA graph.  All
+ *                modes give identical results.
+ *   "autotune"   1 = on the first call per level, time the domain pass on an eighth of the
+ *                frontier for chunk sizes 256, 1024, 4096, 16384 and keep the fastest for later
+ *                passes and calls (reported as stat "chunk_l<l>"); 0 = forget tuned values.
  *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
  *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
  *   "profile"    1 = time every extension-kernel launch with CUDA events and sum its algorithmic
@@ -126,7 +133,9 @@ int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, in
  *   launch durations), "P_launches", "P_bytes" (algorithmic bytes: 4 * (d(v) + end pieces of v)
  *   per (embedding, key position) unit, 4 * (l + 1) per embedding read, and for emit
  *   4 * (l + 3) per embedding written), and the same per extended level size l as
- *   "P_ns_l<l>", "P_launches_l<l>", "P_bytes_l<l>" (l = 1..6).
+ *   "P_ns_l<l>", "P_launches_l<l>", "P_bytes_l<l>" (l = 1..6); "chunk_l<l>" (autotuned chunk
+ *   size of level l, 0 if none).  In launch modes 1 and 2 a pass's time covers its CUDA graph
+ *   (the prefix-sum kernels included).
  */
 int fsm_result_stat(const fsm_result *r, const char *key, int64_t *value);
 

@@ -111,6 +111,8 @@ struct fsm_graph {
     int64_t batch = 0;
     int sms = 0;
     int64_t qp_hint[FSM_MAXL + 1] = {};   // distinct quick patterns seen at each level last time
+    int autotune = 0;
+    int32_t tuned_chunk[FSM_MAXL + 1] = {};   // chunk size chosen by the autotuner per level
     int32_t *row_ptr = nullptr, *col = nullptr, *labels = nullptr, *rank = nullptr, *cls_size = nullptr,
             *end_off = nullptr;
     int64_t *piece_cnt = nullptr;
@@ -183,6 +185,14 @@ struct Miner {
 
     struct Range { int64_t e0, ne; };
 
+    // Pieces per work-stealing chunk: the user's fixed value, else the autotuned one, else 0
+    // (sized from the pass's piece total).
+    int32_t chunk_for(int L) const {
+        if (G->chunk > 0) return G->chunk;
+        if (G->tuned_chunk[L] > 0) return G->tuned_chunk[L];
+        return 0;
+    }
+
     // Run one pass of the extension kernel over the frontier.
     //   launch 0: batches of at most `batch` embeddings, each sized on the host;
     //   launch 1: one persistent work-stealing launch over the whole frontier (sizes stay on the
@@ -253,7 +263,7 @@ struct Miner {
                 A.ne = r.ne;
                 A.total = -1;
                 A.nchunks = 0;
-                A.chunk = G->chunk;
+                A.chunk = chunk_for(L);
                 launch_ext();
             }
             ck(cudaStreamEndCapture(st, &graph), "end capture");
@@ -271,7 +281,7 @@ struct Miner {
                 const int64_t total = d2h(base + r.ne * L, st);
                 if (total == 0) continue;
                 bytes(r);
-                int64_t chunk = G->chunk;
+                int64_t chunk = chunk_for(L);
                 if (chunk <= 0) {
                     chunk = 256;
                     while (chunk < 16384 && total / chunk > warps * 64) chunk <<= 1;
@@ -316,6 +326,53 @@ struct Miner {
         in.fpid = np;
         for (void *p : {(void *)cnt, (void *)doff, tmp, (void *)cur}) mem.release(p);
         return off;
+    }
+
+    // Autotuner: time the domain pass (idempotent: it only ORs domain bits) on a sample of the
+    // frontier for each candidate chunk size and keep the fastest for this level.
+    void tune_chunk(const LevelSet &in, ExtArgs A) {
+        const int L = in.L;
+        if (!G->autotune || G->chunk > 0 || G->tuned_chunk[L] > 0 || in.N == 0) return;
+        const int64_t ne = std::min<int64_t>(in.N, std::max<int64_t>(1024, in.N / 8));
+        const int64_t nu = ne * L;
+        int64_t *cnt = mem.get<int64_t>(nu);
+        int64_t *base = mem.get<int64_t>(nu + 1);
+        void *tmp = mem.get<char>((int64_t)scan_temp_bytes(nu) + 16);
+        unsigned long long *ctr = mem.get<unsigned long long>(1);
+        ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, 0, ne, L, cnt, st), "unit counts");
+        ck(launch_scan_i64(cnt, base, nu, tmp, st), "unit scan");
+        const int64_t total = d2h(base + nu, st);
+        const int grid = grid_for(L, PASS_DOMAIN);
+        A.fv = in.fv;
+        A.fpid = in.fpid;
+        A.fN = in.N;
+        A.e0 = 0;
+        A.ne = ne;
+        A.unit_base = base;
+        A.chunk_ctr = ctr;
+        A.total = total;
+        cudaEvent_t a, b;
+        ck(cudaEventCreate(&a), "event");
+        ck(cudaEventCreate(&b), "event");
+        float best_ms = 0.f;
+        int32_t best = 0;
+        for (int32_t chunk : {256, 1024, 4096, 16384}) {
+            A.chunk = chunk;
+            A.nchunks = (total + chunk - 1) / chunk;
+            ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
+            ck(cudaEventRecord(a, st), "event record");
+            ck(launch_extend_domain(L, A, grid, st), "extension kernel");
+            ck(cudaEventRecord(b, st), "event record");
+            ck(cudaEventSynchronize(b), "event sync");
+            float ms = 0.f;
+            ck(cudaEventElapsedTime(&ms, a, b), "event time");
+            rs.launches += 1;
+            if (best == 0 || ms < best_ms) { best_ms = ms; best = chunk; }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        G->tuned_chunk[L] = best;
+        for (void *p : {(void *)cnt, (void *)base, tmp, (void *)ctr}) mem.release(p);
     }
 
     int err_word() { return d2h(G->err, st); }
@@ -431,7 +488,10 @@ struct Miner {
         A.dom_off = doff;
         A.dom = dom;
         A.stats = nullptr;
-        if (rs.live > 0) run_pass(PASS_DOMAIN, in, A, pat_off);
+        if (rs.live > 0) {
+            tune_chunk(in, A);
+            run_pass(PASS_DOMAIN, in, A, pat_off);
+        }
         unsigned long long *sigma = mem.get<unsigned long long>(np);
         ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
         ck(launch_support(K, orbit, live, doff, words, dom, np, sigma, st), "support");
@@ -678,8 +738,13 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
             if (value != 0 && value != 1) fail(FSM_EINVAL, "profile must be 0 or 1");
             g->profile = (int)value;
         } else if (k == "launch") {
-            if (value != 0 && value != 1) fail(FSM_EINVAL, "launch must be 0 or 1");
+            if (value < 0 || value > 2) fail(FSM_EINVAL, "launch must be 0, 1 or 2");
             g->launch = (int)value;
+        } else if (k == "autotune") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "autotune must be 0 or 1");
+            g->autotune = (int)value;
+            if (!value)
+                for (auto &c : g->tuned_chunk) c = 0;
         } else if (k == "chunk") {
             if (value != 0 && (value < 32 || value > 65536 || (value & (value - 1)))) fail(FSM_EINVAL, "chunk must be 0 or a power of two in [32, 65536]");
             g->chunk = (int32_t)value;
@@ -787,6 +852,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["kernel_launches"] = (launches_so_far() - l0) + rs.launches;
         r->stats["time_ns"] = (int64_t)((double)ms * 1e6);
         r->stats["final_level_ns"] = (int64_t)((double)fms * 1e6);
+        for (int L = 1; L <= FSM_MAXL; ++L) r->stats["chunk_l" + std::to_string(L)] = g->tuned_chunk[L];
         const char *pn[3] = {"count", "domain", "emit"};
         for (int p = 0; p < 3; ++p) {
             double ns = 0;

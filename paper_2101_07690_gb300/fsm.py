@@ -178,7 +178,7 @@ STATS = ["k", "levels", "candidates", "embeddings", "final_embeddings", "quick_p
          "count_ns", "domain_ns", "emit_ns", "count_launches", "domain_launches", "emit_launches",
          "count_bytes", "domain_bytes", "emit_bytes"] + [
              f"{p}_{f}_l{l}" for p in ("count", "domain", "emit") for f in ("ns", "launches", "bytes")
-             for l in range(1, 7)]
+             for l in range(1, 7)] + [f"chunk_l{l}" for l in range(1, 7)]
 
 
 class Graph:

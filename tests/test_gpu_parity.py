@@ -107,7 +107,8 @@ def test_chung_lu_scaled(fsm, t):
 def test_chunking_and_batching_do_not_change_results(fsm):
     g = gg.workload("cl100k", scale=0.005, cap=30)
     ref = check(fsm, g, 4, 6)
-    for opts in ({"chunk": 32}, {"chunk": 65536}, {"batch": 1024}, {"batch": 1024, "chunk": 64}):
+    for opts in ({"chunk": 32}, {"chunk": 65536}, {"batch": 1024}, {"batch": 1024, "chunk": 64},
+                 {"autotune": 1}, {"autotune": 1, "launch": 1}):
         G = fsm.Graph.from_graphgen(g)
         for key, val in opts.items():
             G.set_option(key, val)
@@ -187,6 +188,19 @@ def test_launch_modes_identical(fsm, launch):
         check(fsm, g, k, t, "edge", opts)
         check(fsm, g, k, t, "edge", dict(opts, batch=1024, chunk=64))
         check(fsm, g, k, t, "vertex", opts)
+
+
+def test_autotune_picks_a_candidate_and_keeps_results(fsm):
+    g = gg.workload("cl100k", scale=0.005, cap=30)
+    G = fsm.Graph.from_graphgen(g)
+    G.set_option("autotune", 1)
+    a = G.mine(4, 6, stats=True)
+    b = G.mine(4, 6, stats=True)
+    G.close()
+    assert a["stats"]["chunk_l2"] in (256, 1024, 4096, 16384)
+    assert b["stats"]["chunk_l2"] == a["stats"]["chunk_l2"]
+    _same(a, oracle_at(g, 4, 6), "autotuned")
+    _same(b, oracle_at(g, 4, 6), "autotuned, second call")
 
 
 def test_profile_option_counts_launches(fsm):
