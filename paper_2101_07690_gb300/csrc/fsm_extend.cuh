@@ -114,6 +114,19 @@ __device__ __forceinline__ int64_t qp_find(const QPTab &t, uint64_t key) {
     return -1;
 }
 
+// Is u ~ w, given both row ranges: binary search in the shorter list.
+__device__ __forceinline__ bool adj_rows(const int32_t *col, int32_t bu, int32_t eu, int32_t u, int32_t bw,
+                                         int32_t ew, int32_t w) {
+    int32_t lo, end, x;
+    if (eu - bu <= ew - bw) { lo = bu; end = eu; x = w; } else { lo = bw; end = ew; x = u; }
+    int32_t hi = end;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (__ldg(col + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo < end && __ldg(col + lo) == x;
+}
+
 template <int L>
 __device__ __forceinline__ bool in_s(const int32_t (&S)[L], int32_t x) {
     bool r = false;
@@ -208,7 +221,7 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
 // PIECE_TRI.
 template <int L, int PASS>
 __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
-                                           uint64_t srows, int32_t pid, int i, int shape,
+                                           const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int shape,
                                            const int32_t (&pv)[3], const int (&pl)[3], Tally &tl,
                                            CountCache *cc, DomCache &dc) {
     constexpr int K = L + 2;
@@ -222,15 +235,32 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
     const int lx0 = pl[q0], lx1 = pl[q1];
     uint32_t tj0, tj1, txx;
     piece_join_edges(shape, jpos, tj0, tj1, txx);
+    if constexpr (L == 2) {
+        // Four-vertex joins: the greedy dissection from the smallest vertex m always succeeds
+        // (the one remaining vertex is adjacent to the 3-set), so the join survives only if m
+        // is in the piece and m's first greedy step stays in the piece.  Both are decided
+        // here, before any cross-adjacency test.
+        const int32_t w = S[1 - i];
+        const int32_t mt = min(v, min(x0, x1));
+        if (w < mt) return;                               // m = w: the 3-set contains w
+        if (mt == v) {                                    // m = v: its neighbours are w and the piece's
+            const int32_t first = tj1 ? min(x0, x1) : x0; // tj0 is always set
+            if (w < first) return;
+        }
+    }
 
     // cross adjacency between s \ {v} and {x0, x1}
     uint32_t avail = 0;
+    if constexpr (L >= 2) {
+        const int32_t b0 = __ldg(A.g.row_ptr + x0), e0 = __ldg(A.g.row_ptr + x0 + 1);
+        const int32_t b1 = __ldg(A.g.row_ptr + x1), e1 = __ldg(A.g.row_ptr + x1 + 1);
 #pragma unroll
-    for (int p = 0; p < L; ++p) {
-        if (p == i) continue;
-        const int pp = p < i ? p : p - 1;
-        if (is_adj(A.g, S[p], x0)) avail |= 1u << (2 * pp);
-        if (is_adj(A.g, S[p], x1)) avail |= 1u << (2 * pp + 1);
+        for (int p = 0; p < L; ++p) {
+            if (p == i) continue;
+            const int pp = p < i ? p : p - 1;
+            if (adj_rows(A.g.col, SR[p].x, SR[p].y, S[p], b0, e0, x0)) avail |= 1u << (2 * pp);
+            if (adj_rows(A.g.col, SR[p].x, SR[p].y, S[p], b1, e1, x1)) avail |= 1u << (2 * pp + 1);
+        }
     }
     const uint32_t srow_i = (uint32_t)(srows >> (8 * i)) & 0xffu;
 
@@ -286,12 +316,12 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
 
 template <int L, int PASS>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
-                                         uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
+                                         const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
                                          CountCache *cc, DomCache &dc) {
     const DevGraph &g = A.g;
     const int32_t v = S[i];
-    const int32_t rp = __ldg(g.row_ptr + v);
-    const int32_t d = __ldg(g.row_ptr + v + 1) - rp;
+    const int32_t rp = SR[i].x;
+    const int32_t d = SR[i].y - rp;
     const int64_t nc = (int64_t)d * (d - 1) / 2;
     int32_t pv[3];
     int pl[3];
@@ -310,7 +340,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             pv[0] = v; pl[0] = SL[i];
             if (lab_id_less(la, a, lb, b)) { pv[1] = a; pl[1] = la; pv[2] = b; pl[2] = lb; }
             else { pv[1] = b; pl[1] = lb; pv[2] = a; pl[2] = la; }
-            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
+            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
         }
         if (tri) {
             int32_t t0 = v, t1 = a, t2 = b;
@@ -321,7 +351,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
             pv[0] = t0; pv[1] = t1; pv[2] = t2;
             pl[0] = m0; pl[1] = m1; pl[2] = m2;
-            join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_TRI, pv, pl, tl, cc, dc);
+            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_TRI, pv, pl, tl, cc, dc);
         }
     } else {
         const int64_t lq2 = lq - nc;
@@ -340,7 +370,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         pv[0] = a; pl[0] = la;
         if (lab_id_less(SL[i], v, lb, b)) { pv[1] = v; pl[1] = SL[i]; pv[2] = b; pl[2] = lb; }
         else { pv[1] = b; pl[1] = lb; pv[2] = v; pl[2] = SL[i]; }
-        join_piece<L, PASS>(A, S, SL, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
+        join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
     }
 }
 
@@ -391,6 +421,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
         int64_t cur = -1, ub = 0;
         int32_t S[L];
         int SL[L];
+        int2 SR[L];
         int32_t pid = 0;
         int i = 0;
         uint64_t srows = 0;
@@ -404,12 +435,13 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
                 for (int p = 0; p < L; ++p) {
                     S[p] = __ldg(A.fv + (int64_t)p * A.fN + e);
                     SL[p] = __ldg(A.g.labels + S[p]);
+                    SR[p] = make_int2(__ldg(A.g.row_ptr + S[p]), __ldg(A.g.row_ptr + S[p] + 1));
                 }
                 pid = __ldg(A.fpid + e);
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
                 ub = __ldg(A.unit_base + u);
             }
-            do_piece<L, PASS>(A, S, SL, srows, pid, i, q - ub, tl, cc, dc);
+            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc);
         }
     }
     if (PASS == PASS_COUNT) {
