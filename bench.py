@@ -45,6 +45,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--launch", type=int, default=1, choices=[0, 1, 2],
+                   help="0 batched, 1 persistent work-stealing (CUDA graph), 2 one launch per pattern")
+    p.add_argument("--autotune", type=int, default=1, choices=[0, 1])
     return p.parse_args()
 
 
@@ -171,6 +174,8 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     G = fsm.Graph.from_graphgen(g, args.mode)
     G.set_option("stream", stream.cuda_stream)
+    G.set_option("launch", args.launch)
+    G.set_option("autotune", args.autotune)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
 
     def step(profile: bool):
@@ -234,6 +239,7 @@ def run_ours(args, rank, world, local_rank):
             t0 = time.perf_counter()
             h = fsm.fsm_load_graph(rp.data_ptr(), cl.data_ptr(), lb.data_ptr(), g.n, g.num_labels)
             fsm.fsm_set_option(h, "mode", 0 if args.mode == "edge" else 1)
+            fsm.fsm_set_option(h, "launch", args.launch)
             for t in ths:
                 r = fsm.fsm_mine(h, args.k, t)
                 out = fsm.fsm_result_copy(r, args.k)
@@ -272,7 +278,9 @@ def run_ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                 "data": "synthetic (seeded Chung-Lu stand-in for the paper's MiCo graph)",
-                "config": dict(workload_config(args, g), parallelism=f"replicas{world}"),
+                "config": dict(workload_config(args, g), parallelism=f"replicas{world}",
+                               launch={0: "batched", 1: "persistent", 2: "per-pattern"}[args.launch],
+                               autotune=bool(args.autotune)),
                 "e2e": e2e, "gpu_launches": int(agg["kernel_launches"]),
                 "embeddings_per_step": int(agg["embeddings"] // args.steps),
                 "patterns_per_step": int(agg["patterns_out"] // args.steps),
