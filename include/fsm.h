@@ -157,6 +157,36 @@ const char *fsm_last_error(void);
 int fsm_debug_dissect(int32_t k, const int32_t *ids, const uint32_t *adj, uint32_t *l_mask,
                       int32_t *join, int32_t *used_fallback);
 
+/*
+ * fsm_edge_supports_noalloc -- MNI support and embedding count of every labeled edge pattern
+ * (the size-2 level), computed without allocating any device memory.  The paper has no
+ * counterpart; this entry point exists for callers that cannot call cudaMalloc, such as code
+ * that runs inside an allocator's own callback, or a process whose device memory is fully
+ * reserved by another framework's pool.
+ *   d_row_ptr, d_col, d_labels  DEVICE pointers to a CSR in the layout of fsm_load_graph
+ *                              (validated on the device; malformed input gives FSM_EINVAL).
+ *   n >= 1, 1 <= num_labels <= 64.
+ *   d_support, d_count          DEVICE uint64[num_labels * num_labels] written by the call:
+ *                              entry lo * num_labels + hi (lo <= hi) holds the MNI support and
+ *                              the edge count of the pattern with labels (lo, hi); entries with
+ *                              hi < lo are 0.  fsm_mine(k = 2) returns the same supports and
+ *                              counts for the pairs whose support reaches its threshold.
+ *   stream                      cudaStream_t to run on (NULL = the default stream); the call
+ *                              synchronises it before returning.
+ * Scratch: one static device array of 64 MiB, reserved when the library's device code is
+ * loaded on a GPU and kept until the process exits; no cudaMalloc, cudaFree or allocating
+ * library routine is called.  A graph whose scratch need, about 4 * (n + num_labels *
+ * (n / 32 + num_labels) + 6 * num_labels^2) bytes, exceeds the array is rejected with
+ * FSM_EUNSUPPORTED (and a message giving both sizes) before any device work.  The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call reuses the same array and clears the part it
+ * needs: calls that overlap on the GPU (other threads, other streams) race and must not be
+ * issued.
+ */
+int fsm_edge_supports_noalloc(const int32_t *d_row_ptr, const int32_t *d_col, const int32_t *d_labels,
+                              int32_t n, int32_t num_labels, uint64_t *d_support, uint64_t *d_count,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

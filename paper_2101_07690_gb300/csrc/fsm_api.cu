@@ -101,6 +101,11 @@ T d2h(const T *dptr, cudaStream_t st) {
 
 } // namespace
 
+namespace fsm {
+// lets other translation units of the C ABI report a message through fsm_last_error()
+void set_last_error_message(const std::string &m) { g_last_error = m; }
+} // namespace fsm
+
 struct fsm_graph {
     int device = 0;
     int32_t n = 0, NL = 0;

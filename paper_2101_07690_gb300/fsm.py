@@ -26,7 +26,7 @@ _NAMES = {FSM_EINVAL: "FSM_EINVAL", FSM_ENOMEM: "FSM_ENOMEM", FSM_ECUDA: "FSM_EC
 # every entry point that include/fsm.h declares
 EXPORTS = ["fsm_load_graph", "fsm_set_option", "fsm_mine", "fsm_result_count", "fsm_result_get",
            "fsm_result_embeddings", "fsm_result_copy", "fsm_result_stat", "fsm_free_result",
-           "fsm_free_graph", "fsm_last_error", "fsm_debug_dissect"]
+           "fsm_free_graph", "fsm_last_error", "fsm_debug_dissect", "fsm_edge_supports_noalloc"]
 
 
 class FsmError(RuntimeError):
@@ -62,6 +62,7 @@ def load(path: str | None = None):
         "fsm_free_graph": (None, [vp]),
         "fsm_last_error": (ctypes.c_char_p, []),
         "fsm_debug_dissect": (ctypes.c_int, [i32, P(i32), P(ctypes.c_uint32), P(ctypes.c_uint32), P(i32), P(i32)]),
+        "fsm_edge_supports_noalloc": (ctypes.c_int, [vp, vp, vp, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -171,6 +172,14 @@ def fsm_debug_dissect(ids, adj_rows):
     _check(load().fsm_debug_dissect(len(ids), _ptr(ids, ctypes.c_int32), _ptr(rows, ctypes.c_uint32),
                                     ctypes.byref(lm), ctypes.byref(jn), ctypes.byref(fb)))
     return int(lm.value), int(jn.value), int(fb.value)
+
+
+def fsm_edge_supports_noalloc(d_row_ptr: int, d_col: int, d_labels: int, n: int, num_labels: int,
+                              d_support: int, d_count: int, stream: int = 0) -> None:
+    """Size-2 pattern supports without device allocation; every pointer is a device address
+    (int), outputs uint64[num_labels * num_labels]."""
+    _check(load().fsm_edge_supports_noalloc(d_row_ptr, d_col, d_labels, int(n), int(num_labels),
+                                            d_support, d_count, stream or None))
 
 
 STATS = ["k", "levels", "candidates", "embeddings", "final_embeddings", "quick_patterns", "patterns",
