@@ -47,6 +47,7 @@ enum {
 
 typedef struct fsm_graph fsm_graph;
 typedef struct fsm_result fsm_result;
+typedef struct fsm_mlp fsm_mlp;
 
 /*
  * fsm_load_graph -- copy one labeled graph G = (V, E, L) (Section 2.1) to the current CUDA
@@ -81,6 +82,16 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                passes and calls (reported as stat "chunk_l<l>"); 0 = forget tuned values.
  *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
  *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
+ *   "seed"       64-bit seed of the piece sampling of fsm_mine with sample_rate < 1 (default 0).
+ *   "candidates" 1 = sampled mining returns every candidate pattern of the sampled level with
+ *                its estimated support (smallest orbit popcount / p) and its 32 features
+ *                (fsm_result_features), deciding nothing; 0 = decide (default).
+ *   "model"      an fsm_mlp* (cast to int64) that sampled mining uses to predict supports; 0 =
+ *                none (sampled mining then keeps patterns whose estimate reaches t).  The graph
+ *                borrows the network; keep it alive while the graph uses it.
+ *   "delta_milli" recount band of sampled mining with a model, in thousandths of a natural log
+ *                unit (default 500): patterns with |log prediction - log t| <= delta are
+ *                recounted exactly.
  *   "profile"    1 = time every extension-kernel launch with CUDA events and sum its algorithmic
  *                bytes (reported by fsm_result_stat); adds one synchronisation per launch.
  * Unknown keys or out-of-range values give FSM_EINVAL.
@@ -90,10 +101,17 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value);
 /*
  * fsm_mine -- every pattern with exactly k vertices and MNI support >= min_support
  * (Section 2.2 problem statement; Definition 2).
- *   1 <= k <= 8, min_support >= 1, sample_rate in (0, 1]; 1.0 means exact mining.  Sampled
- *   mining (sample_rate < 1) is not available in this build and gives FSM_EUNSUPPORTED.
- * The supports returned are exact MNI supports; the embedding counts are exact for every
- * returned pattern.
+ *   1 <= k <= 8, min_support >= 1, sample_rate in (0, 1]; 1.0 means exact mining.
+ * Exact mining (sample_rate = 1) returns exact MNI supports and embedding counts.
+ * Sampled mining (sample_rate = p < 1, k >= 3; Section 5's subgraph sampling, here at a rate
+ * instead of a per-key quota): every level but the last is mined exactly; the last level joins
+ * only the pieces {x < y < z} kept by the counter-based rule of option "seed" and rate p
+ * (splitmix64 of the seed and the three ids below floor(p * 2^64)).  Each candidate pattern's
+ * support is then decided by the model (option "model"): predictions above t * e^delta are
+ * kept with the predicted support, predictions within the band are recounted exactly by an
+ * exact last level restricted to the parts those patterns can be dissected into, the rest are
+ * dropped.  Without a model the estimate (smallest sampled orbit popcount) / p decides.
+ * fsm_result_exact tells which supports were counted exactly.
  * Ownership: *out is a host-side result owned by the caller until fsm_free_result().
  */
 int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate,
@@ -122,6 +140,22 @@ int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, in
                     int64_t *embeddings);
 
 /*
+ * fsm_result_exact -- exact[i] = 1 when pattern i's support and count were counted exactly, 0
+ * when they are estimates of sampled mining (int32[count]).
+ */
+int fsm_result_exact(const fsm_result *r, int32_t *exact);
+
+/*
+ * fsm_result_features -- the 32 features of every pattern (float[count * 32], row-major) of a
+ * sampled mining call made with option "candidates" = 1; FSM_EINVAL otherwise.  Features:
+ * [0..8) log1p of each orbit's sampled domain popcount, ascending, zero-padded; [8..16)
+ * log(|V_l| / n) for each canonical position's label; [16..24) mean log1p(degree) over the
+ * sampled domain of each position's orbit; [24..32) k, number of edges, log p,
+ * log1p(sampled embeddings), log(t / n), log |Aut|, log((smallest popcount + 1) / p), log n.
+ */
+int fsm_result_features(const fsm_result *r, float *features);
+
+/*
  * fsm_result_stat -- a run counter of the mining call that made r:
  *   "k", "levels", "candidates" (joins tested), "embeddings" (accepted joins, all levels),
  *   "final_embeddings" (accepted joins of the last level), "quick_patterns" (distinct index
@@ -144,6 +178,34 @@ void fsm_free_graph(fsm_graph *g);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *fsm_last_error(void);
+
+/*
+ * Support-prediction network of sampled mining (no counterpart in the paper): a 32 -> 64 ->
+ * 64 -> 1 multilayer perceptron with ReLU, inputs standardised by stored means and deviations,
+ * BF16 weights in every product with FP32 accumulation, FP32 master weights trained by Adam
+ * on the mean squared error of log(MNI support).  Parameters (6337 floats, FP32): W1[32][64]
+ * (input, unit), b1[64], W2[64][64], b2[64], w3[64], b3.  Host pointers unless named d_*.
+ *   fsm_mlp_create       He-uniform weights from a splitmix64 stream of seed; zero biases.
+ *   fsm_mlp_set_params / fsm_mlp_get_params   copy the 6337 master weights in / out (set also
+ *                        resets Adam's moments).
+ *   fsm_mlp_set_norm     input means and standard deviations (32 each, deviations > 0).
+ *   fsm_mlp_gradients    mean squared error over X[n][32], Y[n] and its gradient (6337 floats).
+ *   fsm_mlp_train        epochs of shuffled minibatches (order from a splitmix64 stream of seed),
+ *                        Adam (beta 0.9, 0.999, eps 1e-8) at rate lr; final_loss = last epoch's
+ *                        mean squared error.
+ *   fsm_mlp_predict      outputs (predicted log support) for X[n][32].
+ *   fsm_mlp_predict_device the same on device arrays, on stream.
+ */
+int fsm_mlp_create(uint64_t seed, fsm_mlp **out);
+int fsm_mlp_set_params(fsm_mlp *m, const float *params);
+int fsm_mlp_get_params(const fsm_mlp *m, float *params);
+int fsm_mlp_set_norm(fsm_mlp *m, const float *mean, const float *stdev);
+int fsm_mlp_gradients(fsm_mlp *m, const float *X, const float *Y, int64_t n, float *grads, float *loss);
+int fsm_mlp_train(fsm_mlp *m, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch,
+                  float lr, uint64_t seed, float *final_loss);
+int fsm_mlp_predict(const fsm_mlp *m, const float *X, int64_t n, float *out);
+int fsm_mlp_predict_device(const fsm_mlp *m, const float *d_X, int64_t n, float *d_out, void *stream);
+void fsm_mlp_free(fsm_mlp *m);
 
 /*
  * fsm_debug_dissect -- host build of the library's smallest-vertex-first dissection

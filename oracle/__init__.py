@@ -53,6 +53,13 @@ def _load():
             lib.oracle_mine.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
                                         P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64]
+            lib.oracle_mine_sampled.restype = ctypes.c_void_p
+            lib.oracle_mine_sampled.argtypes = lib.oracle_mine.argtypes + [ctypes.c_int32, ctypes.c_uint64,
+                                                                           ctypes.c_double]
+            lib.oracle_result_copy_sampled.restype = None
+            lib.oracle_result_copy_sampled.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64)]
+            lib.oracle_dissect.restype = ctypes.c_uint32
+            lib.oracle_dissect.argtypes = [ctypes.c_int32, P(ctypes.c_uint32)]
             lib.oracle_result_count.restype = ctypes.c_int64
             lib.oracle_result_count.argtypes = [ctypes.c_void_p]
             lib.oracle_result_copy.restype = None
@@ -60,6 +67,11 @@ def _load():
                                                P(ctypes.c_int64), P(ctypes.c_int64)]
             lib.oracle_free.restype = None
             lib.oracle_free.argtypes = [ctypes.c_void_p]
+            lib.oracle_pattern_support.restype = ctypes.c_int
+            lib.oracle_pattern_support.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                                                   P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32),
+                                                   ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64,
+                                                   P(ctypes.c_int64), P(ctypes.c_int64)]
             _lib = lib
     return _lib
 
@@ -72,13 +84,16 @@ def _ptr(a, ct):
 
 
 def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = None,
-         max_embeddings: int = 0) -> dict:
+         max_embeddings: int = 0, sample: tuple[float, int] | None = None) -> dict:
     """All k-vertex patterns of graph ``g`` with MNI support >= t.
 
     ``roots=(b, e)`` restricts the enumeration to connected sets whose smallest vertex id is
     in [b, e); ``max_embeddings > 0`` stops after that many embeddings (roots taken in
     ascending order).  Both give a bounded sample of the work, whose supports are those of the
-    sample.
+    sample.  ``sample=(p, seed)`` adds the statistics of sampled mining at rate p: an embedding
+    is kept when the 3-vertex part of its smallest-vertex-first dissection passes the
+    splitmix64 rule; ``ssupport`` and ``scount`` are the MNI support and embedding count over
+    kept embeddings.
     Returns a dict of numpy arrays: labels (P, k) int32, adj (P,) uint64, support (P,) int64,
     count (P,) int64 (number of embeddings of each pattern)."""
     lib = _load()
@@ -88,9 +103,10 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
     if labels.size and (labels.min() < 0 or labels.max() > 255):
         raise ValueError("oracle labels must lie in [0, 255]")
     b, e = (0, g.n) if roots is None else roots
-    res = lib.oracle_mine(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
-                          _ptr(labels, ctypes.c_int32), k, MODES[mode], int(t), int(b), int(e),
-                          int(max_embeddings))
+    sp, sseed = (1.0, 0) if sample is None else sample
+    res = lib.oracle_mine_sampled(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                  _ptr(labels, ctypes.c_int32), k, MODES[mode], int(t), int(b), int(e),
+                                  int(max_embeddings), 1 if sample is not None else 0, int(sseed), float(sp))
     if not res:
         raise ValueError("oracle_mine rejected its arguments")
     try:
@@ -100,9 +116,43 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
         if npat:
             lib.oracle_result_copy(res, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
                                    _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64))
+        if sample is not None:
+            out["ssupport"] = np.zeros(npat, np.int64)
+            out["scount"] = np.zeros(npat, np.int64)
+            if npat:
+                lib.oracle_result_copy_sampled(res, _ptr(out["ssupport"], ctypes.c_int64),
+                                               _ptr(out["scount"], ctypes.c_int64))
     finally:
         lib.oracle_free(res)
     return out
+
+
+def pattern_support(g, labels, adj: int, mode: str = "edge", max_maps: int = 0) -> tuple[int, int]:
+    """(MNI support, embedding count) of one pattern, by matching every label-preserving
+    monomorphism (edge-induced) or induced embedding (vertex-induced) of it.  Raises
+    OverflowError when more than max_maps maps exist (max_maps > 0)."""
+    lib = _load()
+    k = len(labels)
+    row_ptr = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    lab = np.ascontiguousarray(g.labels, dtype=np.int32)
+    plab = np.ascontiguousarray(labels, dtype=np.int32)
+    sup, cnt = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib.oracle_pattern_support(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                    _ptr(lab, ctypes.c_int32), k, _ptr(plab, ctypes.c_int32), int(adj),
+                                    MODES[mode], int(max_maps), ctypes.byref(sup), ctypes.byref(cnt))
+    if rc == -2:
+        raise OverflowError("pattern has more than max_maps maps")
+    if rc != 0:
+        raise ValueError("oracle_pattern_support rejected its arguments")
+    return int(sup.value), int(cnt.value)
+
+
+def dissect(adj_rows) -> int:
+    """3-vertex part (bit mask over positions, which are the vertex ids) of the smallest-vertex-
+    first dissection of a connected graph."""
+    rows = np.ascontiguousarray(adj_rows, dtype=np.uint32)
+    return int(_load().oracle_dissect(len(rows), _ptr(rows, ctypes.c_uint32)))
 
 
 def pattern_edges(adj: int, k: int) -> list[tuple[int, int]]:

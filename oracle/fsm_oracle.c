@@ -149,6 +149,8 @@ typedef struct {
     code_t code;
     int64_t count;                  /* embeddings (V', E') of this pattern */
     vset_t dom[OR_MAXK];            /* D[P][c] */
+    int64_t scount;                 /* sampled mode: kept embeddings */
+    vset_t sdom[OR_MAXK];           /* sampled mode: images over kept embeddings */
 } pattern_t;
 
 typedef struct {
@@ -163,6 +165,9 @@ typedef struct {
     int32_t n;
     int64_t budget, seen;           /* stop after `budget` embeddings (<= 0: no limit) */
     int stop;
+    /* sampled mode: an embedding is kept iff the 3-vertex part of its dissection is kept */
+    int sampled;
+    uint64_t seed, thr;
     canon_ctx_t cx;
     pattern_t *pat; int64_t npat, cappat;
     /* pattern lookup by canonical code: open addressing over indices */
@@ -200,8 +205,8 @@ static int32_t pattern_find_or_add(oracle_t *o, const code_t *c) {
         o->pat = (pattern_t *)realloc(o->pat, sizeof(pattern_t) * (size_t)o->cappat);
     }
     pattern_t *p = &o->pat[o->npat];
-    p->code = *c; p->count = 0;
-    for (int i = 0; i < OR_MAXK; i++) vset_init(&p->dom[i]);
+    p->code = *c; p->count = 0; p->scount = 0;
+    for (int i = 0; i < OR_MAXK; i++) { vset_init(&p->dom[i]); vset_init(&p->sdom[i]); }
     o->pat_slot[h] = (int32_t)o->npat;
     return (int32_t)o->npat++;
 }
@@ -283,6 +288,69 @@ static int spans_connected(int k, const uint32_t *adjrow) {
     return seen == ((1u << k) - 1u);
 }
 
+/* ---- sampled mode: Algorithm 1's dissect (n = 3) and the piece-sampling rule ----
+ * dissect: for each start vertex in ascending id order, visit 3 vertices by always adding the
+ * smallest id adjacent to the visited ones; the 3-set l is kept if the other vertices plus one
+ * vertex v' of l (tried in ascending id order) are connected.  If no start vertex works, take
+ * the smallest (sorted ids of l, id of v') over all connected 3-sets l with a connected rest.
+ * Positions here are already in ascending id order (u[0] < u[1] < ...). */
+static int conn_mask(int k, const uint32_t *adjrow, uint32_t m) {
+    if (!m) return 0;
+    uint32_t seen = m & (~m + 1u), fr = seen;
+    while (fr) {
+        uint32_t nx = 0;
+        for (int i = 0; i < k; i++) if ((fr >> i) & 1u) nx |= adjrow[i];
+        nx &= m & ~seen; seen |= nx; fr = nx;
+    }
+    return seen == m;
+}
+
+static uint32_t dissect_three(int k, const uint32_t *adjrow) {
+    uint32_t all = (1u << k) - 1u;
+    for (int start = 0; start < k; start++) {
+        uint32_t vis = 1u << start;
+        for (int step = 0; step < 2; step++) {
+            uint32_t cand = 0;
+            for (int i = 0; i < k; i++) if ((vis >> i) & 1u) cand |= adjrow[i];
+            cand &= all & ~vis;
+            if (!cand) { vis = 0; break; }
+            vis |= cand & (~cand + 1u);          /* smallest id = lowest position */
+        }
+        if (!vis) continue;
+        for (int v = 0; v < k; v++)
+            if (((vis >> v) & 1u) && conn_mask(k, adjrow, (all & ~vis) | (1u << v))) return vis;
+    }
+    /* exhaustive rule: smallest sorted triple (a < b < c), then smallest join */
+    for (int a = 0; a < k; a++)
+        for (int b = a + 1; b < k; b++)
+            for (int c = b + 1; c < k; c++) {
+                uint32_t l = (1u << a) | (1u << b) | (1u << c);
+                if (!conn_mask(k, adjrow, l)) continue;
+                int js[3] = {a, b, c};
+                for (int q = 0; q < 3; q++)
+                    if (conn_mask(k, adjrow, (all & ~l) | (1u << js[q]))) return l;
+            }
+    return 0;
+}
+
+/* splitmix64 (Steele, Lea, Flood 2014): add the golden gamma, then mix */
+static uint64_t smix(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ULL;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+    return z ^ (z >> 31);
+}
+
+static int kept(const oracle_t *o, const int32_t *u, uint32_t l) {
+    int32_t ids[3]; int c = 0;
+    for (int i = 0; i < o->k; i++) if ((l >> i) & 1u) ids[c++] = u[i];   /* ascending already */
+    uint64_t h = smix(o->seed);
+    h = smix(h ^ (uint64_t)(uint32_t)ids[0]);
+    h = smix(h ^ (uint64_t)(uint32_t)ids[1]);
+    h = smix(h ^ (uint64_t)(uint32_t)ids[2]);
+    return h < o->thr;
+}
+
 static void record(oracle_t *o, const int32_t *u, const int32_t *lab, const uint32_t *adjrow) {
     if (o->stop) return;
     if (o->budget > 0 && ++o->seen >= o->budget) o->stop = 1;
@@ -292,6 +360,12 @@ static void record(oracle_t *o, const int32_t *u, const int32_t *lab, const uint
     const uint8_t *perm = o->pool + m->perm_off;
     for (int32_t q = 0; q < m->nopt; q++, perm += o->k)
         for (int c = 0; c < o->k; c++) vset_insert(&p->dom[c], u[perm[c]]);
+    if (o->sampled && o->k >= 3 && kept(o, u, dissect_three(o->k, adjrow))) {
+        p->scount++;
+        perm = o->pool + m->perm_off;
+        for (int32_t q = 0; q < m->nopt; q++, perm += o->k)
+            for (int c = 0; c < o->k; c++) vset_insert(&p->sdom[c], u[perm[c]]);
+    }
 }
 
 static void process_set(oracle_t *o, const int32_t *vs) {
@@ -361,6 +435,7 @@ typedef struct {
     int32_t *labels;     /* npat x k */
     uint64_t *adj;       /* bit (i*k + j) set for canonical edge i < j */
     int64_t *support, *count;
+    int64_t *ssupport, *scount;   /* sampled mode: min_c |sampled images|, kept embeddings */
 } oracle_result_t;
 
 static int code_sort_k;
@@ -377,14 +452,37 @@ static int idx_cmp(const void *a, const void *b) {
  *   bounded sample of the work, and so does max_embeddings > 0, which stops the enumeration
  *   (roots in ascending order) after that many embeddings.  Returns NULL on bad arguments.
  */
+oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                     const int32_t *labels, int32_t k, int32_t mode, int64_t t,
+                                     int32_t root_begin, int32_t root_end, int64_t max_embeddings,
+                                     int32_t sampled, uint64_t seed, double p);
+
 oracle_result_t *oracle_mine(int32_t n, const int32_t *row_ptr, const int32_t *col,
                              const int32_t *labels, int32_t k, int32_t mode, int64_t t,
                              int32_t root_begin, int32_t root_end, int64_t max_embeddings) {
+    return oracle_mine_sampled(n, row_ptr, col, labels, k, mode, t, root_begin, root_end, max_embeddings,
+                               0, 0, 1.0);
+}
+
+/*
+ * oracle_mine_sampled: oracle_mine, plus (sampled != 0, k >= 3) the sampled statistics of
+ * sampled mining at rate p: an embedding is kept iff the 3-vertex part of its smallest-vertex-
+ * first dissection {a < b < c} gives splitmix64(splitmix64(splitmix64(splitmix64(seed) ^ a)
+ * ^ b) ^ c) < floor(p * 2^64); per pattern, ssupport = min over positions of the number of
+ * images over kept embeddings (every optimal permutation) and scount = kept embeddings.
+ */
+oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                     const int32_t *labels, int32_t k, int32_t mode, int64_t t,
+                                     int32_t root_begin, int32_t root_end, int64_t max_embeddings,
+                                     int32_t sampled, uint64_t seed, double p) {
     if (k < 1 || k > OR_MAXK || n < 0 || (mode != 0 && mode != 1)) return NULL;
     oracle_t o;
     memset(&o, 0, sizeof(o));
     o.k = k; o.mode = mode; o.row_ptr = row_ptr; o.col = col; o.labels = labels; o.n = n;
     o.budget = max_embeddings;
+    o.sampled = sampled;
+    o.seed = seed;
+    o.thr = sampled ? (uint64_t)(p * 18446744073709551616.0) : 0;
     o.cx.k = k;
     gen_perms(&o.cx);
     if (root_begin < 0) root_begin = 0;
@@ -419,6 +517,8 @@ oracle_result_t *oracle_mine(int32_t n, const int32_t *row_ptr, const int32_t *c
     r->adj = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk + 1));
     r->support = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     r->count = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
+    r->ssupport = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
+    r->scount = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     for (int64_t q = 0; q < nk; q++) {
         const pattern_t *p = &o.pat[keep[q]];
         int64_t sigma = -1;
@@ -436,10 +536,17 @@ oracle_result_t *oracle_mine(int32_t n, const int32_t *row_ptr, const int32_t *c
         r->adj[q] = bits;
         r->support[q] = sigma;
         r->count[q] = p->count;
+        int64_t ss = -1;
+        for (int c = 0; c < k; c++) {
+            int64_t s2 = p->sdom[c].size;
+            if (ss < 0 || s2 < ss) ss = s2;
+        }
+        r->ssupport[q] = p->scount ? ss : 0;
+        r->scount[q] = p->scount;
     }
     free(keep);
     for (int64_t p = 0; p < o.npat; p++)
-        for (int c = 0; c < OR_MAXK; c++) free(o.pat[p].dom[c].slot);
+        for (int c = 0; c < OR_MAXK; c++) { free(o.pat[p].dom[c].slot); free(o.pat[p].sdom[c].slot); }
     free(o.pat); free(o.pat_slot); free(o.memo); free(o.pool); free(o.cx.perms);
     return r;
 }
@@ -455,7 +562,140 @@ void oracle_result_copy(const oracle_result_t *r, int32_t *labels, uint64_t *adj
     memcpy(count, r->count, sizeof(int64_t) * (size_t)r->npat);
 }
 
+void oracle_result_copy_sampled(const oracle_result_t *r, int64_t *ssupport, int64_t *scount) {
+    if (!r) return;
+    memcpy(ssupport, r->ssupport, sizeof(int64_t) * (size_t)r->npat);
+    memcpy(scount, r->scount, sizeof(int64_t) * (size_t)r->npat);
+}
+
 void oracle_free(oracle_result_t *r) {
     if (!r) return;
-    free(r->labels); free(r->adj); free(r->support); free(r->count); free(r);
+    free(r->labels); free(r->adj); free(r->support); free(r->count); free(r->ssupport); free(r->scount); free(r);
+}
+
+/* ------------------------------------------------------------------ one pattern at a time */
+
+/*
+ * oracle_pattern_support: MNI support and embedding count of ONE pattern P in G, by matching.
+ *   P has k vertices with labels plab[k] and an edge (i, j), i < j, wherever bit i*k + j of padj
+ *   is set; P must be connected.  Every injective map f from P's vertices to G's vertices that
+ *   keeps labels and sends each pattern edge to a graph edge is enumerated (edge-induced mode:
+ *   the monomorphisms), or that also sends each pattern non-edge to a non-edge (vertex-induced
+ *   mode).  These maps are exactly the isomorphisms from P onto its embeddings, so Definition 2
+ *   gives sigma = min over positions c of |{f(c)}|; each embedding is hit by |Aut(P)| maps, so
+ *   the embedding count is (number of maps) / |Aut(P)|, with Aut(P) found by trying all k!
+ *   vertex permutations of P.
+ *   Returns 0, or -1 on bad arguments, or -2 if more than max_maps maps exist (max_maps > 0).
+ * Independent of oracle_mine: no ESU, no canonical form.
+ */
+typedef struct {
+    int k, mode;
+    const int32_t *row_ptr, *col, *labels;
+    int32_t n;
+    int32_t plab[OR_MAXK];
+    uint32_t padj[OR_MAXK];
+    int order[OR_MAXK], parent[OR_MAXK];
+    int32_t f[OR_MAXK];
+    uint8_t **img;               /* per position: bitmap over n */
+    int64_t maps, max_maps;
+    int over;
+} match_t;
+
+static void match_rec(match_t *m, int depth) {
+    if (m->over) return;
+    if (depth == m->k) {
+        m->maps++;
+        if (m->max_maps > 0 && m->maps > m->max_maps) { m->over = 1; return; }
+        for (int c = 0; c < m->k; c++) m->img[c][m->f[c] >> 3] |= (uint8_t)(1u << (m->f[c] & 7));
+        return;
+    }
+    int c = m->order[depth];
+    int32_t lo, hi;
+    const int32_t *cand;
+    int32_t all_first = 0;
+    if (depth == 0) { lo = 0; hi = m->n; cand = NULL; all_first = 1; }
+    else { int32_t pv = m->f[m->parent[depth]]; lo = m->row_ptr[pv]; hi = m->row_ptr[pv + 1]; cand = m->col; }
+    for (int32_t q = lo; q < hi && !m->over; q++) {
+        int32_t x = all_first ? q : cand[q];
+        if (m->labels[x] != m->plab[c]) continue;
+        int ok = 1;
+        for (int e = 0; e < depth && ok; e++) {
+            int c2 = m->order[e];
+            if (m->f[c2] == x) { ok = 0; break; }
+            int pe = (m->padj[c] >> c2) & 1u;
+            if (pe && !adjacent(m->row_ptr, m->col, x, m->f[c2])) ok = 0;
+            if (!pe && m->mode == 1 && adjacent(m->row_ptr, m->col, x, m->f[c2])) ok = 0;
+        }
+        if (!ok) continue;
+        m->f[c] = x;
+        match_rec(m, depth + 1);
+    }
+}
+
+int oracle_pattern_support(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *labels,
+                           int32_t k, const int32_t *plab, uint64_t padj_bits, int32_t mode,
+                           int64_t max_maps, int64_t *support, int64_t *count) {
+    if (k < 1 || k > OR_MAXK || n < 1 || (mode != 0 && mode != 1) || !support || !count) return -1;
+    match_t m;
+    memset(&m, 0, sizeof(m));
+    m.k = k; m.mode = mode; m.row_ptr = row_ptr; m.col = col; m.labels = labels; m.n = n;
+    m.max_maps = max_maps;
+    for (int i = 0; i < k; i++) m.plab[i] = plab[i];
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++)
+            if ((padj_bits >> (i * k + j)) & 1ULL) { m.padj[i] |= 1u << j; m.padj[j] |= 1u << i; }
+    if (!spans_connected(k, m.padj)) return -1;
+    /* BFS order from position 0: each later position has an already placed neighbour */
+    int seen = 1; m.order[0] = 0; m.parent[0] = -1;
+    for (int d = 0, tail = 1; d < tail; d++) {
+        int c = m.order[d];
+        for (int x = 0; x < k; x++)
+            if (!((seen >> x) & 1) && ((m.padj[c] >> x) & 1u)) {
+                seen |= 1 << x; m.order[tail] = x; m.parent[tail] = d; tail++;
+            }
+    }
+    /* parent[] holds the index in order[]; convert to the position itself */
+    for (int d = 1; d < k; d++) m.parent[d] = m.order[m.parent[d]];
+    m.img = (uint8_t **)malloc(sizeof(uint8_t *) * (size_t)k);
+    for (int c = 0; c < k; c++) m.img[c] = (uint8_t *)calloc((size_t)n / 8 + 1, 1);
+    match_rec(&m, 0);
+    int rc = 0;
+    if (m.over) rc = -2;
+    else {
+        int64_t sigma = -1;
+        for (int c = 0; c < k; c++) {
+            int64_t s = 0;
+            for (int32_t b = 0; b < n / 8 + 1; b++) s += __builtin_popcount(m.img[c][b]);
+            if (sigma < 0 || s < sigma) sigma = s;
+        }
+        /* automorphisms: label- and adjacency-preserving permutations of P */
+        canon_ctx_t cx;
+        memset(&cx, 0, sizeof(cx));
+        cx.k = k;
+        gen_perms(&cx);
+        int64_t aut = 0;
+        for (int p = 0; p < cx.nperm; p++) {
+            const uint8_t *pi = cx.perms + (size_t)p * k;
+            int ok = 1;
+            for (int i = 0; i < k && ok; i++) {
+                if (m.plab[pi[i]] != m.plab[i]) ok = 0;
+                for (int j = 0; j < k && ok; j++)
+                    if ((((m.padj[i] >> j) & 1u)) != ((m.padj[pi[i]] >> pi[j]) & 1u)) ok = 0;
+            }
+            aut += ok;
+        }
+        free(cx.perms);
+        *support = m.maps ? sigma : 0;
+        *count = m.maps / aut;
+    }
+    for (int c = 0; c < k; c++) free(m.img[c]);
+    free(m.img);
+    return rc;
+}
+
+/* dissection of a connected k-vertex graph given as adjacency rows over positions 0..k-1
+ * (positions are the ids); returns the 3-vertex part as a mask, 0 if none */
+uint32_t oracle_dissect(int32_t k, const uint32_t *adjrow) {
+    if (k < 3 || k > OR_MAXK) return 0;
+    return dissect_three(k, adjrow);
 }

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -118,6 +119,13 @@ struct fsm_graph {
     int64_t qp_hint[FSM_MAXL + 1] = {};   // distinct quick patterns seen at each level last time
     int autotune = 0;
     int32_t tuned_chunk[FSM_MAXL + 1] = {};   // chunk size chosen by the autotuner per level
+    // sampled mining
+    uint64_t seed = 0;
+    int candidates = 0;
+    const fsm_mlp *model = nullptr;
+    double delta = 0.5;
+    int32_t *by_rank = nullptr;
+    int64_t *cls_off = nullptr;
     int32_t *row_ptr = nullptr, *col = nullptr, *labels = nullptr, *rank = nullptr, *cls_size = nullptr,
             *end_off = nullptr;
     int64_t *piece_cnt = nullptr;
@@ -142,6 +150,8 @@ struct fsm_result {
     std::vector<int32_t> labels;
     std::vector<uint64_t> adj;
     std::vector<int64_t> support, count;
+    std::vector<int32_t> exact;          // 1: support counted exactly, 0: estimated (sampled mining)
+    std::vector<float> features;         // 32 per pattern, sampled mining with "candidates" only
     std::map<std::string, int64_t> stats;
 };
 
@@ -156,12 +166,14 @@ struct LevelSet {
     uint32_t *cadj = nullptr;
     int32_t *fv = nullptr, *fpid = nullptr;
     int64_t N = 0;                      // stored embeddings
+    float *feat = nullptr;              // sampled level: 32 features per pattern
 };
 
 struct RunStats {
     int64_t tested = 0, accepted = 0, qps = 0, patterns = 0, live = 0, frontier_max = 0, levels = 0,
             final_accepted = 0, launches = 0;
     // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
+    int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0;
     double pass_ns[FSM_MAXL + 1][3] = {};
     int64_t pass_launches[FSM_MAXL + 1][3] = {}, pass_bytes[FSM_MAXL + 1][3] = {};
 };
@@ -210,7 +222,7 @@ struct Miner {
         int64_t B = G->batch > 0 ? G->batch : std::max<int64_t>(1024, ((int64_t)1 << 24) / L);
         std::vector<Range> ranges;
         bool device_total = false;
-        if (G->launch == 2 && (int64_t)pat_off.size() == in.P + 1) {
+        if (G->launch == 2 && (int64_t)pat_off.size() == in.P + 1) {  // frontier grouped by pattern
             for (int64_t p = 0; p < in.P; ++p)
                 for (int64_t e0 = pat_off[p]; e0 < pat_off[p + 1]; e0 += B)
                     ranges.push_back({e0, std::min(B, pat_off[p + 1] - e0)});
@@ -312,7 +324,7 @@ struct Miner {
     // Frontier grouped by pattern id (launch mode 2): returns host offsets, P+1 entries.
     std::vector<int64_t> group_by_pattern(LevelSet &in) {
         std::vector<int64_t> off;
-        if (G->launch != 2 || in.N == 0 || in.P == 0) return off;
+        if (G->launch == 0 || in.N == 0 || in.P == 0) return off;
         int64_t *cnt = mem.get<int64_t>(in.P);
         int64_t *doff = mem.get<int64_t>(in.P + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(in.P) + 16);
@@ -383,7 +395,10 @@ struct Miner {
     int err_word() { return d2h(G->err, st); }
 
     // Extend `in` (size L) to size L+2.  piece_freq == nullptr at the size-3 level.
-    LevelSet extend(const LevelSet &in_level, const uint8_t *piece_freq, bool final) {
+    // sampled: join only pieces kept by the splitmix64 rule at rate p; every candidate pattern
+    // is returned with its sampled support and count and its 32 features.
+    LevelSet extend(const LevelSet &in_level, const uint8_t *piece_freq, bool final, bool sampled = false,
+                    double p = 1.0, const uint8_t *piece_sel = nullptr) {
         LevelSet in = in_level;
         const std::vector<int64_t> pat_off = group_by_pattern(in);
         const int L = in.L, K = L + 2;
@@ -395,7 +410,12 @@ struct Miner {
         A.mode = G->mode;
         A.pat_adj = in.adj8;
         A.piece_freq = piece_freq;
+        A.piece_sel = piece_sel;
         A.err = G->err;
+        A.sampled = sampled ? 1 : 0;
+        A.sample_seed = G->seed;
+        A.sample_thr = sampled ? (uint64_t)(p * 18446744073709551616.0) : 0;
+        const int64_t t_live = sampled ? 1 : t;   // sampled counts say nothing about reaching t
         // ---- pass 1: quick patterns and their embedding counts
         int64_t cap = (int64_t)1 << 20;
         while (cap < 4 * G->qp_hint[L] && cap < ((int64_t)1 << 30)) cap <<= 1;
@@ -469,7 +489,7 @@ struct Miner {
         int64_t *woff = mem.get<int64_t>(np * 8 + 1);
         int64_t *doff = mem.get<int64_t>(np * 8);
         void *stmp2 = mem.get<char>((int64_t)scan_temp_bytes(np * 8) + 16);
-        ck(launch_domain_sizes(K, plab, orbit, minorb, pcount, np, t, G->cls_size, live, words, st), "domain sizes");
+        ck(launch_domain_sizes(K, plab, orbit, minorb, pcount, np, t_live, G->cls_size, live, words, st), "domain sizes");
         ck(launch_scan_i64(words, woff, np * 8, stmp2, st), "domain scan");
         ck(launch_domain_offsets(words, woff, np * 8, doff, st), "domain offsets");
         const int64_t nwords = d2h(woff + np * 8, st);
@@ -500,10 +520,19 @@ struct Miner {
         unsigned long long *sigma = mem.get<unsigned long long>(np);
         ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
         ck(launch_support(K, orbit, live, doff, words, dom, np, sigma, st), "support");
+        float *feat = nullptr;
+        if (sampled && np > 0) {
+            int64_t *aut = mem.get<int64_t>(np);
+            feat = mem.get<float>(np * 32);
+            ck(launch_aut_size(K, plab, padj, np, aut, st), "automorphisms");
+            ck(launch_features(K, plab, padj, orbit, doff, words, dom, pcount, G->cls_size, G->cls_off, G->by_rank,
+                               G->row_ptr, G->n, p, t, np, aut, feat, st), "features");
+            mem.release(aut);
+        }
         int64_t *fflag = mem.get<int64_t>(np + 1);
         int64_t *fscan = mem.get<int64_t>(np + 1);
         int32_t *newid = mem.get<int32_t>(np);
-        ck(launch_freq_flags(sigma, np, t, fflag, st), "frequent flags");
+        ck(launch_freq_flags(sigma, np, sampled ? 1 : t, fflag, st), "frequent flags");
         ck(launch_scan_i64(fflag, fscan, np, stmp2, st), "frequent scan");
         ck(launch_new_ids(fflag, fscan, np, newid, st), "new ids");
         const int64_t nf = d2h(fscan + np, st);
@@ -518,6 +547,11 @@ struct Miner {
         out.count = mem.get<unsigned long long>(nf);
         ck(launch_gather_frequent(K, newid, np, plab, padj, sigma, pcount, out.clab, out.cadj, out.sigma,
                                   out.count, out.lab8, out.adj8, st), "gather");
+        if (feat) {
+            // every sampled pattern has a nonzero popcount, so the frequent ids are the identity
+            if (nf != np) fail(FSM_ECUDA, "sampled level lost candidate patterns");
+            out.feat = feat;
+        }
         if (!final && nf > 0) {
             // ---- pass 3: store the frequent size-K embeddings in canonical order
             unsigned long long *sum = mem.get<unsigned long long>(1);
@@ -668,6 +702,134 @@ void fill_result(fsm_result *r, const LevelSet &s, int k, cudaStream_t st) {
         r->support[p] = (int64_t)sig[p];
         r->count[p] = (int64_t)cnt[p];
     }
+    r->exact.assign((size_t)P, 1);
+}
+
+// Sampled mining, after the sampled last level `cand` (every candidate pattern with its
+// smallest sampled orbit popcount in sigma, sampled embedding count, features):
+//   option "candidates": return them all with estimates and features;
+//   with a model: predict log support; keep predictions >= log t + delta; recount exactly the
+//     patterns inside the band with an exact last level restricted to the stored patterns and
+//     pieces those patterns can be dissected into; drop the rest;
+//   without a model: keep the patterns whose estimate popcount / p reaches t.
+void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSet &stored, const uint8_t *pf,
+                    double p, int k) {
+    fsm_graph *G = m.G;
+    cudaStream_t st = m.st;
+    const int64_t P = cand.P;
+    std::vector<unsigned long long> lab((size_t)P), sig((size_t)P), cnt((size_t)P);
+    std::vector<uint32_t> adj((size_t)P);
+    std::vector<float> pred((size_t)P, 0.f), feat;
+    std::vector<uint8_t> keep((size_t)P, 0), unc((size_t)P, 0);
+    if (P) {
+        ck(cudaMemcpyAsync(lab.data(), cand.clab, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(adj.data(), cand.cadj, 4 * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(sig.data(), cand.sigma, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(cnt.data(), cand.count, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
+    }
+    // exact results of the recount, by canonical code
+    std::map<std::pair<unsigned long long, uint32_t>, std::pair<int64_t, int64_t>> exact;
+    const bool use_model = !G->candidates && G->model != nullptr;
+    if (G->candidates && P) {
+        feat.resize((size_t)P * 32);
+        ck(cudaMemcpyAsync(feat.data(), cand.feat, 4 * 32 * P, cudaMemcpyDeviceToHost, st), "copy");
+    }
+    if (use_model && P) {
+        float *dpred = m.mem.get<float>(P);
+        uint8_t *dkeep = m.mem.get<uint8_t>(P), *dunc = m.mem.get<uint8_t>(P);
+        const int rc = fsm_mlp_predict_device(G->model, cand.feat, P, dpred, st);
+        if (rc != FSM_OK) fail(rc, "support prediction failed");
+        ck(launch_decide(dpred, P, (float)std::log((double)m.t), (float)G->delta, dkeep, dunc, st), "decide");
+        ck(cudaMemcpyAsync(pred.data(), dpred, 4 * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(keep.data(), dkeep, P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(unc.data(), dunc, P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaStreamSynchronize(st), "sync");
+        const int64_t nunc = std::count(unc.begin(), unc.end(), (uint8_t)1);
+        m.rs.recount_patterns = nunc;
+        if (nunc > 0 && stored.N > 0) {
+            // parts the uncertain patterns can be dissected into
+            uint8_t *need_s = m.mem.get<uint8_t>(std::max<int64_t>(stored.P, 1));
+            uint8_t *need_p = m.mem.get<uint8_t>(FSM_PIECE_SPACE);
+            ck(cudaMemsetAsync(need_s, 0, std::max<int64_t>(stored.P, 1), st), "memset");
+            ck(cudaMemsetAsync(need_p, 0, FSM_PIECE_SPACE, st), "memset");
+            ck(launch_needed_parts(k, cand.clab, cand.cadj, dunc, P, stored.clab, stored.cadj, stored.P, need_s, need_p,
+                                   st), "needed parts");
+            if (pf) ck(launch_and_u8(need_p, pf, FSM_PIECE_SPACE, st), "and");
+            // stored embeddings of the needed patterns only
+            int64_t *flag = m.mem.get<int64_t>(stored.N);
+            int64_t *scanned = m.mem.get<int64_t>(stored.N + 1);
+            void *tmp = m.mem.get<char>((int64_t)scan_temp_bytes(stored.N) + 16);
+            ck(launch_flag_count(stored.fpid, stored.N, need_s, flag, st), "flags");
+            ck(launch_scan_i64(flag, scanned, stored.N, tmp, st), "scan");
+            const int64_t N2 = d2h(scanned + stored.N, st);
+            LevelSet sub = stored;
+            sub.N = N2;
+            sub.fv = m.mem.get<int32_t>(std::max<int64_t>(N2, 1) * stored.L);
+            sub.fpid = m.mem.get<int32_t>(std::max<int64_t>(N2, 1));
+            ck(launch_compact_frontier(stored.fv, stored.fpid, stored.N, stored.L, need_s, flag, scanned, tmp, sub.fv,
+                                       N2, sub.fpid, st), "compact");
+            // per-pattern counts of the restricted frontier (needed only by per-pattern launches)
+            if (G->launch != 0) {
+                unsigned long long *c2 = m.mem.get<unsigned long long>(std::max<int64_t>(stored.P, 1));
+                ck(cudaMemsetAsync(c2, 0, 8 * std::max<int64_t>(stored.P, 1), st), "memset");
+                ck(launch_keep_counts(stored.count, need_s, stored.P, c2, st), "counts");
+                sub.count = c2;
+            }
+            m.rs.recount_frontier = N2;
+            LevelSet ex = m.extend(sub, pf, true, false, 1.0, need_p);
+            std::vector<unsigned long long> el((size_t)ex.P), es((size_t)ex.P), ec((size_t)ex.P);
+            std::vector<uint32_t> ea((size_t)ex.P);
+            if (ex.P) {
+                ck(cudaMemcpyAsync(el.data(), ex.clab, 8 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
+                ck(cudaMemcpyAsync(ea.data(), ex.cadj, 4 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
+                ck(cudaMemcpyAsync(es.data(), ex.sigma, 8 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
+                ck(cudaMemcpyAsync(ec.data(), ex.count, 8 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
+            }
+            ck(cudaStreamSynchronize(st), "sync");
+            for (int64_t q = 0; q < ex.P; ++q) exact[{el[q], ea[q]}] = {(int64_t)es[q], (int64_t)ec[q]};
+        }
+    }
+    ck(cudaStreamSynchronize(st), "sync");
+    r->k = k;
+    const int np = k * (k - 1) / 2;
+    for (int64_t q = 0; q < P; ++q) {
+        const double est = (double)sig[q] / p;
+        int64_t sup = 0, c = 0;
+        int32_t ex = 0;
+        if (G->candidates) {
+            sup = (int64_t)std::llround(est);
+            c = (int64_t)std::llround((double)cnt[q] / p);
+        } else if (use_model) {
+            if (keep[q]) {
+                sup = (int64_t)std::llround(std::exp((double)pred[q]));
+                c = (int64_t)std::llround((double)cnt[q] / p);
+            } else if (unc[q]) {
+                auto it = exact.find({lab[q], adj[q]});
+                if (it == exact.end()) continue;   // recounted below t
+                sup = it->second.first;
+                c = it->second.second;
+                ex = 1;
+            } else {
+                continue;
+            }
+        } else {
+            if (est < (double)m.t) continue;
+            sup = (int64_t)std::llround(est);
+            c = (int64_t)std::llround((double)cnt[q] / p);
+        }
+        for (int cc = 0; cc < k; ++cc) r->labels.push_back((int32_t)((lab[q] >> (8 * (7 - cc))) & 0xff));
+        uint64_t bits = 0;
+        int qq = 0;
+        for (int i = 0; i < k; ++i)
+            for (int j = i + 1; j < k; ++j, ++qq)
+                if ((adj[q] >> (np - 1 - qq)) & 1u) bits |= 1ull << (i * k + j);
+        r->adj.push_back(bits);
+        r->support.push_back(sup);
+        r->count.push_back(c);
+        r->exact.push_back(ex);
+        if (G->candidates) r->features.insert(r->features.end(), feat.begin() + q * 32, feat.begin() + q * 32 + 32);
+    }
+    m.rs.candidates_sampled = P;
 }
 
 } // namespace
@@ -721,6 +883,9 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
         const int ew = d2h(g->err, st);
         if (ew) fail(FSM_EINVAL, "malformed CSR: rows must be sorted, symmetric, without self-loops or duplicates, labels in range");
         ck(launch_prepare(g->dg(), g->piece_cnt, g->end_off, g->rank, g->cls_size, st), "prepare");
+        dalloc((void **)&g->by_rank, sizeof(int32_t) * n);
+        dalloc((void **)&g->cls_off, sizeof(int64_t) * 65);
+        ck(launch_by_rank(g->dg(), num_labels, g->cls_size, g->cls_off, g->by_rank, st), "rank table");
         ck(cudaStreamSynchronize(st), "sync");
         *out = g;
         return FSM_OK;
@@ -739,6 +904,16 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
             g->mode = (int)value;
         } else if (k == "stream") {
             g->stream = value ? (cudaStream_t)(intptr_t)value : g->own_stream;
+        } else if (k == "seed") {
+            g->seed = (uint64_t)value;
+        } else if (k == "candidates") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "candidates must be 0 or 1");
+            g->candidates = (int)value;
+        } else if (k == "model") {
+            g->model = (const fsm_mlp *)(intptr_t)value;
+        } else if (k == "delta_milli") {
+            if (value < 0 || value > 20000) fail(FSM_EINVAL, "delta_milli must be in [0, 20000]");
+            g->delta = (double)value / 1000.0;
         } else if (k == "profile") {
             if (value != 0 && value != 1) fail(FSM_EINVAL, "profile must be 0 or 1");
             g->profile = (int)value;
@@ -774,7 +949,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         if (k < 1 || k > FSM_MAXK) fail(FSM_EINVAL, "k must be in [1, 8]");
         if (min_support < 1) fail(FSM_EINVAL, "min_support must be >= 1");
         if (!(sample_rate > 0.0 && sample_rate <= 1.0)) fail(FSM_EINVAL, "sample_rate must be in (0, 1]");
-        if (sample_rate < 1.0) fail(FSM_EUNSUPPORTED, "sampled mining is not available in this build");
+        const bool sampled = sample_rate < 1.0 && k >= 3;   // levels 1 and 2 join no pieces
         ck(cudaSetDevice(g->device), "cudaSetDevice");
         cudaStream_t st = g->stream;
         cudaEvent_t ev0, ev1, evf;
@@ -802,25 +977,38 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
             } else {
                 LevelSet s1 = m.level1(true);
                 const bool odd = (k & 1) != 0;
-                if (k == 3) ck(cudaEventRecord(evf, st), "event record");
-                LevelSet s3 = m.extend(s1, nullptr, k == 3 || !odd);
+                LevelSet stored = s1;            // the level the last one extends
+                const uint8_t *pf = nullptr;
                 if (k == 3) {
-                    res = s3;
+                    ck(cudaEventRecord(evf, st), "event record");
+                    res = m.extend(s1, nullptr, true, sampled, sample_rate);
                 } else {
-                    uint8_t *pf = mem.get<uint8_t>(FSM_PIECE_SPACE);
-                    ck(cudaMemsetAsync(pf, 0, FSM_PIECE_SPACE, st), "memset");
-                    ck(launch_piece_table(s3.clab, s3.cadj, s3.P, pf, st), "piece table");
+                    LevelSet s3 = m.extend(s1, nullptr, !odd);
+                    uint8_t *pfm = mem.get<uint8_t>(FSM_PIECE_SPACE);
+                    ck(cudaMemsetAsync(pfm, 0, FSM_PIECE_SPACE, st), "memset");
+                    ck(launch_piece_table(s3.clab, s3.cadj, s3.P, pfm, st), "piece table");
+                    pf = pfm;
                     LevelSet cur = odd ? s3 : m.level2(true);
                     while (cur.L + 2 <= k) {
                         const bool fin = cur.L + 2 == k;
-                        if (fin) ck(cudaEventRecord(evf, st), "event record");
-                        cur = m.extend(cur, pf, fin);
+                        if (fin) {
+                            ck(cudaEventRecord(evf, st), "event record");
+                            stored = cur;
+                        }
+                        cur = m.extend(cur, pf, fin, fin && sampled, sample_rate);
                     }
                     res = cur;
                 }
+                if (sampled) {
+                    ck(cudaEventRecord(ev1, st), "event record");
+                    finish_sampled(m, r, res, stored, pf, sample_rate, k);
+                    res.P = -1;   // result already filled
+                }
             }
-            ck(cudaEventRecord(ev1, st), "event record");
-            fill_result(r, res, k, st);
+            if (res.P >= 0) {
+                ck(cudaEventRecord(ev1, st), "event record");
+                fill_result(r, res, k, st);
+            }
             if (g->profile) {
                 unsigned long long pb[(FSM_MAXL + 1) * 3];
                 ck(cudaMemcpyAsync(pb, m.prof_bytes, sizeof(pb), cudaMemcpyDeviceToHost, st), "copy");
@@ -857,6 +1045,9 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["kernel_launches"] = (launches_so_far() - l0) + rs.launches;
         r->stats["time_ns"] = (int64_t)((double)ms * 1e6);
         r->stats["final_level_ns"] = (int64_t)((double)fms * 1e6);
+        r->stats["sampled_candidates"] = rs.candidates_sampled;
+        r->stats["recount_patterns"] = rs.recount_patterns;
+        r->stats["recount_frontier"] = rs.recount_frontier;
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["chunk_l" + std::to_string(L)] = g->tuned_chunk[L];
         const char *pn[3] = {"count", "domain", "emit"};
         for (int p = 0; p < 3; ++p) {
@@ -912,6 +1103,22 @@ int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, in
     return FSM_OK;
 }
 
+int fsm_result_exact(const fsm_result *r, int32_t *exact) {
+    if (!r || !exact) { g_last_error = "NULL argument"; return FSM_EINVAL; }
+    if (!r->exact.empty()) std::memcpy(exact, r->exact.data(), sizeof(int32_t) * r->exact.size());
+    return FSM_OK;
+}
+
+int fsm_result_features(const fsm_result *r, float *features) {
+    if (!r || !features) { g_last_error = "NULL argument"; return FSM_EINVAL; }
+    if (r->features.size() != r->support.size() * 32) {
+        g_last_error = "no features: mine with sample_rate < 1 and option candidates = 1";
+        return FSM_EINVAL;
+    }
+    if (!r->features.empty()) std::memcpy(features, r->features.data(), sizeof(float) * r->features.size());
+    return FSM_OK;
+}
+
 int fsm_result_stat(const fsm_result *r, const char *key, int64_t *value) {
     if (!r || !key || !value) { g_last_error = "NULL argument"; return FSM_EINVAL; }
     auto it = r->stats.find(key);
@@ -925,7 +1132,8 @@ void fsm_free_result(fsm_result *r) { delete r; }
 void fsm_free_graph(fsm_graph *g) {
     if (!g) return;
     cudaStream_t st = g->stream ? g->stream : g->own_stream;
-    void *ps[] = {g->row_ptr, g->col, g->labels, g->rank, g->cls_size, g->end_off, g->piece_cnt, g->err, g->stats};
+    void *ps[] = {g->row_ptr, g->col, g->labels, g->rank, g->cls_size, g->end_off, g->piece_cnt, g->err, g->stats,
+                  g->by_rank, g->cls_off};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, st);
     if (st) cudaStreamSynchronize(st);

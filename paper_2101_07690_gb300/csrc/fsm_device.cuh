@@ -111,6 +111,33 @@ FSM_HD uint64_t mix64(uint64_t x) {
     x ^= x >> 33; return x;
 }
 
+// ---------------------------------------------------------------------------- sampling
+//
+// Piece sampling for the sampled final level: a piece {x < y < z} is kept iff
+// h = H(H(H(seed) ^ x) ^ y) ^ z) < thr, thr = floor(p * 2^64), where H is one step of
+// splitmix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators", 2014):
+// add the golden gamma 0x9e3779b97f4a7c15, then the variant-13 mix.  All pieces on one vertex
+// triple share the decision.
+
+FSM_HD uint64_t splitmix_step(uint64_t x) {
+    uint64_t z = x + 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+FSM_HD bool keep_triple(uint64_t seed, uint64_t thr, int32_t a, int32_t b, int32_t c) {
+    int32_t t;
+    if (a > b) { t = a; a = b; b = t; }
+    if (b > c) { t = b; b = c; c = t; }
+    if (a > b) { t = a; a = b; b = t; }
+    uint64_t h = splitmix_step(seed);
+    h = splitmix_step(h ^ (uint64_t)(uint32_t)a);
+    h = splitmix_step(h ^ (uint64_t)(uint32_t)b);
+    h = splitmix_step(h ^ (uint64_t)(uint32_t)c);
+    return h < thr;
+}
+
 // ---------------------------------------------------------------------------- dissection
 //
 // Smallest-vertex-first dissection of a connected K-vertex subgraph into a 3-vertex part l and

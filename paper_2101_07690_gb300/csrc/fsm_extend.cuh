@@ -54,6 +54,8 @@ struct ExtArgs {
     const uint64_t *pat_adj;       // [P] 8 adjacency rows (one byte each) over canonical positions
     // frequent size-3 patterns, by piece index; NULL at level 1 (nothing is known yet)
     const uint8_t *piece_freq;
+    // optional restriction of the pieces joined (exact recount of sampled mining); NULL = all
+    const uint8_t *piece_sel;
     QPTab qp;
     // domains (PASS_DOMAIN)
     const uint8_t *live;           // [P'] pattern has domains
@@ -67,6 +69,9 @@ struct ExtArgs {
     int64_t out_N;
     unsigned long long *out_cursor;
     unsigned long long *stats;     // [0] joins tested, [1] joins accepted
+    // sampled final level: keep a piece iff keep_triple(seed, thr, piece vertices)
+    int sampled;
+    uint64_t sample_seed, sample_thr;
     int *err;
 };
 
@@ -227,6 +232,7 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
     constexpr int K = L + 2;
     const uint32_t pidx = piece_index(shape, pl[0], pl[1], pl[2]);
     if (A.piece_freq && !__ldg(A.piece_freq + pidx)) return;
+    if (A.piece_sel && !__ldg(A.piece_sel + pidx)) return;
     const int32_t v = S[i];
     const int jpos = pv[0] == v ? 0 : (pv[1] == v ? 1 : 2);
     const int q0 = jpos == 0 ? 1 : 0;
@@ -334,6 +340,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         const int32_t a = __ldg(g.col + rp + x), b = __ldg(g.col + rp + y);
         if (L == 1 && a < v) return;                 // size-3 subgraphs keyed at their smallest vertex
         if (in_s<L>(S, a) || in_s<L>(S, b)) return;
+        if (A.sampled && !keep_triple(A.sample_seed, A.sample_thr, v, a, b)) return;
         const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
         const bool tri = is_adj(g, a, b);
         if (A.mode == 0 || !tri) {
@@ -365,6 +372,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         if (b == v) return;
         if (L == 1 && (a < v || b < v)) return;
         if (in_s<L>(S, a) || in_s<L>(S, b)) return;
+        if (A.sampled && !keep_triple(A.sample_seed, A.sample_thr, v, a, b)) return;
         if (A.mode == 1 && is_adj(g, v, b)) return;  // the induced triple is the triangle (centre branch)
         const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
         pv[0] = a; pl[0] = la;

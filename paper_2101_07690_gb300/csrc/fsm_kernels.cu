@@ -931,6 +931,277 @@ cudaError_t launch_level2_tables(int32_t NL, const unsigned long long *pair_sigm
     return cudaGetLastError();
 }
 
+namespace {
+
+__global__ void class_offsets_kernel(int32_t NL, const int32_t *cls_size, int64_t *cls_off) {
+    if (gtid() != 0) return;
+    int64_t run = 0;
+    for (int l = 0; l < NL; ++l) { cls_off[l] = run; run += cls_size[l]; }
+    cls_off[NL] = run;
+}
+
+__global__ void by_rank_kernel(const DevGraph g, const int64_t *cls_off, int32_t *by_rank) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) by_rank[cls_off[g.labels[v]] + g.rank[v]] = (int32_t)v;
+}
+
+// one warp per (pattern, canonical position): popcount and mean log1p(degree) of the orbit's
+// sampled domain; lane 0 of the position-0 warp also writes the scalars
+__global__ void features_kernel(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj,
+                                const uint64_t *orbit, const int64_t *dom_off, const int64_t *words,
+                                const uint32_t *dom, const unsigned long long *pat_count,
+                                const int32_t *cls_size, const int64_t *cls_off, const int32_t *by_rank,
+                                const int32_t *row_ptr, int32_t n, float logp, float p, int64_t t,
+                                int64_t np, const int64_t *aut, float *feat) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = np * 8;
+    for (int64_t w = gtid() >> 5; w < nw; w += gstride() >> 5) {
+        const int64_t P = w >> 3;
+        const int c = (int)(w & 7);
+        float *f = feat + P * 32;
+        if (c >= K) {
+            if (lane == 0) { f[8 + c] = 0.f; f[16 + c] = 0.f; }
+            continue;
+        }
+        const int o = (int)((orbit[P] >> (8 * c)) & 0xff);
+        const int lab = (int)(pat_lab[P] >> (8 * (7 - c))) & 0xff;
+        const int64_t off = dom_off[P * 8 + o], nwd = words[P * 8 + o];
+        float sdeg = 0.f;
+        unsigned long long cnt = 0;
+        for (int64_t x = lane; x < nwd; x += 32) {
+            uint32_t bits = dom[off + x];
+            cnt += __popc(bits);
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int32_t v = by_rank[cls_off[lab] + x * 32 + b];
+                sdeg += log1pf((float)(row_ptr[v + 1] - row_ptr[v]));
+            }
+        }
+#pragma unroll
+        for (int s2 = 16; s2 > 0; s2 >>= 1) {
+            sdeg += __shfl_xor_sync(0xffffffffu, sdeg, s2);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, s2);
+        }
+        if (lane != 0) continue;
+        f[8 + c] = logf((float)cls_size[lab] / (float)n);
+        f[16 + c] = cnt ? sdeg / (float)cnt : 0.f;
+        if (c != 0) continue;
+        // orbit popcounts ascending (recount the representatives' bitmaps)
+        float pc[8];
+        int m = 0;
+        unsigned long long mn = ~0ull;
+        for (int cc = 0; cc < K; ++cc) {
+            if ((int)((orbit[P] >> (8 * cc)) & 0xff) != cc) continue;
+            const int64_t o2 = dom_off[P * 8 + cc], n2 = words[P * 8 + cc];
+            unsigned long long q = 0;
+            for (int64_t x = 0; x < n2; ++x) q += __popc(dom[o2 + x]);
+            if (q < mn) mn = q;
+            pc[m++] = log1pf((float)q);
+        }
+        for (int a = 1; a < m; ++a)
+            for (int b = a; b > 0 && pc[b - 1] > pc[b]; --b) { float tt = pc[b]; pc[b] = pc[b - 1]; pc[b - 1] = tt; }
+        for (int a = 0; a < 8; ++a) f[a] = a < m ? pc[a] : 0.f;
+        f[24] = (float)K;
+        f[25] = (float)__popc(pat_adj[P]);
+        f[26] = logp;
+        f[27] = log1pf((float)pat_count[P]);
+        f[28] = logf((float)t / (float)n);
+        f[29] = logf((float)aut[P]);
+        f[30] = logf(((float)mn + 1.f) / p);
+        f[31] = logf((float)n);
+    }
+}
+
+__global__ void aut_size_kernel(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+                                int64_t *aut) {
+    for (int64_t P = gtid(); P < np; P += gstride()) {
+        int lab[FSM_MAXK], perm[FSM_MAXK], seg[FSM_MAXK];
+        uint32_t adj[FSM_MAXK];
+        decode_code(K, pat_lab[P], pat_adj[P], lab, adj);
+        for (int c = 0; c < K; ++c) {
+            perm[c] = c;
+            seg[c] = (c > 0 && lab[c] == lab[c - 1]) ? seg[c - 1] : c;
+        }
+        int64_t a = 0;
+        do {
+            a += adj_code(K, adj, perm) == pat_adj[P];
+        } while (next_label_perm(K, seg, perm));
+        aut[P] = a;
+    }
+}
+
+} // namespace
+
+cudaError_t launch_by_rank(const DevGraph &g, int32_t NL, const int32_t *cls_size, int64_t *cls_off,
+                           int32_t *by_rank, cudaStream_t st) {
+    LAUNCHED(2);
+    class_offsets_kernel<<<1, 32, 0, st>>>(NL, cls_size, cls_off);
+    by_rank_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, cls_off, by_rank);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_aut_size(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+                            int64_t *aut, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    aut_size_kernel<<<blocks_for(np, 128), 128, 0, st>>>(K, pat_lab, pat_adj, np, aut);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_features(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, const uint64_t *orbit,
+                            const int64_t *dom_off, const int64_t *words, const uint32_t *dom,
+                            const unsigned long long *pat_count, const int32_t *cls_size, const int64_t *cls_off,
+                            const int32_t *by_rank, const int32_t *row_ptr, int32_t n, double p, int64_t t,
+                            int64_t np, const int64_t *aut, float *feat, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    features_kernel<<<blocks_for(np * 8 * 32), kThreads, 0, st>>>(K, pat_lab, pat_adj, orbit, dom_off, words, dom,
+                                                                  pat_count, cls_size, cls_off, by_rank, row_ptr, n,
+                                                                  (float)log(p), (float)p, t, np, aut, feat);
+    return cudaGetLastError();
+}
+
+namespace {
+
+__device__ bool mask_conn(uint32_t m, const uint32_t *adj, int K) { return mask_connected(m, adj, K); }
+
+__global__ void needed_parts_kernel(int K, const unsigned long long *lab, const uint32_t *adj, const uint8_t *uncertain,
+                                    int64_t np, const unsigned long long *s_lab, const uint32_t *s_adj, int64_t s_np,
+                                    uint8_t *need_s, uint8_t *need_piece) {
+    for (int64_t P = gtid(); P < np; P += gstride()) {
+        if (!uncertain[P]) continue;
+        int lb[FSM_MAXK];
+        uint32_t ad[FSM_MAXK];
+        decode_code(K, lab[P], adj[P], lb, ad);
+        const uint32_t all = (1u << K) - 1u;
+        for (uint32_t l = 0; l <= all; ++l) {
+            if (popc32(l) != 3) continue;
+            uint32_t la[FSM_MAXK];
+            for (int h = 0; h < K; ++h) la[h] = ad[h] & l;
+            if (!mask_conn(l, la, K)) continue;
+            // the piece: shape and labels of P restricted to l
+            int v3[3], c = 0;
+            for (int h = 0; h < K; ++h) if (l >> h & 1u) v3[c++] = h;
+            const uint32_t e01 = ad[v3[0]] >> v3[1] & 1u, e02 = ad[v3[0]] >> v3[2] & 1u, e12 = ad[v3[1]] >> v3[2] & 1u;
+            uint32_t pidx;
+            if (e01 && e02 && e12) pidx = tri_index(lb[v3[0]], lb[v3[1]], lb[v3[2]]);
+            else if (e01 && e02) pidx = wedge_index(lb[v3[0]], lb[v3[1]], lb[v3[2]]);
+            else if (e01 && e12) pidx = wedge_index(lb[v3[1]], lb[v3[0]], lb[v3[2]]);
+            else pidx = wedge_index(lb[v3[2]], lb[v3[0]], lb[v3[1]]);
+            for (int q = 0; q < 3; ++q) {
+                const uint32_t r = (all & ~l) | (1u << v3[q]);
+                uint32_t ra[FSM_MAXK];
+                for (int h = 0; h < K; ++h) ra[h] = ad[h] & r;
+                if (!mask_conn(r, ra, K)) continue;
+                need_piece[pidx] = 1;
+                // canonical code of the (K-2)-vertex part, then its id among the stored patterns
+                int sl[FSM_MAXK], map[FSM_MAXK], m = 0;
+                for (int h = 0; h < K; ++h) if (r >> h & 1u) { map[h] = m; sl[m++] = lb[h]; }
+                uint32_t sa[FSM_MAXK] = {0};
+                for (int h = 0; h < K; ++h) {
+                    if (!(r >> h & 1u)) continue;
+                    for (int h2 = 0; h2 < K; ++h2)
+                        if ((r >> h2 & 1u) && (ad[h] >> h2 & 1u)) sa[map[h]] |= 1u << map[h2];
+                }
+                unsigned long long cl;
+                uint32_t ca, inv;
+                canonicalise(m, sl, sa, cl, ca, inv);
+                int64_t lo = 0, hi = s_np;
+                while (lo < hi) {
+                    const int64_t mid = (lo + hi) >> 1;
+                    if (s_lab[mid] < cl || (s_lab[mid] == cl && s_adj[mid] < ca)) lo = mid + 1; else hi = mid;
+                }
+                if (lo < s_np && s_lab[lo] == cl && s_adj[lo] == ca) need_s[lo] = 1;
+            }
+        }
+    }
+}
+
+__global__ void flag_keep_kernel(const int32_t *fpid, int64_t N, const uint8_t *keep, int64_t *flag) {
+    for (int64_t e = gtid(); e < N; e += gstride()) flag[e] = keep[fpid[e]] ? 1 : 0;
+}
+
+__global__ void compact_frontier_kernel(const int32_t *fv, const int32_t *fpid, int64_t N, int L, const int64_t *flag,
+                                        const int64_t *scanned, int32_t *out_v, int64_t outN, int32_t *out_pid) {
+    for (int64_t e = gtid(); e < N; e += gstride()) {
+        if (!flag[e]) continue;
+        const int64_t pos = scanned[e];
+        for (int c = 0; c < L; ++c) out_v[(int64_t)c * outN + pos] = fv[(int64_t)c * N + e];
+        out_pid[pos] = fpid[e];
+    }
+}
+
+__global__ void and_u8_kernel(uint8_t *a, const uint8_t *b, int64_t n) {
+    for (int64_t i = gtid(); i < n; i += gstride()) a[i] = a[i] & b[i];
+}
+
+} // namespace
+
+cudaError_t launch_needed_parts(int K, const unsigned long long *lab, const uint32_t *adj, const uint8_t *uncertain,
+                                int64_t np, const unsigned long long *s_lab, const uint32_t *s_adj, int64_t s_np,
+                                uint8_t *need_s, uint8_t *need_piece, cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    needed_parts_kernel<<<blocks_for(np, 64), 64, 0, st>>>(K, lab, adj, uncertain, np, s_lab, s_adj, s_np, need_s, need_piece);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_count(const int32_t *fpid, int64_t N, const uint8_t *keep, int64_t *flag, cudaStream_t st) {
+    if (N <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    flag_keep_kernel<<<blocks_for(N), kThreads, 0, st>>>(fpid, N, keep, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_frontier(const int32_t *fv, const int32_t *fpid, int64_t N, int L, const uint8_t *keep,
+                                    int64_t *flag, int64_t *scanned, void *scan_tmp, int32_t *out_v, int64_t outN,
+                                    int32_t *out_pid, cudaStream_t st) {
+    (void)keep;
+    if (N <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    compact_frontier_kernel<<<blocks_for(N), kThreads, 0, st>>>(fv, fpid, N, L, flag, scanned, out_v, outN, out_pid);
+    (void)scan_tmp;
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void keep_counts_kernel(const unsigned long long *count, const uint8_t *keep, int64_t np, unsigned long long *out) {
+    for (int64_t P = gtid(); P < np; P += gstride()) out[P] = keep[P] ? count[P] : 0ull;
+}
+} // namespace
+
+cudaError_t launch_keep_counts(const unsigned long long *count, const uint8_t *keep, int64_t np, unsigned long long *out,
+                               cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    keep_counts_kernel<<<blocks_for(np), kThreads, 0, st>>>(count, keep, np, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_and_u8(uint8_t *a, const uint8_t *b, int64_t n, cudaStream_t st) {
+    LAUNCHED(1);
+    and_u8_kernel<<<blocks_for(n), kThreads, 0, st>>>(a, b, n);
+    return cudaGetLastError();
+}
+
+namespace {
+__global__ void decide_kernel(const float *pred, int64_t np, float logt, float delta, uint8_t *keep, uint8_t *unc) {
+    for (int64_t P = gtid(); P < np; P += gstride()) {
+        const float d = pred[P] - logt;
+        keep[P] = d >= delta ? 1 : 0;
+        unc[P] = (d < delta && d >= -delta) ? 1 : 0;
+    }
+}
+} // namespace
+
+cudaError_t launch_decide(const float *pred, int64_t np, float logt, float delta, uint8_t *keep, uint8_t *uncertain,
+                          cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    decide_kernel<<<blocks_for(np), kThreads, 0, st>>>(pred, np, logt, delta, keep, uncertain);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;

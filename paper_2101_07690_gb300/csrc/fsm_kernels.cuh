@@ -123,6 +123,49 @@ cudaError_t launch_level2_tables(int32_t NL, const unsigned long long *pair_sigm
 int64_t launches_so_far();
 void note_launches(int64_t n);
 
+// ---- sampled final level
+// by_rank[cls_off[l] + rank[v]] = v for every vertex v of label l (cls_off: exclusive prefix of
+// class sizes, computed by the kernel itself)
+cudaError_t launch_by_rank(const DevGraph &g, int32_t NL, const int32_t *cls_size, int64_t *cls_off,
+                           int32_t *by_rank, cudaStream_t st);
+// The 32 features of every candidate pattern of a sampled level (layout in fsm_api.cu):
+//   [0..8)   log1p of the sampled domain popcount of each orbit, ascending, zero-padded
+//   [8..16)  log(|V_l| / n) of the label of each canonical position, zero-padded
+//   [16..24) mean log1p(degree) over the sampled domain of each canonical position's orbit
+//   [24..32) k, edges, log p, log1p(sampled embeddings), log(t / n), log |Aut|,
+//            log((smallest popcount + 1) / p), log n
+cudaError_t launch_features(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, const uint64_t *orbit,
+                            const int64_t *dom_off, const int64_t *words, const uint32_t *dom,
+                            const unsigned long long *pat_count, const int32_t *cls_size, const int64_t *cls_off,
+                            const int32_t *by_rank, const int32_t *row_ptr, int32_t n, double p, int64_t t,
+                            int64_t np, const int64_t *aut, float *feat, cudaStream_t st);
+// Automorphism group size of each pattern (the orbits kernel enumerates the same orders)
+cudaError_t launch_aut_size(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+                            int64_t *aut, cudaStream_t st);
+
+// Exact recount of sampled mining: for every pattern with uncertain[P], every dissection of
+// its canonical graph into a connected 3-vertex part and a connected (K-2)-vertex part sharing
+// one vertex: mark the part's size-(K-2) pattern (its id found by binary search among the
+// sorted codes s_lab/s_adj of the stored level) in need_s and the piece in need_piece.
+cudaError_t launch_needed_parts(int K, const unsigned long long *lab, const uint32_t *adj, const uint8_t *uncertain,
+                                int64_t np, const unsigned long long *s_lab, const uint32_t *s_adj, int64_t s_np,
+                                uint8_t *need_s, uint8_t *need_piece, cudaStream_t st);
+// keep the stored embeddings whose pattern is flagged: out has room for N rows
+cudaError_t launch_compact_frontier(const int32_t *fv, const int32_t *fpid, int64_t N, int L, const uint8_t *keep,
+                                    int64_t *flag, int64_t *scanned, void *scan_tmp, int32_t *out_v, int64_t outN,
+                                    int32_t *out_pid, cudaStream_t st);
+cudaError_t launch_flag_count(const int32_t *fpid, int64_t N, const uint8_t *keep, int64_t *flag, cudaStream_t st);
+cudaError_t launch_and_u8(uint8_t *a, const uint8_t *b, int64_t n, cudaStream_t st);
+// out[P] = keep[P] ? count[P] : 0
+cudaError_t launch_keep_counts(const unsigned long long *count, const uint8_t *keep, int64_t np, unsigned long long *out,
+                               cudaStream_t st);
+
+// decision of sampled mining with a model: pred = predicted log support; keep[P] = 1 when
+// pred >= logt + delta, uncertain[P] = 1 when |pred - logt| <= delta (strictly inside: below
+// logt + delta)
+cudaError_t launch_decide(const float *pred, int64_t np, float logt, float delta, uint8_t *keep, uint8_t *uncertain,
+                          cudaStream_t st);
+
 // ---- pieces: mark the frequent size-3 patterns by piece index
 cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st);

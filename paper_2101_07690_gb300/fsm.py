@@ -26,7 +26,12 @@ _NAMES = {FSM_EINVAL: "FSM_EINVAL", FSM_ENOMEM: "FSM_ENOMEM", FSM_ECUDA: "FSM_EC
 # every entry point that include/fsm.h declares
 EXPORTS = ["fsm_load_graph", "fsm_set_option", "fsm_mine", "fsm_result_count", "fsm_result_get",
            "fsm_result_embeddings", "fsm_result_copy", "fsm_result_stat", "fsm_free_result",
-           "fsm_free_graph", "fsm_last_error", "fsm_debug_dissect", "fsm_edge_supports_noalloc"]
+           "fsm_free_graph", "fsm_last_error", "fsm_debug_dissect", "fsm_edge_supports_noalloc",
+           "fsm_result_exact", "fsm_result_features", "fsm_mlp_create", "fsm_mlp_set_params",
+           "fsm_mlp_get_params", "fsm_mlp_set_norm", "fsm_mlp_gradients", "fsm_mlp_train",
+           "fsm_mlp_predict", "fsm_mlp_predict_device", "fsm_mlp_free"]
+
+MLP_NPARAM = 32 * 64 + 64 + 64 * 64 + 64 + 64 + 1
 
 
 class FsmError(RuntimeError):
@@ -63,6 +68,19 @@ def load(path: str | None = None):
         "fsm_last_error": (ctypes.c_char_p, []),
         "fsm_debug_dissect": (ctypes.c_int, [i32, P(i32), P(ctypes.c_uint32), P(ctypes.c_uint32), P(i32), P(i32)]),
         "fsm_edge_supports_noalloc": (ctypes.c_int, [vp, vp, vp, i32, i32, vp, vp, vp]),
+        "fsm_result_exact": (ctypes.c_int, [vp, P(i32)]),
+        "fsm_result_features": (ctypes.c_int, [vp, P(ctypes.c_float)]),
+        "fsm_mlp_create": (ctypes.c_int, [u64, P(vp)]),
+        "fsm_mlp_set_params": (ctypes.c_int, [vp, P(ctypes.c_float)]),
+        "fsm_mlp_get_params": (ctypes.c_int, [vp, P(ctypes.c_float)]),
+        "fsm_mlp_set_norm": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float)]),
+        "fsm_mlp_gradients": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float), i64, P(ctypes.c_float),
+                                             P(ctypes.c_float)]),
+        "fsm_mlp_train": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float), i64, i32, i32, ctypes.c_float,
+                                         u64, P(ctypes.c_float)]),
+        "fsm_mlp_predict": (ctypes.c_int, [vp, P(ctypes.c_float), i64, P(ctypes.c_float)]),
+        "fsm_mlp_predict_device": (ctypes.c_int, [vp, vp, i64, vp, vp]),
+        "fsm_mlp_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -182,10 +200,82 @@ def fsm_edge_supports_noalloc(d_row_ptr: int, d_col: int, d_labels: int, n: int,
                                             d_support, d_count, stream or None))
 
 
+def fsm_result_exact(r: int) -> np.ndarray:
+    out = np.zeros(fsm_result_count(r), np.int32)
+    _check(load().fsm_result_exact(r, _ptr(out, ctypes.c_int32)))
+    return out
+
+
+def fsm_result_features(r: int) -> np.ndarray:
+    out = np.zeros((fsm_result_count(r), 32), np.float32)
+    _check(load().fsm_result_features(r, _ptr(out, ctypes.c_float)))
+    return out
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def fsm_mlp_create(seed: int = 0) -> int:
+    m = ctypes.c_void_p()
+    _check(load().fsm_mlp_create(int(seed), ctypes.byref(m)))
+    return m.value
+
+
+def fsm_mlp_set_params(m: int, params) -> None:
+    p = _f32(params).reshape(MLP_NPARAM)
+    _check(load().fsm_mlp_set_params(m, _ptr(p, ctypes.c_float)))
+
+
+def fsm_mlp_get_params(m: int) -> np.ndarray:
+    out = np.zeros(MLP_NPARAM, np.float32)
+    _check(load().fsm_mlp_get_params(m, _ptr(out, ctypes.c_float)))
+    return out
+
+
+def fsm_mlp_set_norm(m: int, mean, stdev) -> None:
+    mu, sd = _f32(mean).reshape(32), _f32(stdev).reshape(32)
+    _check(load().fsm_mlp_set_norm(m, _ptr(mu, ctypes.c_float), _ptr(sd, ctypes.c_float)))
+
+
+def fsm_mlp_gradients(m: int, X, Y):
+    X, Y = _f32(X).reshape(-1, 32), _f32(Y).reshape(-1)
+    g = np.zeros(MLP_NPARAM, np.float32)
+    loss = ctypes.c_float()
+    _check(load().fsm_mlp_gradients(m, _ptr(X, ctypes.c_float), _ptr(Y, ctypes.c_float), len(Y),
+                                    _ptr(g, ctypes.c_float), ctypes.byref(loss)))
+    return g, float(loss.value)
+
+
+def fsm_mlp_train(m: int, X, Y, epochs: int, batch: int, lr: float, seed: int = 0) -> float:
+    X, Y = _f32(X).reshape(-1, 32), _f32(Y).reshape(-1)
+    loss = ctypes.c_float()
+    _check(load().fsm_mlp_train(m, _ptr(X, ctypes.c_float), _ptr(Y, ctypes.c_float), len(Y), int(epochs),
+                                int(batch), float(lr), int(seed), ctypes.byref(loss)))
+    return float(loss.value)
+
+
+def fsm_mlp_predict(m: int, X) -> np.ndarray:
+    X = _f32(X).reshape(-1, 32)
+    out = np.zeros(len(X), np.float32)
+    _check(load().fsm_mlp_predict(m, _ptr(X, ctypes.c_float), len(X), _ptr(out, ctypes.c_float)))
+    return out
+
+
+def fsm_mlp_predict_device(m: int, d_X: int, n: int, d_out: int, stream: int = 0) -> None:
+    _check(load().fsm_mlp_predict_device(m, d_X, int(n), d_out, stream or None))
+
+
+def fsm_mlp_free(m: int) -> None:
+    if m:
+        load().fsm_mlp_free(m)
+
+
 STATS = ["k", "levels", "candidates", "embeddings", "final_embeddings", "quick_patterns", "patterns",
          "live_patterns", "frontier_max", "kernel_launches", "time_ns", "final_level_ns",
          "count_ns", "domain_ns", "emit_ns", "count_launches", "domain_launches", "emit_launches",
-         "count_bytes", "domain_bytes", "emit_bytes"] + [
+         "count_bytes", "domain_bytes", "emit_bytes", "sampled_candidates", "recount_patterns",
+         "recount_frontier"] + [
              f"{p}_{f}_l{l}" for p in ("count", "domain", "emit") for f in ("ns", "launches", "bytes")
              for l in range(1, 7)] + [f"chunk_l{l}" for l in range(1, 7)]
 
@@ -208,10 +298,13 @@ class Graph:
     def set_option(self, key: str, value: int):
         fsm_set_option(self.handle, key, value)
 
-    def mine(self, k: int, t: int, sample_rate: float = 1.0, stats: bool = False):
+    def mine(self, k: int, t: int, sample_rate: float = 1.0, stats: bool = False, features: bool = False):
         r = fsm_mine(self.handle, k, t, sample_rate)
         try:
             out = fsm_result_copy(r, k)
+            out["exact"] = fsm_result_exact(r)
+            if features:
+                out["features"] = fsm_result_features(r)
             if stats:
                 out["stats"] = {s: fsm_result_stat(r, s) for s in STATS}
         finally:

@@ -117,3 +117,22 @@ def test_dissect_total_and_valid(fsm, k):
             front = nx
         assert seen == rm
     print(f"k={k}: fallback rule used {fallbacks} times")
+
+
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_dissect_agrees_with_oracle(fsm, k):
+    """The library's dissection rule and the oracle's (both written from Algorithm 1 with the
+    same exhaustive fallback) pick the same 3-vertex part on every connected graph."""
+    import oracle
+    pairs = [(i, j) for i in range(k) for j in range(i + 1, k)]
+    ids = list(range(k))
+    for mask in range(1 << len(pairs)):
+        rows = [0] * k
+        for q, (a, b) in enumerate(pairs):
+            if mask >> q & 1:
+                rows[a] |= 1 << b
+                rows[b] |= 1 << a
+        if not _connected(k, rows):
+            continue
+        lm, _, _ = fsm.fsm_debug_dissect(ids, rows)
+        assert oracle.dissect(rows) == lm, (k, rows)

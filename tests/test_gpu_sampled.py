@@ -1,0 +1,166 @@
+"""Sampled mining and the support-prediction network on the GPU.
+
+* The sampled last level against the oracle: an embedding is kept iff the 3-vertex part of its
+  smallest-vertex-first dissection passes the splitmix64 rule; for every exactly frequent
+  pattern (all of whose embeddings the GPU generates) the sampled MNI support and embedding
+  count agree exactly, and for the other candidates the GPU's (pruned) values never exceed
+  the oracle's.
+* The network's forward pass, gradient and Adam step against the float64 reference
+  (oracle/mlp.py), with the GPU's BF16-rounded weights.
+* Sampled mining with a trained network: exactly recounted supports are exact, and the
+  network's decisions beat the plain estimator on held-out graphs.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+import oracle.mlp as ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fsm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2101_07690_gb300 import build, fsm as f
+    build.build()
+    f.load()
+    return f
+
+
+def _keys(res, k):
+    return [tuple(int(x) for x in l) + (int(a),) for l, a in zip(res["labels"], res["adj"])]
+
+
+@pytest.mark.parametrize("case", [("er1000", 3, 10, 0.25), ("er1000", 4, 10, 0.25), ("er1000", 5, 10, 0.5),
+                                  ("cl", 4, 5, 0.1), ("cl", 4, 5, 0.5)])
+def test_sampled_candidates_match_oracle(fsm, case):
+    name, k, t, p = case
+    g = gg.workload("er1000") if name == "er1000" else gg.workload("cl100k", scale=0.005, cap=30)
+    seed = 12345
+    G = fsm.Graph.from_graphgen(g)
+    G.set_option("candidates", 1)
+    G.set_option("seed", seed)
+    got = G.mine(k, t, sample_rate=p, features=True, stats=True)
+    G.close()
+    o = oracle.mine(g, k, 1, sample=(p, seed))
+    okeys = {q: i for i, q in enumerate(_keys(o, k))}
+    checked = 0
+    for i, q in enumerate(_keys(got, k)):
+        j = okeys[q]
+        est_s = int(np.rint(o["ssupport"][j] / p))
+        est_c = int(np.rint(o["scount"][j] / p))
+        if o["support"][j] >= t:
+            assert (int(got["support"][i]), int(got["count"][i])) == (est_s, est_c), q
+            checked += 1
+        else:
+            assert got["support"][i] <= est_s and got["count"][i] <= est_c, q
+    # every exactly frequent pattern with a kept embedding is a candidate
+    cand = set(_keys(got, k))
+    for q, j in okeys.items():
+        if o["support"][j] >= t and o["scount"][j] > 0:
+            assert q in cand, q
+    assert checked > 0
+    assert np.all(got["exact"] == 0)
+    assert got["features"].shape == (len(got["support"]), 32) and np.all(np.isfinite(got["features"]))
+
+
+def _random_net(fsm, seed):
+    rng = np.random.default_rng(seed)
+    theta = rng.normal(0, 0.25, ref.NPARAM).astype(np.float32)
+    mean = rng.normal(0, 1, 32).astype(np.float32)
+    sd = rng.uniform(0.5, 2, 32).astype(np.float32)
+    m = fsm.fsm_mlp_create(seed)
+    fsm.fsm_mlp_set_params(m, theta)
+    fsm.fsm_mlp_set_norm(m, mean, sd)
+    X = rng.normal(0, 2, (777, 32)).astype(np.float32)
+    Y = rng.normal(0, 1, 777).astype(np.float32)
+    return m, theta, mean, sd, X, Y
+
+
+def test_mlp_forward_and_gradient_match_reference(fsm):
+    m, theta, mean, sd, X, Y = _random_net(fsm, 3)
+    try:
+        p = ref.gpu_weights(theta)
+        y_ref, _ = ref.forward(p, X, mean.astype(np.float64), sd.astype(np.float64))
+        y_gpu = fsm.fsm_mlp_predict(m, X)
+        # FP32 accumulation of <= 64-term products of BF16 weights and FP32 activations
+        assert np.allclose(y_gpu, y_ref, rtol=1e-4, atol=1e-4)
+        loss_ref, g_ref = ref.loss_and_grad(p, X, Y, mean.astype(np.float64), sd.astype(np.float64))
+        g_gpu, loss_gpu = fsm.fsm_mlp_gradients(m, X, Y)
+        assert abs(loss_gpu - loss_ref) <= 1e-4 * max(1.0, loss_ref)
+        assert np.allclose(g_gpu, g_ref, rtol=1e-3, atol=1e-5 * max(1.0, float(np.abs(g_ref).max())))
+    finally:
+        fsm.fsm_mlp_free(m)
+
+
+def test_adam_step_matches_reference(fsm):
+    m, theta, mean, sd, X, Y = _random_net(fsm, 5)
+    try:
+        p = ref.gpu_weights(theta)
+        _, g = ref.loss_and_grad(p, X, Y, mean.astype(np.float64), sd.astype(np.float64))
+        th_ref, _, _ = ref.adam_step(theta.astype(np.float64), np.zeros(ref.NPARAM), np.zeros(ref.NPARAM), g, 1, 1e-3)
+        fsm.fsm_mlp_train(m, X, Y, epochs=1, batch=len(Y), lr=1e-3, seed=0)
+        th_gpu = fsm.fsm_mlp_get_params(m)
+        # the first Adam step moves each weight by about lr * sign(g); compare the moves
+        assert np.allclose(th_gpu - theta, th_ref - theta, atol=2e-5)
+    finally:
+        fsm.fsm_mlp_free(m)
+
+
+def test_training_fits_a_smooth_function(fsm):
+    rng = np.random.default_rng(9)
+    X = rng.normal(0, 1, (4096, 32)).astype(np.float32)
+    Y = (np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2]).astype(np.float32)
+    m = fsm.fsm_mlp_create(1)
+    try:
+        fsm.fsm_mlp_set_norm(m, np.zeros(32), np.ones(32))
+        _, l0 = fsm.fsm_mlp_gradients(m, X, Y)
+        l1 = fsm.fsm_mlp_train(m, X, Y, epochs=60, batch=128, lr=3e-3, seed=2)
+        assert l1 < 0.2 * l0
+    finally:
+        fsm.fsm_mlp_free(m)
+
+
+def test_learned_sampling_recounts_exactly_and_beats_the_plain_estimator(fsm):
+    from paper_2101_07690_gb300 import learn
+    k, p = 4, 0.1
+    train = [gg.workload("cl100k", scale=0.03, cap=60, seed=s) for s in range(10, 16)]
+    held = [gg.workload("cl100k", scale=0.03, cap=60, seed=s) for s in (40, 41)]
+    t = 30
+    Xs, ys = [], []
+    for g in train:
+        X, y, _ = learn.training_pairs(g, k, t, p, seed=1)
+        Xs.append(X)
+        ys.append(y)
+    X, y = np.concatenate(Xs), np.concatenate(ys)
+    m = learn.fit(X, y, epochs=200, batch=256, lr=3e-3, seed=0)
+    try:
+        stats = {"model": [], "plain": []}
+        for g in held:
+            G = fsm.Graph.from_graphgen(g)
+            exact = learn.frequent_set(G.mine(k, t), k)
+            G.set_option("seed", 1)
+            plain = G.mine(k, t, sample_rate=p)
+            G.set_option("model", m)
+            G.set_option("delta_milli", 700)
+            learned = G.mine(k, t, sample_rate=p)
+            G.close()
+            # exactly recounted supports are the exact ones
+            for q, s, e in zip(_keys(learned, k), learned["support"], learned["exact"]):
+                if e:
+                    assert exact.get(q) == int(s)
+            stats["model"].append(learn.compare(exact, learn.frequent_set(learned, k)))
+            stats["plain"].append(learn.compare(exact, learn.frequent_set(plain, k)))
+        rec_m = np.mean([s["recall"] for s in stats["model"]])
+        rec_p = np.mean([s["recall"] for s in stats["plain"]])
+        f1 = lambda s: 2 * s["precision"] * s["recall"] / max(s["precision"] + s["recall"], 1e-9)
+        f1_m = np.mean([f1(s) for s in stats["model"]])
+        f1_p = np.mean([f1(s) for s in stats["plain"]])
+        print("learned", stats["model"], "plain", stats["plain"])
+        assert f1_m >= f1_p and rec_m >= rec_p
+    finally:
+        fsm.fsm_mlp_free(m)

@@ -244,3 +244,80 @@ def test_er1000_runs_quickly():
     assert np.all(o["support"] >= 30)
     # label sequences are nondecreasing in canonical order
     assert np.all(np.diff(o["labels"], axis=1) >= 0)
+
+
+# --------------------------------------------------------------------- one-pattern matcher
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_pattern_matcher_agrees_with_enumeration(mode, seed):
+    """oracle.pattern_support (backtracking over label-preserving maps) and oracle.mine (ESU
+    plus canonical codes) are independent; they must agree on every pattern."""
+    g = gg.random_small(9, 0.4, 2, seed)
+    for k in (1, 2, 3, 4, 5):
+        o = oracle.mine(g, k, 1, mode)
+        for lab, adj, s, c in zip(o["labels"], o["adj"], o["support"], o["count"]):
+            assert oracle.pattern_support(g, lab, int(adj), mode) == (int(s), int(c))
+
+
+def test_pattern_matcher_closed_forms():
+    # path P_k inside P_9: sigma = 9 - 2*floor((k-1)/2), 9-k+1 embeddings
+    for k in (2, 3, 4, 5):
+        adj = sum(1 << (i * k + i + 1) for i in range(k - 1))
+        assert oracle.pattern_support(gg.path(9), [0] * k, adj) == (9 - 2 * ((k - 1) // 2), 9 - k + 1)
+    # triangle in K_5: sigma 5, C(5,3) embeddings; absent pattern gives (0, 0)
+    assert oracle.pattern_support(gg.complete(5), [0, 0, 0], 2 + 4 + 32) == (5, 10)
+    assert oracle.pattern_support(gg.path(6), [0, 0, 0], 2 + 4 + 32) == (0, 0)
+    # star K_{1,3} centred at position 0 has 8 * 7 * 6 * 5 maps into K_8
+    with pytest.raises(OverflowError):
+        oracle.pattern_support(gg.complete(8), [0, 0, 0, 0], 2 + 4 + 8, max_maps=10)
+
+
+# --------------------------------------------------------------------- network reference
+
+def test_mlp_reference_gradient_matches_finite_differences():
+    import oracle.mlp as mlp
+    rng = np.random.default_rng(0)
+    theta = rng.normal(0, 0.3, mlp.NPARAM)
+    X = rng.normal(0, 1, (16, 32))
+    Y = rng.normal(0, 1, 16)
+    mu, sd = np.zeros(32), np.ones(32)
+    p = mlp.unpack(theta)
+    loss, g = mlp.loss_and_grad(p, X, Y, mu, sd)
+    for idx in rng.choice(mlp.NPARAM, size=60, replace=False):
+        h = 1e-6
+        tp, tm = theta.copy(), theta.copy()
+        tp[idx] += h
+        tm[idx] -= h
+        num = (mlp.loss_and_grad(mlp.unpack(tp), X, Y, mu, sd)[0] - mlp.loss_and_grad(mlp.unpack(tm), X, Y, mu, sd)[0]) / (2 * h)
+        assert abs(num - g[idx]) <= 1e-6 + 1e-5 * abs(num), idx
+
+
+def test_mlp_reference_closed_form():
+    """With W1 = I on the first 32 units, W2 = I, w3 = e_0 and zero biases the network returns
+    relu(x'_0); the loss against 0 is mean(relu(x_0)^2)."""
+    import oracle.mlp as mlp
+    parts = {"W1": np.eye(32, 64), "b1": np.zeros(64), "W2": np.eye(64), "b2": np.zeros(64),
+             "w3": np.eye(64)[0], "b3": np.zeros(1)}
+    X = np.zeros((4, 32))
+    X[:, 0] = [-1.0, 0.5, 2.0, 3.0]
+    y, _ = mlp.forward(parts, X, np.zeros(32), np.ones(32))
+    assert np.allclose(y, [0.0, 0.5, 2.0, 3.0])
+    loss, _ = mlp.loss_and_grad(parts, X, np.zeros(4), np.zeros(32), np.ones(32))
+    assert np.isclose(loss, (0.25 + 4 + 9) / 4)
+
+
+def test_bf16_rounding():
+    import oracle.mlp as mlp
+    # 1 + 2^-8 is halfway between bfloat16 neighbours 1 and 1 + 2^-7: ties to even gives 1
+    assert mlp.bf16_round(np.float32(1 + 2 ** -8)) == 1.0
+    assert mlp.bf16_round(np.float32(1 + 3 * 2 ** -8)) == 1 + 2 ** -6
+    assert mlp.bf16_round(np.float32(-2.0)) == -2.0
+
+
+def test_adam_reference_first_step():
+    """Adam's first bias-corrected step moves each weight by lr * sign(g) (up to eps)."""
+    import oracle.mlp as mlp
+    g = np.array([0.5, -2.0, 1e-3])
+    th, m, v = mlp.adam_step(np.zeros(3), np.zeros(3), np.zeros(3), g, 1, 0.01)
+    assert np.allclose(th, -0.01 * np.sign(g), atol=1e-6)
