@@ -324,7 +324,9 @@ struct Miner {
     // Frontier grouped by pattern id (launch mode 2): returns host offsets, P+1 entries.
     std::vector<int64_t> group_by_pattern(LevelSet &in) {
         std::vector<int64_t> off;
-        if (G->launch == 0 || in.N == 0 || in.P == 0) return off;
+        // per-pattern launches need the frontier grouped; the persistent launch keeps the emission
+        // order, whose consecutive units share key vertices (measured faster than grouping)
+        if (G->launch != 2 || in.N == 0 || in.P == 0) return off;
         int64_t *cnt = mem.get<int64_t>(in.P);
         int64_t *doff = mem.get<int64_t>(in.P + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(in.P) + 16);

@@ -178,6 +178,32 @@ FSM_HD int smallest_in(uint32_t m, const int32_t *gid, int K) {
     return best;
 }
 
+// The exhaustive rule, out of line: it almost never runs, and keeping it out of the join path
+// keeps that path small in the instruction cache.
+static __host__ __device__ __noinline__ void dissect3_exhaustive(int K, const int32_t *gid, const uint32_t *adj,
+                                                         uint32_t &l_mask, int &join) {
+    const uint32_t all = (1u << K) - 1u;
+    l_mask = 0; join = -1;
+    int32_t bk0 = 0, bk1 = 0, bk2 = 0, bkv = 0;
+    for (uint32_t m = 0; m <= all; ++m) {
+        if (popc32(m) != 3 || !mask_connected(m, adj, K)) continue;
+        int32_t ids[3]; int c = 0;
+        for (int h = 0; h < K; ++h) if (m >> h & 1u) ids[c++] = gid[h];
+        int32_t t;
+        if (ids[0] > ids[1]) { t = ids[0]; ids[0] = ids[1]; ids[1] = t; }
+        if (ids[1] > ids[2]) { t = ids[1]; ids[1] = ids[2]; ids[2] = t; }
+        if (ids[0] > ids[1]) { t = ids[0]; ids[0] = ids[1]; ids[1] = t; }
+        for (int h = 0; h < K; ++h) {
+            if (!(m >> h & 1u)) continue;
+            if (!mask_connected((all & ~m) | (1u << h), adj, K)) continue;
+            bool better = l_mask == 0 ||
+                ids[0] < bk0 || (ids[0] == bk0 && (ids[1] < bk1 || (ids[1] == bk1 &&
+                (ids[2] < bk2 || (ids[2] == bk2 && gid[h] < bkv)))));
+            if (better) { l_mask = m; join = h; bk0 = ids[0]; bk1 = ids[1]; bk2 = ids[2]; bkv = gid[h]; }
+        }
+    }
+}
+
 // Returns true when the greedy rule answered, false when the exhaustive rule did.
 // l_mask = 0 means no dissection exists (the input was not connected).
 FSM_HD bool dissect3(int K, const int32_t *gid, const uint32_t *adj, uint32_t &l_mask, int &join) {
@@ -205,26 +231,7 @@ FSM_HD bool dissect3(int K, const int32_t *gid, const uint32_t *adj, uint32_t &l
             if (mask_connected(rest | (1u << hv), adj, K)) { l_mask = vis; join = hv; return true; }
         }
     }
-    // exhaustive rule
-    l_mask = 0; join = -1;
-    int32_t bk0 = 0, bk1 = 0, bk2 = 0, bkv = 0;
-    for (uint32_t m = 0; m <= all; ++m) {
-        if (popc32(m) != 3 || !mask_connected(m, adj, K)) continue;
-        int32_t ids[3]; int c = 0;
-        for (int h = 0; h < K; ++h) if (m >> h & 1u) ids[c++] = gid[h];
-        int32_t t;
-        if (ids[0] > ids[1]) { t = ids[0]; ids[0] = ids[1]; ids[1] = t; }
-        if (ids[1] > ids[2]) { t = ids[1]; ids[1] = ids[2]; ids[2] = t; }
-        if (ids[0] > ids[1]) { t = ids[0]; ids[0] = ids[1]; ids[1] = t; }
-        for (int h = 0; h < K; ++h) {
-            if (!(m >> h & 1u)) continue;
-            if (!mask_connected((all & ~m) | (1u << h), adj, K)) continue;
-            bool better = l_mask == 0 ||
-                ids[0] < bk0 || (ids[0] == bk0 && (ids[1] < bk1 || (ids[1] == bk1 &&
-                (ids[2] < bk2 || (ids[2] == bk2 && gid[h] < bkv)))));
-            if (better) { l_mask = m; join = h; bk0 = ids[0]; bk1 = ids[1]; bk2 = ids[2]; bkv = gid[h]; }
-        }
-    }
+    dissect3_exhaustive(K, gid, adj, l_mask, join);
     return false;
 }
 

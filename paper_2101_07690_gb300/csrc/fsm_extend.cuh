@@ -142,6 +142,9 @@ __device__ __forceinline__ bool in_s(const int32_t (&S)[L], int32_t x) {
 
 struct Tally { unsigned long long tested, accepted; };
 
+// neighbour-adjacency masks of single-unit chunks: key vertices of degree up to 32 * this
+#define FSM_MASK_WORDS 64
+
 // Per-block aggregation of quick-pattern counts (PASS_COUNT).  Hot keys (the dominant label
 // patterns) would otherwise serialise on one global counter; each block sums them in shared
 // memory and flushes once when the persistent loop ends.
@@ -224,11 +227,34 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
 // Join s (vertices S, pattern pid, key position i) with one piece.  Piece vertices pv[0..2]
 // are in the piece's own order, pl their labels; shape is PIECE_WEDGE (centre pv[0]) or
 // PIECE_TRI.
+// Cross bits of a vertex x: bit p' set when x ~ s[p] (p != i, p' = p minus one if p > i),
+// by binary search in the shorter neighbour list.
+template <int L>
+__device__ __forceinline__ uint32_t cross_bits(const ExtArgs &A, const int32_t (&S)[L], const int2 (&SR)[L], int i,
+                                               int32_t x) {
+    uint32_t c = 0;
+    if constexpr (L >= 2) {
+        const int32_t bx = __ldg(A.g.row_ptr + x), ex = __ldg(A.g.row_ptr + x + 1);
+#pragma unroll
+        for (int p = 0; p < L; ++p) {
+            if (p == i) continue;
+            const int pp = p < i ? p : p - 1;
+            if (adj_rows(A.g.col, SR[p].x, SR[p].y, S[p], bx, ex, x)) c |= 1u << pp;
+        }
+    }
+    return c;
+}
+
+// Join s (vertices S, pattern pid, key position i) with one piece.  Piece vertices pv[0..2]
+// are in the piece's own order, pl their labels; shape is PIECE_WEDGE (centre pv[0]) or
+// PIECE_TRI.  The piece's two non-key vertices are va and vb; their cross bits ca / cb are
+// already known when have_a / have_b is set.
 template <int L, int PASS>
 __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                            const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int shape,
                                            const int32_t (&pv)[3], const int (&pl)[3], Tally &tl,
-                                           CountCache *cc, DomCache &dc) {
+                                           CountCache *cc, DomCache &dc, int32_t va, uint32_t ca, bool have_a,
+                                           uint32_t cb, bool have_b) {
     constexpr int K = L + 2;
     const uint32_t pidx = piece_index(shape, pl[0], pl[1], pl[2]);
     if (A.piece_freq && !__ldg(A.piece_freq + pidx)) return;
@@ -258,15 +284,14 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
     // cross adjacency between s \ {v} and {x0, x1}
     uint32_t avail = 0;
     if constexpr (L >= 2) {
-        const int32_t b0 = __ldg(A.g.row_ptr + x0), e0 = __ldg(A.g.row_ptr + x0 + 1);
-        const int32_t b1 = __ldg(A.g.row_ptr + x1), e1 = __ldg(A.g.row_ptr + x1 + 1);
+        const bool x0a = x0 == va;
+        const uint32_t c0 = x0a ? (have_a ? ca : cross_bits<L>(A, S, SR, i, x0))
+                                : (have_b ? cb : cross_bits<L>(A, S, SR, i, x0));
+        const uint32_t c1 = x0a ? (have_b ? cb : cross_bits<L>(A, S, SR, i, x1))
+                                : (have_a ? ca : cross_bits<L>(A, S, SR, i, x1));
 #pragma unroll
-        for (int p = 0; p < L; ++p) {
-            if (p == i) continue;
-            const int pp = p < i ? p : p - 1;
-            if (adj_rows(A.g.col, SR[p].x, SR[p].y, S[p], b0, e0, x0)) avail |= 1u << (2 * pp);
-            if (adj_rows(A.g.col, SR[p].x, SR[p].y, S[p], b1, e1, x1)) avail |= 1u << (2 * pp + 1);
-        }
+        for (int pp = 0; pp < L - 1; ++pp)
+            avail |= ((c0 >> pp & 1u) << (2 * pp)) | ((c1 >> pp & 1u) << (2 * pp + 1));
     }
     const uint32_t srow_i = (uint32_t)(srows >> (8 * i)) & 0xffu;
 
@@ -320,10 +345,19 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
     }
 }
 
+// Cross bits of neighbour number x of the key vertex from the warp's masks (see extend_kernel).
+template <int L>
+__device__ __forceinline__ uint32_t mask_bits(const uint32_t *mk, int32_t x) {
+    uint32_t c = 0;
+#pragma unroll
+    for (int pp = 0; pp < L - 1; ++pp) c |= ((mk[pp * FSM_MASK_WORDS + (x >> 5)] >> (x & 31)) & 1u) << pp;
+    return c;
+}
+
 template <int L, int PASS>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                          const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
-                                         CountCache *cc, DomCache &dc) {
+                                         CountCache *cc, DomCache &dc, const uint32_t *mk) {
     const DevGraph &g = A.g;
     const int32_t v = S[i];
     const int32_t rp = SR[i].x;
@@ -343,11 +377,13 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         if (A.sampled && !keep_triple(A.sample_seed, A.sample_thr, v, a, b)) return;
         const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
         const bool tri = is_adj(g, a, b);
+        const bool hm = mk != nullptr;
+        const uint32_t ca = hm ? mask_bits<L>(mk, x) : 0u, cb = hm ? mask_bits<L>(mk, y) : 0u;
         if (A.mode == 0 || !tri) {
             pv[0] = v; pl[0] = SL[i];
             if (lab_id_less(la, a, lb, b)) { pv[1] = a; pl[1] = la; pv[2] = b; pl[2] = lb; }
             else { pv[1] = b; pl[1] = lb; pv[2] = a; pl[2] = la; }
-            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
+            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc, a, ca, hm, cb, hm);
         }
         if (tri) {
             int32_t t0 = v, t1 = a, t2 = b;
@@ -358,7 +394,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
             pv[0] = t0; pv[1] = t1; pv[2] = t2;
             pl[0] = m0; pl[1] = m1; pl[2] = m2;
-            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_TRI, pv, pl, tl, cc, dc);
+            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_TRI, pv, pl, tl, cc, dc, a, ca, hm, cb, hm);
         }
     } else {
         const int64_t lq2 = lq - nc;
@@ -378,7 +414,9 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         pv[0] = a; pl[0] = la;
         if (lab_id_less(SL[i], v, lb, b)) { pv[1] = v; pl[1] = SL[i]; pv[2] = b; pl[2] = lb; }
         else { pv[1] = b; pl[1] = lb; pv[2] = v; pl[2] = SL[i]; }
-        join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc);
+        const bool hm = mk != nullptr;
+        join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc, a,
+                            hm ? mask_bits<L>(mk, lo) : 0u, hm, 0u, false);
     }
 }
 
@@ -388,6 +426,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
     const int64_t nunits = A.ne * L;
     Tally tl{0ull, 0ull};
     DomCache dc{nullptr, 0u};
+    __shared__ uint32_t mask_s[8 * (L > 1 ? L - 1 : 1) * FSM_MASK_WORDS];   // per warp, see below
     extern __shared__ unsigned long long dyn_smem[];   // CountCache in PASS_COUNT launches
     CountCache *cc = PASS == PASS_COUNT ? reinterpret_cast<CountCache *>(dyn_smem) : nullptr;
     if (PASS == PASS_COUNT) {
@@ -426,6 +465,40 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
         }
         ulo = __shfl_sync(0xffffffffu, ulo, 0);
         uhi = __shfl_sync(0xffffffffu, uhi, 0);
+        // A chunk inside one unit (hub keys: most of the work) first records, for every
+        // neighbour of the key vertex v, its adjacency to each other vertex of s as bit masks in
+        // shared memory: the cross tests of centre pieces and of the first vertex of end pieces
+        // then read a bit instead of searching a neighbour list.
+        const uint32_t *mk = nullptr;
+        if constexpr (L >= 2) {
+            if (ulo == uhi) {
+                const int64_t e = A.e0 + ulo / L;
+                const int iu = (int)(ulo % L);
+                const int32_t v = __ldg(A.fv + (int64_t)iu * A.fN + e);
+                const int32_t rb = __ldg(A.g.row_ptr + v), dv = __ldg(A.g.row_ptr + v + 1) - rb;
+                if (dv <= FSM_MASK_WORDS * 32) {
+                    uint32_t *wm = mask_s + (threadIdx.x >> 5) * ((L - 1) * FSM_MASK_WORDS);
+#pragma unroll
+                    for (int p = 0; p < L; ++p) {
+                        if (p == iu) continue;
+                        const int pp = p < iu ? p : p - 1;
+                        const int32_t sp = __ldg(A.fv + (int64_t)p * A.fN + e);
+                        const int32_t sb = __ldg(A.g.row_ptr + sp), se = __ldg(A.g.row_ptr + sp + 1);
+                        for (int32_t base = 0; base < dv; base += 32) {
+                            bool bit = false;
+                            if (base + lane < dv) {
+                                const int32_t x = __ldg(A.g.col + rb + base + lane);
+                                bit = adj_rows(A.g.col, sb, se, sp, __ldg(A.g.row_ptr + x), __ldg(A.g.row_ptr + x + 1), x);
+                            }
+                            const uint32_t word = __ballot_sync(0xffffffffu, bit);
+                            if (lane == 0) wm[pp * FSM_MASK_WORDS + (base >> 5)] = word;
+                        }
+                    }
+                    __syncwarp();
+                    mk = wm;
+                }
+            }
+        }
         int64_t cur = -1, ub = 0;
         int32_t S[L];
         int SL[L];
@@ -449,7 +522,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
                 ub = __ldg(A.unit_base + u);
             }
-            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc);
+            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk);
         }
     }
     if (PASS == PASS_COUNT) {

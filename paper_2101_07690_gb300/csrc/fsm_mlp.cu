@@ -201,6 +201,19 @@ uint64_t host_mix(uint64_t &state) {
     return z ^ (z >> 31);
 }
 
+// the kernels' shared memory exceeds the 48 KB default: opt in once per process and device
+bool mlp_smem_ready() {
+    static int done[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (done[dev]) return true;
+    const int bytes = (int)sizeof(Smem);
+    if (cudaFuncSetAttribute(infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+    if (cudaFuncSetAttribute(grad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return false;
+    done[dev] = 1;
+    return true;
+}
+
 int mlp_fail(int code, const std::string &m) {
     fsm::set_last_error_message(m);
     return code;
@@ -229,6 +242,7 @@ extern "C" {
 int fsm_mlp_create(uint64_t seed, fsm_mlp **out) {
     if (!out) return mlp_fail(FSM_EINVAL, "out is NULL");
     *out = nullptr;
+    if (!mlp_smem_ready()) return mlp_fail(FSM_ECUDA, "could not enable the network kernels' shared memory");
     fsm_mlp *M = new fsm_mlp();
     if (!mlp_alloc(M)) { fsm_mlp_free(M); return mlp_fail(FSM_ENOMEM, "device allocation for the network failed"); }
     // He-uniform initial weights from a splitmix64 stream, zero biases, identity standardisation
@@ -287,6 +301,7 @@ static int mlp_upload(const float *X, const float *Y, int64_t n, float **dX, flo
 }
 
 int fsm_mlp_gradients(fsm_mlp *M, const float *X, const float *Y, int64_t n, float *grads, float *loss) {
+    if (!mlp_smem_ready()) return mlp_fail(FSM_ECUDA, "could not enable the network kernels' shared memory");
     if (!M || !X || !Y || !grads || n < 1) return mlp_fail(FSM_EINVAL, "NULL argument or n < 1");
     float *dX = nullptr, *dY = nullptr;
     int rc = mlp_upload(X, Y, n, &dX, &dY);
@@ -312,6 +327,7 @@ int fsm_mlp_gradients(fsm_mlp *M, const float *X, const float *Y, int64_t n, flo
 
 int fsm_mlp_train(fsm_mlp *M, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch, float lr,
                   uint64_t seed, float *final_loss) {
+    if (!mlp_smem_ready()) return mlp_fail(FSM_ECUDA, "could not enable the network kernels' shared memory");
     if (!M || !X || !Y || n < 1 || epochs < 1 || batch < 1 || !(lr > 0.f))
         return mlp_fail(FSM_EINVAL, "bad training arguments");
     float *dX = nullptr, *dY = nullptr;
@@ -367,6 +383,7 @@ int fsm_mlp_predict(const fsm_mlp *M, const float *X, int64_t n, float *out) {
 }
 
 int fsm_mlp_predict_device(const fsm_mlp *M, const float *d_X, int64_t n, float *d_out, void *stream) {
+    if (!mlp_smem_ready()) return mlp_fail(FSM_ECUDA, "could not enable the network kernels' shared memory");
     if (!M || !d_X || !d_out || n < 0) return mlp_fail(FSM_EINVAL, "NULL argument");
     if (n == 0) return FSM_OK;
     const int grid = (int)std::min<int64_t>((n + MLP_TILE - 1) / MLP_TILE, 2048);

@@ -150,8 +150,11 @@ def test_errors(fsm):
         G.mine(3, 0)
     assert e.value.code == fsm.FSM_EINVAL
     with pytest.raises(fsm.FsmError) as e:
-        G.mine(3, 1, sample_rate=0.5)
-    assert e.value.code == fsm.FSM_EUNSUPPORTED
+        G.mine(3, 1, sample_rate=0.0)
+    assert e.value.code == fsm.FSM_EINVAL
+    with pytest.raises(fsm.FsmError) as e:
+        G.mine(3, 1, sample_rate=1.5)
+    assert e.value.code == fsm.FSM_EINVAL
     with pytest.raises(fsm.FsmError):
         G.set_option("mode", 2)
     G.close()
