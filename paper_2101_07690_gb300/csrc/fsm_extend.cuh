@@ -145,29 +145,47 @@ struct Tally { unsigned long long tested, accepted; };
 // neighbour-adjacency masks of single-unit chunks: key vertices of degree up to 32 * this
 #define FSM_MASK_WORDS 64
 
-// Per-block aggregation of quick-pattern counts (PASS_COUNT).  Hot keys (the dominant label
-// patterns) would otherwise serialise on one global counter; each block sums them in shared
-// memory and flushes once when the persistent loop ends.
-#define FSM_SMEM_SLOTS 1024
+// Per-warp aggregation of quick-pattern counts (PASS_COUNT).  Within one chunk the same few
+// keys repeat (one unit, one pattern, a few piece labels), so each warp sums them in its own
+// shared-memory table and flushes the table to the global one at the end of the chunk; keys
+// that find no free slot go straight to the global table.  Hot keys (the dominant label
+// patterns) would otherwise serialise on one global counter.
+#define FSM_WARP_SLOTS 128
 #define FSM_SMEM_PROBES 16
 struct CountCache {
-    unsigned long long key[FSM_SMEM_SLOTS];
-    unsigned long long cnt[FSM_SMEM_SLOTS];
+    unsigned long long key[8][FSM_WARP_SLOTS];
+    unsigned long long cnt[8][FSM_WARP_SLOTS];
 };
 
 __device__ __forceinline__ void count_key(const ExtArgs &A, CountCache *cc, uint64_t key, unsigned n) {
-    uint32_t h = (uint32_t)mix64(key) & (FSM_SMEM_SLOTS - 1);
+    const int w = threadIdx.x >> 5;
+    uint32_t h = (uint32_t)mix64(key) & (FSM_WARP_SLOTS - 1);
     for (int probe = 0; probe < FSM_SMEM_PROBES; ++probe) {
-        unsigned long long cur = cc->key[h];
-        if (cur == FSM_EMPTY_KEY) cur = atomicCAS(cc->key + h, FSM_EMPTY_KEY, key);
+        unsigned long long cur = cc->key[w][h];
+        if (cur == FSM_EMPTY_KEY) cur = atomicCAS(&cc->key[w][h], FSM_EMPTY_KEY, key);
         if (cur == FSM_EMPTY_KEY || cur == key) {
-            atomicAdd(cc->cnt + h, (unsigned long long)n);
+            atomicAdd(&cc->cnt[w][h], (unsigned long long)n);
             return;
         }
-        h = (h + 1) & (FSM_SMEM_SLOTS - 1);
+        h = (h + 1) & (FSM_WARP_SLOTS - 1);
     }
     int64_t slot = qp_insert(A.qp, key, A.err);
     if (slot >= 0) atomicAdd(A.qp.count + slot, (unsigned long long)n);
+}
+
+// warp-synchronous: every lane of the warp calls it
+__device__ __forceinline__ void flush_warp_counts(const ExtArgs &A, CountCache *cc) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncwarp();
+    for (int x = lane; x < FSM_WARP_SLOTS; x += 32) {
+        const unsigned long long key = cc->key[w][x];
+        if (key == FSM_EMPTY_KEY) continue;
+        int64_t slot = qp_insert(A.qp, key, A.err);
+        if (slot >= 0) atomicAdd(A.qp.count + slot, cc->cnt[w][x]);
+        cc->key[w][x] = FSM_EMPTY_KEY;
+        cc->cnt[w][x] = 0ull;
+    }
+    __syncwarp();
 }
 
 // One accepted join: act according to PASS.
@@ -430,9 +448,9 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
     extern __shared__ unsigned long long dyn_smem[];   // CountCache in PASS_COUNT launches
     CountCache *cc = PASS == PASS_COUNT ? reinterpret_cast<CountCache *>(dyn_smem) : nullptr;
     if (PASS == PASS_COUNT) {
-        for (int x = threadIdx.x; x < FSM_SMEM_SLOTS; x += blockDim.x) {
-            cc->key[x] = FSM_EMPTY_KEY;
-            cc->cnt[x] = 0ull;
+        for (int x = threadIdx.x; x < 8 * FSM_WARP_SLOTS; x += blockDim.x) {
+            cc->key[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = FSM_EMPTY_KEY;
+            cc->cnt[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = 0ull;
         }
         __syncthreads();
     }
@@ -524,16 +542,9 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
             }
             do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk);
         }
+        if (PASS == PASS_COUNT) flush_warp_counts(A, cc);
     }
-    if (PASS == PASS_COUNT) {
-        __syncthreads();
-        for (int x = threadIdx.x; x < FSM_SMEM_SLOTS; x += blockDim.x) {
-            const unsigned long long key = cc->key[x];
-            if (key == FSM_EMPTY_KEY) continue;
-            int64_t slot = qp_insert(A.qp, key, A.err);
-            if (slot >= 0) atomicAdd(A.qp.count + slot, cc->cnt[x]);
-        }
-    }
+
     // per-warp totals, one atomic per warp
     unsigned long long t0 = tl.tested, t1 = tl.accepted;
 #pragma unroll

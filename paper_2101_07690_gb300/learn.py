@@ -56,3 +56,71 @@ def compare(exact: dict, got: dict) -> dict:
     err = [abs(got[q] - exact[q]) / exact[q] for q in tp]
     return {"precision": prec, "recall": rec, "median_rel_err": float(np.median(err)) if err else 0.0,
             "exact_patterns": len(exact), "returned": len(got)}
+
+
+def study(workload: str, k: int, t: int, p: float, train_scale: float, train_seeds, cap, test_scale: float = 1.0,
+          test_cap=None, delta: float = 0.5, epochs: int = 200, seed: int = 1) -> dict:
+    """Train on scaled copies of a workload, then mine the test graph exactly, with the plain
+    sampled estimator and with the learned decision plus exact recount; report time and
+    accuracy of each against the exact result."""
+    import time
+
+    import graphgen as gg
+
+    test = gg.workload(workload, scale=test_scale, cap=test_cap)
+    Xs, ys = [], []
+    for s in train_seeds:
+        g = gg.workload(workload, scale=train_scale, cap=cap, seed=s)
+        # the same threshold relative to the graph size (the paper's thresholds are fractions of n)
+        X, y, _ = training_pairs(g, k, max(1, int(round(t * g.n / test.n))), p, seed=seed)
+        Xs.append(X)
+        ys.append(y)
+    X, y = np.concatenate(Xs), np.concatenate(ys)
+    m = fit(X, y, epochs=epochs, seed=seed)
+    try:
+        g = test
+        G = fsm.Graph.from_graphgen(g)
+        G.set_option("launch", 1)
+        out = {"train_pairs": int(len(y)), "test_n": g.n, "test_m": g.m, "k": k, "t": t, "p": p}
+        t0 = time.perf_counter()
+        exact = frequent_set(G.mine(k, t), k)
+        out["exact_s"] = time.perf_counter() - t0
+        G.set_option("seed", seed)
+        t0 = time.perf_counter()
+        plain = frequent_set(G.mine(k, t, sample_rate=p), k)
+        out["plain_s"] = time.perf_counter() - t0
+        G.set_option("model", m)
+        G.set_option("delta_milli", int(delta * 1000))
+        t0 = time.perf_counter()
+        r = G.mine(k, t, sample_rate=p, stats=True)
+        out["learned_s"] = time.perf_counter() - t0
+        learned = frequent_set(r, k)
+        out["recounted"] = int(r["stats"]["recount_patterns"])
+        out["exactly_counted"] = int(r["exact"].sum())
+        G.close()
+        out["plain"] = compare(exact, plain)
+        out["learned"] = compare(exact, learned)
+        return out
+    finally:
+        fsm.fsm_mlp_free(m)
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="learned sampled mining study")
+    ap.add_argument("--workload", default="cl100k")
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--t", type=int, default=1000)
+    ap.add_argument("--p", type=float, default=0.05)
+    ap.add_argument("--train-scale", type=float, default=0.05)
+    ap.add_argument("--train-seeds", default="10-29")
+    ap.add_argument("--cap", type=float, default=60)
+    ap.add_argument("--test-cap", type=float, default=300)
+    ap.add_argument("--delta", type=float, default=0.5)
+    ap.add_argument("--epochs", type=int, default=200)
+    a = ap.parse_args()
+    lo, hi = (int(x) for x in a.train_seeds.split("-"))
+    print(json.dumps(study(a.workload, a.k, a.t, a.p, a.train_scale, range(lo, hi + 1), a.cap,
+                           test_cap=a.test_cap, delta=a.delta, epochs=a.epochs)))
