@@ -104,11 +104,14 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value);
  *   1 <= k <= 8, min_support >= 1, sample_rate in (0, 1]; 1.0 means exact mining.
  * Exact mining (sample_rate = 1) returns exact MNI supports and embedding counts.
  * Sampled mining (sample_rate = p < 1, k >= 3; Section 5's subgraph sampling, here at a rate
- * instead of a per-key quota): every level but the last is mined exactly; the last level joins
- * only the pieces {x < y < z} kept by the counter-based rule of option "seed" and rate p
- * (splitmix64 of the seed and the three ids below floor(p * 2^64)).  Each candidate pattern's
+ * instead of a per-key quota): every level but the last is mined exactly; in the last level a
+ * directed edge x -> y is kept iff splitmix64(splitmix64(splitmix64(seed) ^ x) ^ y) <
+ * floor(sqrt(p) * 2^64) (seed from option "seed"), and only pieces made of kept edges seen
+ * from the joining vertex v are enumerated: {v; a, b} with v -> a and v -> b kept, v - a - b
+ * with v -> a and a -> b kept, about p of all pieces.  Each candidate pattern's
  * support is then decided by the model (option "model"): predictions above t * e^delta are
- * kept with the predicted support, predictions within the band are recounted exactly by an
+ * kept with the predicted support (clamped between the sampled support, a lower bound, and the
+ * smallest label class of the pattern, an upper bound), predictions within the band are recounted exactly by an
  * exact last level restricted to the parts those patterns can be dissected into, the rest are
  * dropped.  Without a model the estimate (smallest sampled orbit popcount) / p decides.
  * fsm_result_exact tells which supports were counted exactly.

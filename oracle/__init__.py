@@ -38,7 +38,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -90,9 +90,10 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
     ``roots=(b, e)`` restricts the enumeration to connected sets whose smallest vertex id is
     in [b, e); ``max_embeddings > 0`` stops after that many embeddings (roots taken in
     ascending order).  Both give a bounded sample of the work, whose supports are those of the
-    sample.  ``sample=(p, seed)`` adds the statistics of sampled mining at rate p: an embedding
-    is kept when the 3-vertex part of its smallest-vertex-first dissection passes the
-    splitmix64 rule; ``ssupport`` and ``scount`` are the MNI support and embedding count over
+    sample.  ``sample=(p, seed)`` adds the statistics of sampled mining at rate p: directed
+    edges are kept by a splitmix64 rule at rate sqrt(p), and an embedding is kept when the
+    3-vertex part of its smallest-vertex-first dissection is made of kept edges as seen from
+    the join vertex; ``ssupport`` and ``scount`` are the MNI support and embedding count over
     kept embeddings.
     Returns a dict of numpy arrays: labels (P, k) int32, adj (P,) uint64, support (P,) int64,
     count (P,) int64 (number of embeddings of each pattern)."""

@@ -36,6 +36,7 @@
  * Results are memoised per raw (label tuple, adjacency) key so the k! scan runs once per
  * distinct raw key.  Image sets are growable open-addressing hash sets of vertex ids.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -305,7 +306,7 @@ static int conn_mask(int k, const uint32_t *adjrow, uint32_t m) {
     return seen == m;
 }
 
-static uint32_t dissect_three(int k, const uint32_t *adjrow) {
+static uint32_t dissect_three_join(int k, const uint32_t *adjrow, int *join) {
     uint32_t all = (1u << k) - 1u;
     for (int start = 0; start < k; start++) {
         uint32_t vis = 1u << start;
@@ -318,7 +319,7 @@ static uint32_t dissect_three(int k, const uint32_t *adjrow) {
         }
         if (!vis) continue;
         for (int v = 0; v < k; v++)
-            if (((vis >> v) & 1u) && conn_mask(k, adjrow, (all & ~vis) | (1u << v))) return vis;
+            if (((vis >> v) & 1u) && conn_mask(k, adjrow, (all & ~vis) | (1u << v))) { *join = v; return vis; }
     }
     /* exhaustive rule: smallest sorted triple (a < b < c), then smallest join */
     for (int a = 0; a < k; a++)
@@ -328,9 +329,15 @@ static uint32_t dissect_three(int k, const uint32_t *adjrow) {
                 if (!conn_mask(k, adjrow, l)) continue;
                 int js[3] = {a, b, c};
                 for (int q = 0; q < 3; q++)
-                    if (conn_mask(k, adjrow, (all & ~l) | (1u << js[q]))) return l;
+                    if (conn_mask(k, adjrow, (all & ~l) | (1u << js[q]))) { *join = js[q]; return l; }
             }
+    *join = -1;
     return 0;
+}
+
+static uint32_t dissect_three(int k, const uint32_t *adjrow) {
+    int j;
+    return dissect_three_join(k, adjrow, &j);
 }
 
 /* splitmix64 (Steele, Lea, Flood 2014): add the golden gamma, then mix */
@@ -341,14 +348,27 @@ static uint64_t smix(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-static int kept(const oracle_t *o, const int32_t *u, uint32_t l) {
-    int32_t ids[3]; int c = 0;
-    for (int i = 0; i < o->k; i++) if ((l >> i) & 1u) ids[c++] = u[i];   /* ascending already */
+/* directed edge x -> y kept at rate q: H(H(H(seed) ^ x) ^ y) < floor(q * 2^64) */
+static int edge_kept(const oracle_t *o, int32_t x, int32_t y) {
     uint64_t h = smix(o->seed);
-    h = smix(h ^ (uint64_t)(uint32_t)ids[0]);
-    h = smix(h ^ (uint64_t)(uint32_t)ids[1]);
-    h = smix(h ^ (uint64_t)(uint32_t)ids[2]);
+    h = smix(h ^ (uint64_t)(uint32_t)x);
+    h = smix(h ^ (uint64_t)(uint32_t)y);
     return h < o->thr;
+}
+
+/* The 3-vertex part l of the embedding's dissection, seen from its join vertex j: if j is
+ * adjacent (in the embedding) to both other vertices x, y of l, the part is kept iff j -> x and
+ * j -> y are kept edges; otherwise j is the end of a wedge with centre c and other end z, and
+ * the part is kept iff j -> c and c -> z are kept. */
+static int kept(const oracle_t *o, const int32_t *u, const uint32_t *adjrow) {
+    int j;
+    uint32_t l = dissect_three_join(o->k, adjrow, &j);
+    int other[2], c = 0;
+    for (int i = 0; i < o->k; i++) if (((l >> i) & 1u) && i != j) other[c++] = i;
+    int ax = (adjrow[j] >> other[0]) & 1u, ay = (adjrow[j] >> other[1]) & 1u;
+    if (ax && ay) return edge_kept(o, u[j], u[other[0]]) && edge_kept(o, u[j], u[other[1]]);
+    int cen = ax ? other[0] : other[1], end = ax ? other[1] : other[0];
+    return edge_kept(o, u[j], u[cen]) && edge_kept(o, u[cen], u[end]);
 }
 
 static void record(oracle_t *o, const int32_t *u, const int32_t *lab, const uint32_t *adjrow) {
@@ -360,7 +380,7 @@ static void record(oracle_t *o, const int32_t *u, const int32_t *lab, const uint
     const uint8_t *perm = o->pool + m->perm_off;
     for (int32_t q = 0; q < m->nopt; q++, perm += o->k)
         for (int c = 0; c < o->k; c++) vset_insert(&p->dom[c], u[perm[c]]);
-    if (o->sampled && o->k >= 3 && kept(o, u, dissect_three(o->k, adjrow))) {
+    if (o->sampled && o->k >= 3 && kept(o, u, adjrow)) {
         p->scount++;
         perm = o->pool + m->perm_off;
         for (int32_t q = 0; q < m->nopt; q++, perm += o->k)
@@ -466,10 +486,11 @@ oracle_result_t *oracle_mine(int32_t n, const int32_t *row_ptr, const int32_t *c
 
 /*
  * oracle_mine_sampled: oracle_mine, plus (sampled != 0, k >= 3) the sampled statistics of
- * sampled mining at rate p: an embedding is kept iff the 3-vertex part of its smallest-vertex-
- * first dissection {a < b < c} gives splitmix64(splitmix64(splitmix64(splitmix64(seed) ^ a)
- * ^ b) ^ c) < floor(p * 2^64); per pattern, ssupport = min over positions of the number of
- * images over kept embeddings (every optimal permutation) and scount = kept embeddings.
+ * sampled mining at rate p: directed edges x -> y are kept when splitmix64(splitmix64(
+ * splitmix64(seed) ^ x) ^ y) < floor(sqrt(p) * 2^64), and an embedding is kept when the
+ * 3-vertex part of its smallest-vertex-first dissection is kept as seen from the join vertex
+ * (see kept()); per pattern, ssupport = min over positions of the number of images over kept
+ * embeddings (every optimal permutation) and scount = kept embeddings.
  */
 oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const int32_t *col,
                                      const int32_t *labels, int32_t k, int32_t mode, int64_t t,
@@ -482,7 +503,7 @@ oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const in
     o.budget = max_embeddings;
     o.sampled = sampled;
     o.seed = seed;
-    o.thr = sampled ? (uint64_t)(p * 18446744073709551616.0) : 0;
+    o.thr = sampled ? (uint64_t)(sqrt(p) * 18446744073709551616.0) : 0;
     o.cx.k = k;
     gen_perms(&o.cx);
     if (root_begin < 0) root_begin = 0;

@@ -141,6 +141,10 @@ struct fsm_graph {
         g.rank = rank;
         g.piece_cnt = piece_cnt;
         g.end_off = end_off;
+        g.prow = row_ptr;
+        g.pcol = col;
+        g.pend = end_off;
+        g.ppc = piece_cnt;
         return g;
     }
 };
@@ -173,7 +177,7 @@ struct RunStats {
     int64_t tested = 0, accepted = 0, qps = 0, patterns = 0, live = 0, frontier_max = 0, levels = 0,
             final_accepted = 0, launches = 0;
     // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
-    int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0;
+    int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0, sampled_edges = 0;
     double pass_ns[FSM_MAXL + 1][3] = {};
     int64_t pass_launches[FSM_MAXL + 1][3] = {}, pass_bytes[FSM_MAXL + 1][3] = {};
 };
@@ -257,7 +261,7 @@ struct Miner {
             rs.pass_launches[L][pass] += 1;
         };
         auto bytes = [&](const Range &r) {
-            if (prof) ck(launch_unit_bytes(G->row_ptr, G->piece_cnt, in.fv, in.N, r.e0, r.ne, L,
+            if (prof) ck(launch_unit_bytes(A.g.prow, A.g.ppc, in.fv, in.N, r.e0, r.ne, L,
                                            prof_bytes + L * 3 + pass, st), "unit bytes");
         };
         auto new_ev = [&]() {
@@ -272,7 +276,7 @@ struct Miner {
             cudaGraphExec_t exec = nullptr;
             ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
+                ck(launch_unit_counts(A.g.ppc, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
                 ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
                 bytes(r);
                 ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
@@ -293,7 +297,7 @@ struct Miner {
             ck(cudaGraphDestroy(graph), "graph destroy");
         } else {
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
+                ck(launch_unit_counts(A.g.ppc, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
                 ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
                 const int64_t total = d2h(base + r.ne * L, st);
                 if (total == 0) continue;
@@ -358,7 +362,7 @@ struct Miner {
         int64_t *base = mem.get<int64_t>(nu + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(nu) + 16);
         unsigned long long *ctr = mem.get<unsigned long long>(1);
-        ck(launch_unit_counts(G->piece_cnt, in.fv, in.N, 0, ne, L, cnt, st), "unit counts");
+        ck(launch_unit_counts(A.g.ppc, in.fv, in.N, 0, ne, L, cnt, st), "unit counts");
         ck(launch_scan_i64(cnt, base, nu, tmp, st), "unit scan");
         const int64_t total = d2h(base + nu, st);
         const int grid = grid_for(L, PASS_DOMAIN);
@@ -415,8 +419,26 @@ struct Miner {
         A.piece_sel = piece_sel;
         A.err = G->err;
         A.sampled = sampled ? 1 : 0;
-        A.sample_seed = G->seed;
-        A.sample_thr = sampled ? (uint64_t)(p * 18446744073709551616.0) : 0;
+        if (sampled) {
+            // pieces come from the kept directed edges only (rate sqrt(p) each)
+            const uint64_t thr = (uint64_t)(std::sqrt(p) * 18446744073709551616.0);
+            int64_t *cnt = mem.get<int64_t>(G->n);
+            int64_t *prow64 = mem.get<int64_t>(G->n + 1);
+            void *tmp = mem.get<char>((int64_t)scan_temp_bytes(G->n) + 16);
+            ck(launch_sample_count(A.g, G->seed, thr, cnt, st), "sample count");
+            ck(launch_scan_i64(cnt, prow64, G->n, tmp, st), "sample scan");
+            const int64_t kept = d2h(prow64 + G->n, st);
+            int32_t *prow = mem.get<int32_t>(G->n + 1);
+            int32_t *pcol = mem.get<int32_t>(std::max<int64_t>(kept, 1));
+            int32_t *pend = mem.get<int32_t>(std::max<int64_t>(kept, 1));
+            int64_t *ppc = mem.get<int64_t>(G->n);
+            ck(launch_sample_lists(A.g, G->seed, thr, prow64, prow, pcol, pend, ppc, st), "sample lists");
+            A.g.prow = prow;
+            A.g.pcol = pcol;
+            A.g.pend = pend;
+            A.g.ppc = ppc;
+            rs.sampled_edges = kept;
+        }
         const int64_t t_live = sampled ? 1 : t;   // sampled counts say nothing about reaching t
         // ---- pass 1: quick patterns and their embedding counts
         int64_t cap = (int64_t)1 << 20;
@@ -723,6 +745,8 @@ void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSe
     std::vector<uint32_t> adj((size_t)P);
     std::vector<float> pred((size_t)P, 0.f), feat;
     std::vector<uint8_t> keep((size_t)P, 0), unc((size_t)P, 0);
+    std::vector<int32_t> cls(64, 0);
+    ck(cudaMemcpyAsync(cls.data(), G->cls_size, sizeof(int32_t) * 64, cudaMemcpyDeviceToHost, st), "copy");
     if (P) {
         ck(cudaMemcpyAsync(lab.data(), cand.clab, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaMemcpyAsync(adj.data(), cand.cadj, 4 * P, cudaMemcpyDeviceToHost, st), "copy");
@@ -803,7 +827,14 @@ void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSe
             c = (int64_t)std::llround((double)cnt[q] / p);
         } else if (use_model) {
             if (keep[q]) {
-                sup = (int64_t)std::llround(std::exp((double)pred[q]));
+                // predicted support, clamped to what is certain: the sampled domains are subsets
+                // of the true ones (lower bound) and no orbit outgrows its label class (upper)
+                double hi = 1e300;
+                for (int cc = 0; cc < k; ++cc)
+                    hi = std::min(hi, (double)cls[(lab[q] >> (8 * (7 - cc))) & 0xff]);
+                const double lo = (double)sig[q];
+                const double pr = std::exp(std::min((double)pred[q], 60.0));
+                sup = (int64_t)std::llround(std::max(lo, std::min(hi, pr)));
                 c = (int64_t)std::llround((double)cnt[q] / p);
             } else if (unc[q]) {
                 auto it = exact.find({lab[q], adj[q]});
@@ -1050,6 +1081,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["sampled_candidates"] = rs.candidates_sampled;
         r->stats["recount_patterns"] = rs.recount_patterns;
         r->stats["recount_frontier"] = rs.recount_frontier;
+        r->stats["sampled_edges"] = rs.sampled_edges;
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["chunk_l" + std::to_string(L)] = g->tuned_chunk[L];
         const char *pn[3] = {"count", "domain", "emit"};
         for (int p = 0; p < 3; ++p) {

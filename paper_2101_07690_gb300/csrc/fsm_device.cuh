@@ -39,6 +39,11 @@ struct DevGraph {
     const int32_t *rank;      // [n] index of v within its label class
     const int64_t *piece_cnt; // [n] piece slots keyed at v: C(d,2) + sum_{a in N(v)} d(a)
     const int32_t *end_off;   // [nnz] exclusive prefix of d(a) over N(v), per row
+    // Lists the pieces are drawn from.  Exact mining: the graph itself (prow = row_ptr, ...).
+    // Sampled last level: the kept directed edges only (piece_cnt / end_off computed on them);
+    // adjacency tests always use row_ptr / col.
+    const int32_t *prow, *pcol, *pend;
+    const int64_t *ppc;
 };
 
 // Is w a neighbour of u?  Binary search in the shorter of the two sorted lists.
@@ -113,11 +118,12 @@ FSM_HD uint64_t mix64(uint64_t x) {
 
 // ---------------------------------------------------------------------------- sampling
 //
-// Piece sampling for the sampled final level: a piece {x < y < z} is kept iff
-// h = H(H(H(seed) ^ x) ^ y) ^ z) < thr, thr = floor(p * 2^64), where H is one step of
-// splitmix64 (Steele, Lea, Flood, "Fast splittable pseudorandom number generators", 2014):
-// add the golden gamma 0x9e3779b97f4a7c15, then the variant-13 mix.  All pieces on one vertex
-// triple share the decision.
+// Sampled last level: the directed edge (x -> y) is kept iff H(H(H(seed) ^ x) ^ y) < thr,
+// thr = floor(q * 2^64) with q = sqrt(p), where H is one step of splitmix64 (Steele, Lea,
+// Flood, "Fast splittable pseudorandom number generators", 2014): add the golden gamma
+// 0x9e3779b97f4a7c15, then the variant-13 mix.  A centre piece {v; a, b} is joined iff both
+// v -> a and v -> b are kept, an end piece v - a - b iff v -> a and a -> b are kept, so about
+// p of the pieces survive and only those are enumerated.
 
 FSM_HD uint64_t splitmix_step(uint64_t x) {
     uint64_t z = x + 0x9e3779b97f4a7c15ull;
@@ -126,15 +132,10 @@ FSM_HD uint64_t splitmix_step(uint64_t x) {
     return z ^ (z >> 31);
 }
 
-FSM_HD bool keep_triple(uint64_t seed, uint64_t thr, int32_t a, int32_t b, int32_t c) {
-    int32_t t;
-    if (a > b) { t = a; a = b; b = t; }
-    if (b > c) { t = b; b = c; c = t; }
-    if (a > b) { t = a; a = b; b = t; }
+FSM_HD bool keep_edge(uint64_t seed, uint64_t thr, int32_t x, int32_t y) {
     uint64_t h = splitmix_step(seed);
-    h = splitmix_step(h ^ (uint64_t)(uint32_t)a);
-    h = splitmix_step(h ^ (uint64_t)(uint32_t)b);
-    h = splitmix_step(h ^ (uint64_t)(uint32_t)c);
+    h = splitmix_step(h ^ (uint64_t)(uint32_t)x);
+    h = splitmix_step(h ^ (uint64_t)(uint32_t)y);
     return h < thr;
 }
 

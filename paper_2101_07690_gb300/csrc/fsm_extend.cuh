@@ -69,9 +69,8 @@ struct ExtArgs {
     int64_t out_N;
     unsigned long long *out_cursor;
     unsigned long long *stats;     // [0] joins tested, [1] joins accepted
-    // sampled final level: keep a piece iff keep_triple(seed, thr, piece vertices)
+    // sampled last level (pieces come from the kept edges in g.prow / g.pcol)
     int sampled;
-    uint64_t sample_seed, sample_thr;
     int *err;
 };
 
@@ -378,8 +377,8 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
                                          CountCache *cc, DomCache &dc, const uint32_t *mk) {
     const DevGraph &g = A.g;
     const int32_t v = S[i];
-    const int32_t rp = SR[i].x;
-    const int32_t d = SR[i].y - rp;
+    const int32_t rp = __ldg(g.prow + v);               // the lists pieces are drawn from
+    const int32_t d = __ldg(g.prow + v + 1) - rp;
     const int64_t nc = (int64_t)d * (d - 1) / 2;
     int32_t pv[3];
     int pl[3];
@@ -389,10 +388,9 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         while ((int64_t)y * (y - 1) / 2 > lq) --y;
         while ((int64_t)(y + 1) * y / 2 <= lq) ++y;
         const int32_t x = (int32_t)(lq - (int64_t)y * (y - 1) / 2);
-        const int32_t a = __ldg(g.col + rp + x), b = __ldg(g.col + rp + y);
+        const int32_t a = __ldg(g.pcol + rp + x), b = __ldg(g.pcol + rp + y);
         if (L == 1 && a < v) return;                 // size-3 subgraphs keyed at their smallest vertex
         if (in_s<L>(S, a) || in_s<L>(S, b)) return;
-        if (A.sampled && !keep_triple(A.sample_seed, A.sample_thr, v, a, b)) return;
         const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
         const bool tri = is_adj(g, a, b);
         const bool hm = mk != nullptr;
@@ -419,14 +417,13 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         int32_t lo = 0, hi = d - 1;
         while (lo < hi) {
             const int32_t mid = (lo + hi + 1) >> 1;
-            if ((int64_t)__ldg(g.end_off + rp + mid) <= lq2) lo = mid; else hi = mid - 1;
+            if ((int64_t)__ldg(g.pend + rp + mid) <= lq2) lo = mid; else hi = mid - 1;
         }
-        const int32_t a = __ldg(g.col + rp + lo);
-        const int32_t b = __ldg(g.col + __ldg(g.row_ptr + a) + (int32_t)(lq2 - __ldg(g.end_off + rp + lo)));
+        const int32_t a = __ldg(g.pcol + rp + lo);
+        const int32_t b = __ldg(g.pcol + __ldg(g.prow + a) + (int32_t)(lq2 - __ldg(g.pend + rp + lo)));
         if (b == v) return;
         if (L == 1 && (a < v || b < v)) return;
         if (in_s<L>(S, a) || in_s<L>(S, b)) return;
-        if (A.sampled && !keep_triple(A.sample_seed, A.sample_thr, v, a, b)) return;
         if (A.mode == 1 && is_adj(g, v, b)) return;  // the induced triple is the triangle (centre branch)
         const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
         pv[0] = a; pl[0] = la;
@@ -493,7 +490,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
                 const int64_t e = A.e0 + ulo / L;
                 const int iu = (int)(ulo % L);
                 const int32_t v = __ldg(A.fv + (int64_t)iu * A.fN + e);
-                const int32_t rb = __ldg(A.g.row_ptr + v), dv = __ldg(A.g.row_ptr + v + 1) - rb;
+                const int32_t rb = __ldg(A.g.prow + v), dv = __ldg(A.g.prow + v + 1) - rb;
                 if (dv <= FSM_MASK_WORDS * 32) {
                     uint32_t *wm = mask_s + (threadIdx.x >> 5) * ((L - 1) * FSM_MASK_WORDS);
 #pragma unroll
@@ -505,7 +502,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
                         for (int32_t base = 0; base < dv; base += 32) {
                             bool bit = false;
                             if (base + lane < dv) {
-                                const int32_t x = __ldg(A.g.col + rb + base + lane);
+                                const int32_t x = __ldg(A.g.pcol + rb + base + lane);
                                 bit = adj_rows(A.g.col, sb, se, sp, __ldg(A.g.row_ptr + x), __ldg(A.g.row_ptr + x + 1), x);
                             }
                             const uint32_t word = __ballot_sync(0xffffffffu, bit);

@@ -1032,6 +1032,52 @@ __global__ void aut_size_kernel(int K, const unsigned long long *pat_lab, const 
 
 } // namespace
 
+namespace {
+__global__ void sample_count_kernel(const DevGraph g, uint64_t seed, uint64_t thr, int64_t *cnt) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) {
+        int64_t c = 0;
+        for (int32_t j = g.row_ptr[v]; j < g.row_ptr[v + 1]; ++j) c += keep_edge(seed, thr, (int32_t)v, g.col[j]);
+        cnt[v] = c;
+    }
+}
+__global__ void sample_fill_kernel(const DevGraph g, uint64_t seed, uint64_t thr, const int64_t *prow64, int32_t *prow,
+                                   int32_t *pcol) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) {
+        int64_t o = prow64[v];
+        prow[v] = (int32_t)o;
+        if (v == g.n - 1) prow[g.n] = (int32_t)prow64[g.n];
+        for (int32_t j = g.row_ptr[v]; j < g.row_ptr[v + 1]; ++j)
+            if (keep_edge(seed, thr, (int32_t)v, g.col[j])) pcol[o++] = g.col[j];
+    }
+}
+__global__ void sample_pieces_kernel(int32_t n, const int32_t *prow, const int32_t *pcol, int32_t *pend, int64_t *ppc) {
+    for (int64_t v = gtid(); v < n; v += gstride()) {
+        const int64_t d = prow[v + 1] - prow[v];
+        int64_t run = 0;
+        for (int32_t j = prow[v]; j < prow[v + 1]; ++j) {
+            pend[j] = (int32_t)run;
+            const int32_t a = pcol[j];
+            run += prow[a + 1] - prow[a];
+        }
+        ppc[v] = d * (d - 1) / 2 + run;
+    }
+}
+} // namespace
+
+cudaError_t launch_sample_count(const DevGraph &g, uint64_t seed, uint64_t thr, int64_t *cnt, cudaStream_t st) {
+    LAUNCHED(1);
+    sample_count_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, seed, thr, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_lists(const DevGraph &g, uint64_t seed, uint64_t thr, const int64_t *prow64, int32_t *prow,
+                                int32_t *pcol, int32_t *pend, int64_t *ppc, cudaStream_t st) {
+    LAUNCHED(2);
+    sample_fill_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, seed, thr, prow64, prow, pcol);
+    sample_pieces_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g.n, prow, pcol, pend, ppc);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_by_rank(const DevGraph &g, int32_t NL, const int32_t *cls_size, int64_t *cls_off,
                            int32_t *by_rank, cudaStream_t st) {
     LAUNCHED(2);

@@ -124,6 +124,11 @@ int64_t launches_so_far();
 void note_launches(int64_t n);
 
 // ---- sampled final level
+// Lists of the kept directed edges (v -> a kept iff keep_edge(seed, thr, v, a)): counts, then
+// (after an exclusive scan into prow64) the lists, the end-piece prefixes and piece counts.
+cudaError_t launch_sample_count(const DevGraph &g, uint64_t seed, uint64_t thr, int64_t *cnt, cudaStream_t st);
+cudaError_t launch_sample_lists(const DevGraph &g, uint64_t seed, uint64_t thr, const int64_t *prow64, int32_t *prow,
+                                int32_t *pcol, int32_t *pend, int64_t *ppc, cudaStream_t st);
 // by_rank[cls_off[l] + rank[v]] = v for every vertex v of label l (cls_off: exclusive prefix of
 // class sizes, computed by the kernel itself)
 cudaError_t launch_by_rank(const DevGraph &g, int32_t NL, const int32_t *cls_size, int64_t *cls_off,

@@ -114,9 +114,9 @@ if __name__ == "__main__":
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--t", type=int, default=1000)
     ap.add_argument("--p", type=float, default=0.05)
-    ap.add_argument("--train-scale", type=float, default=0.05)
-    ap.add_argument("--train-seeds", default="10-29")
-    ap.add_argument("--cap", type=float, default=60)
+    ap.add_argument("--train-scale", type=float, default=1.0)
+    ap.add_argument("--train-seeds", default="10-13")
+    ap.add_argument("--cap", type=float, default=300)
     ap.add_argument("--test-cap", type=float, default=300)
     ap.add_argument("--delta", type=float, default=0.5)
     ap.add_argument("--epochs", type=int, default=200)
