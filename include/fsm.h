@@ -82,6 +82,11 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                passes and calls (reported as stat "chunk_l<l>"); 0 = forget tuned values.
  *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
  *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
+ *   "fused"      1 = the last level counts quick patterns and fills MNI domains in one pass,
+ *                into per-key bitmaps merged per pattern afterwards (default); 0 = a count pass
+ *                then a domain pass.  Both give identical results; a pool shortfall falls back
+ *                to the two passes.
+ *   "fused_pool" size in 32-bit words of the per-key bitmap pool (0 = sized automatically).
  *   "seed"       64-bit seed of the piece sampling of fsm_mine with sample_rate < 1 (default 0).
  *   "candidates" 1 = sampled mining returns every candidate pattern of the sampled level with
  *                its estimated support (smallest orbit popcount / p) and its 32 features

@@ -118,6 +118,9 @@ struct fsm_graph {
     int sms = 0;
     int64_t qp_hint[FSM_MAXL + 1] = {};   // distinct quick patterns seen at each level last time
     int autotune = 0;
+    int fused = 1;
+    unsigned long long pool_hint[FSM_MAXL + 1] = {};   // pool words the fused pass used last time
+    unsigned long long pool_force = 0;                 // option "fused_pool": fixed pool size
     int32_t tuned_chunk[FSM_MAXL + 1] = {};   // chunk size chosen by the autotuner per level
     // sampled mining
     uint64_t seed = 0;
@@ -178,8 +181,8 @@ struct RunStats {
             final_accepted = 0, launches = 0;
     // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
     int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0, sampled_edges = 0;
-    double pass_ns[FSM_MAXL + 1][3] = {};
-    int64_t pass_launches[FSM_MAXL + 1][3] = {}, pass_bytes[FSM_MAXL + 1][3] = {};
+    double pass_ns[FSM_MAXL + 1][4] = {};
+    int64_t pass_launches[FSM_MAXL + 1][4] = {}, pass_bytes[FSM_MAXL + 1][4] = {};
 };
 
 struct Miner {
@@ -193,6 +196,7 @@ struct Miner {
         int bps = 0;
         cudaError_t e = pass == PASS_COUNT ? occupancy_extend_count(L, &bps)
                       : pass == PASS_DOMAIN ? occupancy_extend_domain(L, &bps)
+                      : pass == PASS_FUSED ? occupancy_extend_fused(L, &bps)
                                             : occupancy_extend_emit(L, &bps);
         ck(e, "occupancy query");
         if (bps < 1) bps = 1;
@@ -202,7 +206,7 @@ struct Miner {
     // Profiling records: one event pair per timed region, read after the call's last sync.
     struct ProfEv { cudaEvent_t a, b; int L, pass; };
     std::vector<ProfEv> prof_ev;
-    unsigned long long *prof_bytes = nullptr;   // [(FSM_MAXL + 1) * 3] algorithmic bytes, device
+    unsigned long long *prof_bytes = nullptr;   // [(FSM_MAXL + 1) * 4] algorithmic bytes, device
 
     struct Range { int64_t e0, ne; };
 
@@ -255,6 +259,7 @@ struct Miner {
         auto launch_ext = [&]() {
             cudaError_t e = pass == PASS_COUNT ? launch_extend_count(L, A, grid, st)
                           : pass == PASS_DOMAIN ? launch_extend_domain(L, A, grid, st)
+                          : pass == PASS_FUSED ? launch_extend_fused(L, A, grid, st)
                                                 : launch_extend_emit(L, A, grid, st);
             ck(e, "extension kernel");
             rs.launches += 1;
@@ -262,7 +267,7 @@ struct Miner {
         };
         auto bytes = [&](const Range &r) {
             if (prof) ck(launch_unit_bytes(A.g.prow, A.g.ppc, in.fv, in.N, r.e0, r.ne, L,
-                                           prof_bytes + L * 3 + pass, st), "unit bytes");
+                                           prof_bytes + L * 4 + pass, st), "unit bytes");
         };
         auto new_ev = [&]() {
             ProfEv ev{nullptr, nullptr, L, pass};
@@ -440,10 +445,32 @@ struct Miner {
             rs.sampled_edges = kept;
         }
         const int64_t t_live = sampled ? 1 : t;   // sampled counts say nothing about reaching t
-        // ---- pass 1: quick patterns and their embedding counts
+        // ---- pass 1: quick patterns and their embedding counts (last level: fused with the
+        // domains, into per-key bitmaps from a pool, when the pool can be had)
         int64_t cap = (int64_t)1 << 20;
         while (cap < 4 * G->qp_hint[L] && cap < ((int64_t)1 << 30)) cap <<= 1;
-        unsigned long long *keys = nullptr, *qcount = nullptr, *used = nullptr;
+        unsigned long long *keys = nullptr, *qcount = nullptr, *used = nullptr, *qdom = nullptr, *ptop = nullptr;
+        uint32_t *pool = nullptr;
+        unsigned long long pool_words = 0;
+        bool fused = final && G->fused;
+        if (fused) {
+            size_t fr = 0, tot = 0;
+            ck(cudaMemGetInfo(&fr, &tot), "memory info");
+            // the size the last call needed (twice, for safety), else 40% of the free memory
+            const unsigned long long cap_words = (unsigned long long)std::min<size_t>(fr / 4 * 2 / 5, (size_t)12 << 30);
+            pool_words = G->pool_hint[L] ? std::min(cap_words, 2 * G->pool_hint[L] + (1ull << 22)) : cap_words;
+            pool_words = std::max<unsigned long long>(pool_words, 1ull << 20);
+            if (G->pool_force) pool_words = G->pool_force;
+            void *pp = nullptr;
+            if (cudaMallocAsync(&pp, pool_words * 4, st) != cudaSuccess) {
+                cudaGetLastError();
+                fused = false;   // no room for the pool: separate count and domain passes
+            } else {
+                pool = (uint32_t *)pp;
+                mem.ptrs.push_back(pp);
+                ptop = mem.get<unsigned long long>(1);
+            }
+        }
         for (;;) {
             keys = mem.get<unsigned long long>(cap);
             qcount = mem.get<unsigned long long>(cap);
@@ -453,23 +480,41 @@ struct Miner {
             ck(cudaMemsetAsync(used, 0, sizeof(unsigned long long), st), "memset");
             ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
             ck(cudaMemsetAsync(G->stats, 0, 2 * sizeof(unsigned long long), st), "memset");
-                        A.qp.keys = keys;
+            if (fused) {
+                qdom = mem.get<unsigned long long>(cap * 8);
+                ck(cudaMemsetAsync(qdom, 0, sizeof(unsigned long long) * cap * 8, st), "memset");
+                ck(cudaMemsetAsync(pool, 0, pool_words * 4, st), "memset");
+                ck(cudaMemsetAsync(ptop, 0, sizeof(unsigned long long), st), "memset");
+                A.qp_dom = qdom;
+                A.pool = pool;
+                A.pool_top = ptop;
+                A.pool_words = pool_words;
+                A.cls_size = G->cls_size;
+            }
+            A.qp.keys = keys;
             A.qp.count = qcount;
             A.qp.mask = (uint64_t)cap - 1;
             A.qp.used = used;
             A.qp.max_used = (unsigned long long)(cap / 2);
             A.stats = G->stats;
-            run_pass(PASS_COUNT, in, A, pat_off);
+            run_pass(fused ? PASS_FUSED : PASS_COUNT, in, A, pat_off);
             const int ew = err_word();
             if (ew & FSM_ERR_QP_OVERFLOW) {
                 mem.release(keys);
                 mem.release(qcount);
                 mem.release(used);
+                if (qdom) mem.release(qdom);
                 if (cap >= ((int64_t)1 << 31)) fail(FSM_EUNSUPPORTED, "more than 2^30 distinct quick patterns in one level");
                 cap <<= 2;
                 continue;
             }
-            if (ew) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+            if (ew & ~FSM_ERR_POOL) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+            if (ew & FSM_ERR_POOL) {
+                fused = false;   // pool too small: the separate domain pass decides
+                G->pool_hint[L] = 0;
+            } else if (fused) {
+                G->pool_hint[L] = d2h(ptop, st);
+            }
             break;
         }
         unsigned long long st2[2];
@@ -538,8 +583,17 @@ struct Miner {
         A.dom = dom;
         A.stats = nullptr;
         if (rs.live > 0) {
-            tune_chunk(in, A);
-            run_pass(PASS_DOMAIN, in, A, pat_off);
+            if (fused) {
+                ck(launch_merge_domains(K, slots, nq, qpat, qperm, qdom, pool, live, orbit, doff, words, dom, st),
+                   "merge domains");
+            } else {
+                tune_chunk(in, A);
+                run_pass(PASS_DOMAIN, in, A, pat_off);
+            }
+        }
+        if (pool) {
+            mem.release(pool);
+            pool = nullptr;
         }
         unsigned long long *sigma = mem.get<unsigned long long>(np);
         ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
@@ -602,6 +656,7 @@ struct Miner {
         }
         const int ew = err_word();
         if (ew) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+        if (qdom) mem.release(qdom);
         for (void *p : std::initializer_list<void *>{keys, qcount, used, slots, nq_d, qpat, qperm, flag, ids, stmp, plab,
                                                      padj, orbit, minorb, pcount, live, words, woff, doff, stmp2, sigma,
                                                      fflag, fscan, newid})
@@ -937,6 +992,12 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
             g->mode = (int)value;
         } else if (k == "stream") {
             g->stream = value ? (cudaStream_t)(intptr_t)value : g->own_stream;
+        } else if (k == "fused") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "fused must be 0 or 1");
+            g->fused = (int)value;
+        } else if (k == "fused_pool") {
+            if (value < 0) fail(FSM_EINVAL, "fused_pool must be >= 0");
+            g->pool_force = (unsigned long long)value;
         } else if (k == "seed") {
             g->seed = (uint64_t)value;
         } else if (k == "candidates") {
@@ -997,8 +1058,8 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
             Arena mem(st);
             Miner m{g, st, mem, min_support, rs};
             if (g->profile) {
-                m.prof_bytes = mem.get<unsigned long long>((FSM_MAXL + 1) * 3);
-                ck(cudaMemsetAsync(m.prof_bytes, 0, sizeof(unsigned long long) * (FSM_MAXL + 1) * 3, st), "memset");
+                m.prof_bytes = mem.get<unsigned long long>((FSM_MAXL + 1) * 4);
+                ck(cudaMemsetAsync(m.prof_bytes, 0, sizeof(unsigned long long) * (FSM_MAXL + 1) * 4, st), "memset");
             }
             LevelSet res;
             if (k == 1) {
@@ -1043,11 +1104,11 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
                 fill_result(r, res, k, st);
             }
             if (g->profile) {
-                unsigned long long pb[(FSM_MAXL + 1) * 3];
+                unsigned long long pb[(FSM_MAXL + 1) * 4];
                 ck(cudaMemcpyAsync(pb, m.prof_bytes, sizeof(pb), cudaMemcpyDeviceToHost, st), "copy");
                 ck(cudaStreamSynchronize(st), "sync");
                 for (int L = 0; L <= FSM_MAXL; ++L)
-                    for (int p = 0; p < 3; ++p) rs.pass_bytes[L][p] += (int64_t)pb[L * 3 + p];
+                    for (int p = 0; p < 4; ++p) rs.pass_bytes[L][p] += (int64_t)pb[L * 4 + p];
                 for (auto &ev : m.prof_ev) {
                     float ems = 0.f;
                     ck(cudaEventElapsedTime(&ems, ev.a, ev.b), "event time");
@@ -1083,8 +1144,8 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["recount_frontier"] = rs.recount_frontier;
         r->stats["sampled_edges"] = rs.sampled_edges;
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["chunk_l" + std::to_string(L)] = g->tuned_chunk[L];
-        const char *pn[3] = {"count", "domain", "emit"};
-        for (int p = 0; p < 3; ++p) {
+        const char *pn[4] = {"count", "domain", "emit", "fused"};
+        for (int p = 0; p < 4; ++p) {
             double ns = 0;
             int64_t nl = 0, nb = 0;
             for (int L = 1; L <= FSM_MAXL; ++L) {

@@ -25,6 +25,7 @@
 #define FSM_ERR_QP_MISSING   2   // a key seen in a later pass was not in the table
 #define FSM_ERR_BOUNDS       4   // an index check failed
 #define FSM_ERR_CSR          8   // malformed CSR found by validation
+#define FSM_ERR_POOL        16   // the fused pass ran out of per-key bitmap pool: domain pass instead
 
 namespace fsm {
 

@@ -16,7 +16,11 @@
 // (Section 4.4).  The pass template parameter says what an accepted join does:
 //   PASS_COUNT   insert the key into the quick-pattern table and count it;
 //   PASS_DOMAIN  set the MNI domain bits of its pattern's orbits (Definition 2);
-//   PASS_EMIT    write it, permuted into canonical order, to the next frontier.
+//   PASS_EMIT    write it, permuted into canonical order, to the next frontier;
+//   PASS_FUSED   (last level) count it and set the bits of its vertices in bitmaps kept per
+//                (quick-pattern key, local position), allocated on first use from a pool;
+//                after canonicalisation they are merged into the patterns' orbit bitmaps, so
+//                the last level is enumerated once instead of twice.
 //
 // Scheduling: the pieces of a batch of units form one index space [0, total) (exclusive prefix
 // `unit_base`); warps take fixed-size chunks of it from an atomic counter, so hub vertices
@@ -26,7 +30,7 @@
 
 namespace fsm {
 
-enum { PASS_COUNT = 0, PASS_DOMAIN = 1, PASS_EMIT = 2 };
+enum { PASS_COUNT = 0, PASS_DOMAIN = 1, PASS_EMIT = 2, PASS_FUSED = 3 };
 
 struct QPTab {
     unsigned long long *keys;      // [cap], FSM_EMPTY_KEY when free
@@ -69,6 +73,12 @@ struct ExtArgs {
     int64_t out_N;
     unsigned long long *out_cursor;
     unsigned long long *stats;     // [0] joins tested, [1] joins accepted
+    // fused pass: per-key bitmaps (offset + 1 into pool, 0 = none) and their pool
+    unsigned long long *qp_dom;    // [cap * 8]
+    uint32_t *pool;
+    unsigned long long *pool_top;
+    unsigned long long pool_words;
+    const int32_t *cls_size;
     // sampled last level (pieces come from the kept edges in g.prow / g.pcol)
     int sampled;
     int *err;
@@ -154,7 +164,32 @@ struct Tally { unsigned long long tested, accepted; };
 struct CountCache {
     unsigned long long key[8][FSM_WARP_SLOTS];
     unsigned long long cnt[8][FSM_WARP_SLOTS];
+    long long slot[8][FSM_WARP_SLOTS];   // global slot of the key, -1 until resolved
 };
+
+// Count n more joins of key through the warp's table; returns the key's global slot (resolved
+// once per table entry; a race resolves it twice to the same value).
+__device__ __forceinline__ int64_t count_key_slot(const ExtArgs &A, CountCache *cc, uint64_t key, unsigned n) {
+    const int w = threadIdx.x >> 5;
+    uint32_t h = (uint32_t)mix64(key) & (FSM_WARP_SLOTS - 1);
+    for (int probe = 0; probe < FSM_SMEM_PROBES; ++probe) {
+        unsigned long long cur = cc->key[w][h];
+        if (cur == FSM_EMPTY_KEY) cur = atomicCAS(&cc->key[w][h], FSM_EMPTY_KEY, key);
+        if (cur == FSM_EMPTY_KEY || cur == key) {
+            atomicAdd(&cc->cnt[w][h], (unsigned long long)n);
+            long long s = ((volatile long long *)cc->slot[w])[h];
+            if (s < 0) {
+                s = qp_insert(A.qp, key, A.err);
+                ((volatile long long *)cc->slot[w])[h] = s;
+            }
+            return s;
+        }
+        h = (h + 1) & (FSM_WARP_SLOTS - 1);
+    }
+    int64_t slot = qp_insert(A.qp, key, A.err);
+    if (slot >= 0) atomicAdd(A.qp.count + slot, (unsigned long long)n);
+    return slot;
+}
 
 __device__ __forceinline__ void count_key(const ExtArgs &A, CountCache *cc, uint64_t key, unsigned n) {
     const int w = threadIdx.x >> 5;
@@ -179,10 +214,12 @@ __device__ __forceinline__ void flush_warp_counts(const ExtArgs &A, CountCache *
     for (int x = lane; x < FSM_WARP_SLOTS; x += 32) {
         const unsigned long long key = cc->key[w][x];
         if (key == FSM_EMPTY_KEY) continue;
-        int64_t slot = qp_insert(A.qp, key, A.err);
+        int64_t slot = cc->slot[w][x];
+        if (slot < 0) slot = qp_insert(A.qp, key, A.err);
         if (slot >= 0) atomicAdd(A.qp.count + slot, cc->cnt[w][x]);
         cc->key[w][x] = FSM_EMPTY_KEY;
         cc->cnt[w][x] = 0ull;
+        cc->slot[w][x] = -1;
     }
     __syncwarp();
 }
@@ -199,6 +236,37 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
         const unsigned grp = __match_any_sync(act, key);
         const int lane = threadIdx.x & 31;
         if (lane == __ffs(grp) - 1) count_key(A, cc, key, __popc(grp));
+        return;
+    }
+    if (PASS == PASS_FUSED) {
+        const unsigned act = __activemask();
+        const unsigned grp = __match_any_sync(act, key);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(grp) - 1;
+        long long slot = -1;
+        if (lane == leader) slot = count_key_slot(A, cc, key, __popc(grp));
+        slot = __shfl_sync(grp, slot, leader);
+        if (slot < 0) return;   // table overflow: the pass is repeated with a larger table
+#pragma unroll
+        for (int h = 0; h < K; ++h) {
+            unsigned long long *pp = A.qp_dom + slot * 8 + h;
+            unsigned long long off = *(volatile unsigned long long *)pp;
+            if (off == 0ull) {
+                const int lab = __ldg(A.g.labels + gid[h]);
+                const unsigned long long words = ((unsigned long long)__ldg(A.cls_size + lab) + 31ull) / 32ull;
+                const unsigned long long res = atomicAdd(A.pool_top, words);
+                if (res + words > A.pool_words) { atomicOr(A.err, FSM_ERR_POOL); return; }
+                const unsigned long long old = atomicCAS(pp, 0ull, res + 1ull);
+                off = old ? old : res + 1ull;
+            }
+            const int32_t r = __ldg(A.g.rank + gid[h]);
+            uint32_t *w = A.pool + (off - 1ull) + (r >> 5);
+            const uint32_t bit = 1u << (r & 31);
+            if (w == dc.w && (dc.bits & bit)) continue;
+            if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+            if (w != dc.w) { dc.w = w; dc.bits = 0; }
+            dc.bits |= bit;
+        }
         return;
     }
     int64_t slot = qp_find(A.qp, key);
@@ -443,11 +511,13 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
     DomCache dc{nullptr, 0u};
     __shared__ uint32_t mask_s[8 * (L > 1 ? L - 1 : 1) * FSM_MASK_WORDS];   // per warp, see below
     extern __shared__ unsigned long long dyn_smem[];   // CountCache in PASS_COUNT launches
-    CountCache *cc = PASS == PASS_COUNT ? reinterpret_cast<CountCache *>(dyn_smem) : nullptr;
-    if (PASS == PASS_COUNT) {
+    constexpr bool counts = PASS == PASS_COUNT || PASS == PASS_FUSED;
+    CountCache *cc = counts ? reinterpret_cast<CountCache *>(dyn_smem) : nullptr;
+    if (counts) {
         for (int x = threadIdx.x; x < 8 * FSM_WARP_SLOTS; x += blockDim.x) {
             cc->key[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = FSM_EMPTY_KEY;
             cc->cnt[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = 0ull;
+            cc->slot[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = -1;
         }
         __syncthreads();
     }
@@ -466,7 +536,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
         unsigned long long c = 0;
         if (lane == 0) {
             // an overflowing count pass is repeated with a larger table: stop early
-            if (PASS == PASS_COUNT && (*(volatile int *)A.err & FSM_ERR_QP_OVERFLOW)) c = ~0ull;
+            if ((PASS == PASS_COUNT || PASS == PASS_FUSED) && (*(volatile int *)A.err & FSM_ERR_QP_OVERFLOW)) c = ~0ull;
             else c = atomicAdd(A.chunk_ctr, 1ull);
         }
         c = __shfl_sync(0xffffffffu, c, 0);
@@ -539,7 +609,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
             }
             do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk);
         }
-        if (PASS == PASS_COUNT) flush_warp_counts(A, cc);
+        if (counts) flush_warp_counts(A, cc);
     }
 
     // per-warp totals, one atomic per warp
@@ -559,6 +629,8 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
 cudaError_t launch_extend_count(int L, const ExtArgs &A, int grid, cudaStream_t st);
 cudaError_t launch_extend_domain(int L, const ExtArgs &A, int grid, cudaStream_t st);
 cudaError_t launch_extend_emit(int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t launch_extend_fused(int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t occupancy_extend_fused(int L, int *blocks_per_sm);
 cudaError_t occupancy_extend_count(int L, int *blocks_per_sm);
 cudaError_t occupancy_extend_domain(int L, int *blocks_per_sm);
 cudaError_t occupancy_extend_emit(int L, int *blocks_per_sm);

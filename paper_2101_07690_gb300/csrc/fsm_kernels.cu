@@ -1248,6 +1248,44 @@ cudaError_t launch_decide(const float *pred, int64_t np, float logt, float delta
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void merge_domains_kernel(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                                     const uint32_t *qp_perm, const unsigned long long *qp_dom, const uint32_t *pool,
+                                     const uint8_t *live, const uint64_t *orbit, const int64_t *dom_off,
+                                     const int64_t *words, uint32_t *dom) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = nq * K;
+    for (int64_t w = gtid() >> 5; w < nw; w += gstride() >> 5) {
+        const int64_t slot = slots[w / K];
+        const int h = (int)(w % K);
+        const int32_t P = qp_pattern[slot];
+        if (!live[P]) continue;
+        const unsigned long long off = qp_dom[slot * 8 + h];
+        if (off == 0ull) continue;
+        const int c = (int)((qp_perm[slot] >> (3 * h)) & 7u);
+        const int o = (int)((orbit[P] >> (8 * c)) & 0xff);
+        uint32_t *dst = dom + dom_off[(int64_t)P * 8 + o];
+        const uint32_t *src = pool + (off - 1ull);
+        const int64_t n = words[(int64_t)P * 8 + o];
+        for (int64_t x = lane; x < n; x += 32) {
+            const uint32_t v = src[x];
+            if (v) atomicOr(dst + x, v);
+        }
+    }
+}
+} // namespace
+
+cudaError_t launch_merge_domains(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                                 const uint32_t *qp_perm, const unsigned long long *qp_dom, const uint32_t *pool,
+                                 const uint8_t *live, const uint64_t *orbit, const int64_t *dom_off,
+                                 const int64_t *words, uint32_t *dom, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    merge_domains_kernel<<<blocks_for(nq * K * 32), kThreads, 0, st>>>(K, slots, nq, qp_pattern, qp_perm, qp_dom, pool,
+                                                                       live, orbit, dom_off, words, dom);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;

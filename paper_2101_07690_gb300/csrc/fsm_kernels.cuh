@@ -171,6 +171,13 @@ cudaError_t launch_keep_counts(const unsigned long long *count, const uint8_t *k
 cudaError_t launch_decide(const float *pred, int64_t np, float logt, float delta, uint8_t *keep, uint8_t *uncertain,
                           cudaStream_t st);
 
+// Fused last level: OR each live pattern's per-key bitmaps (qp_dom: offset + 1 into pool per
+// (slot, local position)) into the pattern's orbit bitmaps; one warp per (key, position).
+cudaError_t launch_merge_domains(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                                 const uint32_t *qp_perm, const unsigned long long *qp_dom, const uint32_t *pool,
+                                 const uint8_t *live, const uint64_t *orbit, const int64_t *dom_off,
+                                 const int64_t *words, uint32_t *dom, cudaStream_t st);
+
 // ---- pieces: mark the frequent size-3 patterns by piece index
 cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st);

@@ -59,10 +59,11 @@ def compare(exact: dict, got: dict) -> dict:
 
 
 def study(workload: str, k: int, t: int, p: float, train_scale: float, train_seeds, cap, test_scale: float = 1.0,
-          test_cap=None, delta: float = 0.5, epochs: int = 200, seed: int = 1) -> dict:
-    """Train on scaled copies of a workload, then mine the test graph exactly, with the plain
-    sampled estimator and with the learned decision plus exact recount; report time and
-    accuracy of each against the exact result."""
+          test_cap=None, deltas=(0.0, 0.1, 0.25, 0.5), epochs: int = 200, seed: int = 1) -> dict:
+    """Train on copies of a workload (other seeds), then mine the test graph exactly, with the
+    plain sampled estimator, and with the learned decision plus exact recount for each recount
+    band delta; report time and accuracy of each against the exact result, and the network's
+    error on held-out training pairs."""
     import time
 
     import graphgen as gg
@@ -76,12 +77,18 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
         Xs.append(X)
         ys.append(y)
     X, y = np.concatenate(Xs), np.concatenate(ys)
-    m = fit(X, y, epochs=epochs, seed=seed)
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(len(y))
+    nval = len(y) // 10
+    val, tr = perm[:nval], perm[nval:]
+    m = fit(X[tr], y[tr], epochs=epochs, seed=seed)
     try:
-        g = test
-        G = fsm.Graph.from_graphgen(g)
+        err = fsm.fsm_mlp_predict(m, X[val]) - y[val]
+        out = {"train_pairs": int(len(tr)), "val_rmse_log": float(np.sqrt(np.mean(err ** 2))),
+               "val_median_abs_log_err": float(np.median(np.abs(err))),
+               "test_n": test.n, "test_m": test.m, "k": k, "t": t, "p": p}
+        G = fsm.Graph.from_graphgen(test)
         G.set_option("launch", 1)
-        out = {"train_pairs": int(len(y)), "test_n": g.n, "test_m": g.m, "k": k, "t": t, "p": p}
         t0 = time.perf_counter()
         exact = frequent_set(G.mine(k, t), k)
         out["exact_s"] = time.perf_counter() - t0
@@ -89,17 +96,18 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
         t0 = time.perf_counter()
         plain = frequent_set(G.mine(k, t, sample_rate=p), k)
         out["plain_s"] = time.perf_counter() - t0
-        G.set_option("model", m)
-        G.set_option("delta_milli", int(delta * 1000))
-        t0 = time.perf_counter()
-        r = G.mine(k, t, sample_rate=p, stats=True)
-        out["learned_s"] = time.perf_counter() - t0
-        learned = frequent_set(r, k)
-        out["recounted"] = int(r["stats"]["recount_patterns"])
-        out["exactly_counted"] = int(r["exact"].sum())
-        G.close()
         out["plain"] = compare(exact, plain)
-        out["learned"] = compare(exact, learned)
+        G.set_option("model", m)
+        out["learned"] = []
+        for delta in deltas:
+            G.set_option("delta_milli", int(delta * 1000))
+            t0 = time.perf_counter()
+            r = G.mine(k, t, sample_rate=p, stats=True)
+            row = {"delta": delta, "seconds": time.perf_counter() - t0,
+                   "recounted": int(r["stats"]["recount_patterns"]), "exactly_counted": int(r["exact"].sum())}
+            row.update(compare(exact, frequent_set(r, k)))
+            out["learned"].append(row)
+        G.close()
         return out
     finally:
         fsm.fsm_mlp_free(m)
@@ -118,9 +126,9 @@ if __name__ == "__main__":
     ap.add_argument("--train-seeds", default="10-13")
     ap.add_argument("--cap", type=float, default=300)
     ap.add_argument("--test-cap", type=float, default=300)
-    ap.add_argument("--delta", type=float, default=0.5)
+    ap.add_argument("--deltas", default="0,0.05,0.1,0.25,0.5")
     ap.add_argument("--epochs", type=int, default=200)
     a = ap.parse_args()
     lo, hi = (int(x) for x in a.train_seeds.split("-"))
     print(json.dumps(study(a.workload, a.k, a.t, a.p, a.train_scale, range(lo, hi + 1), a.cap,
-                           test_cap=a.test_cap, delta=a.delta, epochs=a.epochs)))
+                           test_cap=a.test_cap, deltas=[float(x) for x in a.deltas.split(",")], epochs=a.epochs)))

@@ -108,7 +108,8 @@ def test_chunking_and_batching_do_not_change_results(fsm):
     g = gg.workload("cl100k", scale=0.005, cap=30)
     ref = check(fsm, g, 4, 6)
     for opts in ({"chunk": 32}, {"chunk": 65536}, {"batch": 1024}, {"batch": 1024, "chunk": 64},
-                 {"autotune": 1}, {"autotune": 1, "launch": 1}):
+                 {"autotune": 1}, {"autotune": 1, "launch": 1}, {"fused": 0}, {"fused": 0, "launch": 2},
+                 {"fused_pool": 64}, {"fused_pool": 4096, "launch": 1}):
         G = fsm.Graph.from_graphgen(g)
         for key, val in opts.items():
             G.set_option(key, val)
@@ -177,6 +178,14 @@ def test_stats(fsm):
     assert s["levels"] == 2 and s["kernel_launches"] > 0 and s["time_ns"] > 0
     # every returned embedding was accepted in the last level
     assert s["final_embeddings"] >= int(r["count"].sum())
+
+
+@pytest.mark.parametrize("fused", [0, 1])
+def test_fused_and_two_pass_last_level(fsm, fused):
+    for g, k, t in [(gg.workload("er1000"), 3, 30), (gg.workload("er1000"), 4, 10),
+                    (gg.erdos_renyi(40, 2.5, seed=7, num_labels=2), 6, 2)]:
+        for mode in ("edge", "vertex"):
+            check(fsm, g, k, t, mode, {"fused": fused})
 
 
 @pytest.mark.parametrize("launch", [0, 1, 2])
