@@ -512,6 +512,7 @@ struct Miner {
             if (ew & FSM_ERR_POOL) {
                 fused = false;   // pool too small: the separate domain pass decides
                 G->pool_hint[L] = 0;
+                ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
             } else if (fused) {
                 G->pool_hint[L] = d2h(ptop, st);
             }
