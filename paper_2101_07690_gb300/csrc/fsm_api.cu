@@ -356,9 +356,10 @@ struct Miner {
         return off;
     }
 
-    // Autotuner: time the domain pass (idempotent: it only ORs domain bits) on a sample of the
-    // frontier for each candidate chunk size and keep the fastest for this level.
-    void tune_chunk(const LevelSet &in, ExtArgs A) {
+    // Autotuner: time a pass on a sample of the frontier for each candidate chunk size and keep
+    // the fastest for this level: the domain pass (idempotent: it only ORs domain bits), or the
+    // fused pass, whose tables the caller wipes afterwards.
+    void tune_chunk(const LevelSet &in, ExtArgs A, int pass = PASS_DOMAIN) {
         const int L = in.L;
         if (!G->autotune || G->chunk > 0 || G->tuned_chunk[L] > 0 || in.N == 0) return;
         const int64_t ne = std::min<int64_t>(in.N, std::max<int64_t>(1024, in.N / 8));
@@ -370,7 +371,8 @@ struct Miner {
         ck(launch_unit_counts(A.g.ppc, in.fv, in.N, 0, ne, L, cnt, st), "unit counts");
         ck(launch_scan_i64(cnt, base, nu, tmp, st), "unit scan");
         const int64_t total = d2h(base + nu, st);
-        const int grid = grid_for(L, PASS_DOMAIN);
+        const int grid = grid_for(L, pass);
+        A.stats = nullptr;
         A.fv = in.fv;
         A.fpid = in.fpid;
         A.fN = in.N;
@@ -389,7 +391,8 @@ struct Miner {
             A.nchunks = (total + chunk - 1) / chunk;
             ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
             ck(cudaEventRecord(a, st), "event record");
-            ck(launch_extend_domain(L, A, grid, st), "extension kernel");
+            ck(pass == PASS_FUSED ? launch_extend_fused(L, A, grid, st) : launch_extend_domain(L, A, grid, st),
+               "extension kernel");
             ck(cudaEventRecord(b, st), "event record");
             ck(cudaEventSynchronize(b), "event sync");
             float ms = 0.f;
@@ -497,6 +500,18 @@ struct Miner {
             A.qp.used = used;
             A.qp.max_used = (unsigned long long)(cap / 2);
             A.stats = G->stats;
+            if (fused && G->autotune && G->chunk <= 0 && G->tuned_chunk[L] <= 0) {
+                // trial fused passes on a sample; their counts and bits are then wiped
+                tune_chunk(in, A, PASS_FUSED);
+                ck(launch_fill_u64(keys, FSM_EMPTY_KEY, cap, st), "fill");
+                ck(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long) * cap, st), "memset");
+                ck(cudaMemsetAsync(used, 0, sizeof(unsigned long long), st), "memset");
+                ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
+                ck(cudaMemsetAsync(G->stats, 0, 2 * sizeof(unsigned long long), st), "memset");
+                ck(cudaMemsetAsync(qdom, 0, sizeof(unsigned long long) * cap * 8, st), "memset");
+                ck(cudaMemsetAsync(pool, 0, pool_words * 4, st), "memset");
+                ck(cudaMemsetAsync(ptop, 0, sizeof(unsigned long long), st), "memset");
+            }
             run_pass(fused ? PASS_FUSED : PASS_COUNT, in, A, pat_off);
             const int ew = err_word();
             if (ew & FSM_ERR_QP_OVERFLOW) {
