@@ -226,3 +226,13 @@ def test_profile_option_counts_launches(fsm):
         assert s["count_launches_l3"] >= 1 and s["count_ns_l3"] > 0 and s["count_bytes_l3"] > 0
         assert s["domain_launches_l1"] >= 1 and s["emit_launches_l1"] >= 1
     G.close()
+
+
+@pytest.mark.parametrize("shape", [("cl3700k", 0.00012, 12), ("cl1100k", 0.0008, 12)])
+def test_config_shaped_graphs_k5(fsm, shape):
+    """Chung-Lu graphs shaped like the 3.7M-vertex workload (beta 2.3, 37 Zipf labels) and the
+    1.1M-vertex one (beta 2.0, 16 uniform labels), scaled to about a thousand vertices, k = 5."""
+    name, scale, cap = shape
+    g = gg.workload(name, scale=scale, cap=cap)
+    for t in (2, 4):
+        check(fsm, g, 5, t, "edge", {"launch": 1})
