@@ -181,7 +181,7 @@ def run_ours(args, rank, world, local_rank):
     def step(profile: bool):
         G.set_option("profile", 1 if profile else 0)
         tot = {"embeddings": 0, "kernel_launches": 0, "patterns_out": 0, "final_embeddings": 0}
-        tot.update({f"{p}_{f}_l{l}": 0 for p in ("count", "domain", "emit") for f in ("ns", "launches", "bytes")
+        tot.update({f"{p}_{f}_l{l}": 0 for p in ("count", "domain", "emit", "fused") for f in ("ns", "launches", "bytes")
                     for l in range(1, 7)})
         for t in ths:
             r = G.mine(args.k, t, stats=True)
@@ -253,7 +253,7 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant extension pass (launch durations from CUDA events in the library)
     passes = {(p, l): (agg[f"{p}_ns_l{l}"], agg[f"{p}_bytes_l{l}"], agg[f"{p}_launches_l{l}"])
-              for p in ("count", "domain", "emit") for l in range(1, 7)}
+              for p in ("count", "domain", "emit", "fused") for l in range(1, 7)}
     dom = max(passes, key=lambda q: passes[q][0])
     ns, byts, nl = passes[dom]
     peak, peak_kind = read_peaks()

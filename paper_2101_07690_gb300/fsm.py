@@ -274,9 +274,9 @@ def fsm_mlp_free(m: int) -> None:
 STATS = ["k", "levels", "candidates", "embeddings", "final_embeddings", "quick_patterns", "patterns",
          "live_patterns", "frontier_max", "kernel_launches", "time_ns", "final_level_ns",
          "count_ns", "domain_ns", "emit_ns", "count_launches", "domain_launches", "emit_launches",
-         "count_bytes", "domain_bytes", "emit_bytes", "sampled_candidates", "recount_patterns",
-         "recount_frontier"] + [
-             f"{p}_{f}_l{l}" for p in ("count", "domain", "emit") for f in ("ns", "launches", "bytes")
+         "count_bytes", "domain_bytes", "emit_bytes", "fused_ns", "fused_launches", "fused_bytes",
+         "sampled_candidates", "recount_patterns", "recount_frontier", "sampled_edges"] + [
+             f"{p}_{f}_l{l}" for p in ("count", "domain", "emit", "fused") for f in ("ns", "launches", "bytes")
              for l in range(1, 7)] + [f"chunk_l{l}" for l in range(1, 7)]
 
 

@@ -223,8 +223,9 @@ def test_profile_option_counts_launches(fsm):
         G.set_option("launch", launch)
         r = G.mine(5, 10, stats=True)
         s = r["stats"]
-        assert s["count_launches_l3"] >= 1 and s["count_ns_l3"] > 0 and s["count_bytes_l3"] > 0
-        assert s["domain_launches_l1"] >= 1 and s["emit_launches_l1"] >= 1
+        # the last level (3 -> 5) is one fused pass; the size-3 level has count, domain, emit
+        assert s["fused_launches_l3"] >= 1 and s["fused_ns_l3"] > 0 and s["fused_bytes_l3"] > 0
+        assert s["count_launches_l1"] >= 1 and s["domain_launches_l1"] >= 1 and s["emit_launches_l1"] >= 1
     G.close()
 
 
