@@ -83,9 +83,10 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
  *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
  *   "fused"      1 = the last level counts quick patterns and fills MNI domains in one pass,
- *                into per-key bitmaps merged per pattern afterwards (default); 0 = a count pass
- *                then a domain pass.  Both give identical results; a pool shortfall falls back
- *                to the two passes.
+ *                into per-key bitmaps merged per pattern afterwards; 0 = a count pass then a
+ *                domain pass (default: measured faster, as per-key bitmaps multiply the bit
+ *                atomics).  Both give identical results; a pool shortfall falls back to the two
+ *                passes.
  *   "fused_pool" size in 32-bit words of the per-key bitmap pool (0 = sized automatically).
  *   "seed"       64-bit seed of the piece sampling of fsm_mine with sample_rate < 1 (default 0).
  *   "candidates" 1 = sampled mining returns every candidate pattern of the sampled level with

@@ -118,7 +118,7 @@ struct fsm_graph {
     int sms = 0;
     int64_t qp_hint[FSM_MAXL + 1] = {};   // distinct quick patterns seen at each level last time
     int autotune = 0;
-    int fused = 1;
+    int fused = 0;
     unsigned long long pool_hint[FSM_MAXL + 1] = {};   // pool words the fused pass used last time
     unsigned long long pool_force = 0;                 // option "fused_pool": fixed pool size
     int32_t tuned_chunk[FSM_MAXL + 1] = {};   // chunk size chosen by the autotuner per level
