@@ -166,7 +166,8 @@ int fsm_result_features(const fsm_result *r, float *features);
 
 /*
  * fsm_result_stat -- a run counter of the mining call that made r:
- *   "k", "levels", "candidates" (joins tested), "embeddings" (accepted joins, all levels),
+ *   "k", "levels", "pieces" (size-3 pieces enumerated by the count passes), "candidates" (joins
+ *   tested), "embeddings" (accepted joins, all levels),
  *   "final_embeddings" (accepted joins of the last level), "quick_patterns" (distinct index
  *   based quick patterns, i.e. canonicalisations, all levels), "patterns" (distinct patterns
  *   of the last level), "live_patterns" (last-level patterns given a domain),

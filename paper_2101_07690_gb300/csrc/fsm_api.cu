@@ -177,7 +177,7 @@ struct LevelSet {
 };
 
 struct RunStats {
-    int64_t tested = 0, accepted = 0, qps = 0, patterns = 0, live = 0, frontier_max = 0, levels = 0,
+    int64_t tested = 0, accepted = 0, pieces = 0, qps = 0, patterns = 0, live = 0, frontier_max = 0, levels = 0,
             final_accepted = 0, launches = 0;
     // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
     int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0, sampled_edges = 0;
@@ -482,7 +482,7 @@ struct Miner {
             ck(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long) * cap, st), "memset");
             ck(cudaMemsetAsync(used, 0, sizeof(unsigned long long), st), "memset");
             ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
-            ck(cudaMemsetAsync(G->stats, 0, 2 * sizeof(unsigned long long), st), "memset");
+            ck(cudaMemsetAsync(G->stats, 0, 3 * sizeof(unsigned long long), st), "memset");
             if (fused) {
                 qdom = mem.get<unsigned long long>(cap * 8);
                 ck(cudaMemsetAsync(qdom, 0, sizeof(unsigned long long) * cap * 8, st), "memset");
@@ -507,7 +507,7 @@ struct Miner {
                 ck(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long) * cap, st), "memset");
                 ck(cudaMemsetAsync(used, 0, sizeof(unsigned long long), st), "memset");
                 ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
-                ck(cudaMemsetAsync(G->stats, 0, 2 * sizeof(unsigned long long), st), "memset");
+                ck(cudaMemsetAsync(G->stats, 0, 3 * sizeof(unsigned long long), st), "memset");
                 ck(cudaMemsetAsync(qdom, 0, sizeof(unsigned long long) * cap * 8, st), "memset");
                 ck(cudaMemsetAsync(pool, 0, pool_words * 4, st), "memset");
                 ck(cudaMemsetAsync(ptop, 0, sizeof(unsigned long long), st), "memset");
@@ -533,11 +533,12 @@ struct Miner {
             }
             break;
         }
-        unsigned long long st2[2];
+        unsigned long long st2[3];
         ck(cudaMemcpyAsync(st2, G->stats, sizeof(st2), cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaStreamSynchronize(st), "sync");
         rs.tested += (int64_t)st2[0];
         rs.accepted += (int64_t)st2[1];
+        rs.pieces += (int64_t)st2[2];
         if (final) rs.final_accepted = (int64_t)st2[1];
         // ---- distinct quick patterns -> canonical codes -> pattern ids
         int64_t *slots = mem.get<int64_t>(cap);
@@ -597,6 +598,9 @@ struct Miner {
         A.orbit = orbit;
         A.dom_off = doff;
         A.dom = dom;
+        int64_t *sbase = mem.get<int64_t>(cap * 8);
+        ck(launch_slot_bases(K, slots, nq, qpat, qperm, live, orbit, doff, sbase, st), "slot bases");
+        A.slot_base = sbase;
         A.stats = nullptr;
         if (rs.live > 0) {
             if (fused) {
@@ -673,6 +677,7 @@ struct Miner {
         const int ew = err_word();
         if (ew) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
         if (qdom) mem.release(qdom);
+        mem.release(sbase);
         for (void *p : std::initializer_list<void *>{keys, qcount, used, slots, nq_d, qpat, qperm, flag, ids, stmp, plab,
                                                      padj, orbit, minorb, pcount, live, words, woff, doff, stmp2, sigma,
                                                      fflag, fscan, newid})
@@ -1146,6 +1151,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["k"] = k;
         r->stats["levels"] = rs.levels;
         r->stats["candidates"] = rs.tested;
+        r->stats["pieces"] = rs.pieces;
         r->stats["embeddings"] = rs.accepted;
         r->stats["final_embeddings"] = rs.final_accepted;
         r->stats["quick_patterns"] = rs.qps;

@@ -66,13 +66,14 @@ struct ExtArgs {
     const uint64_t *orbit;         // [P'] 8 bytes: orbit representative per canonical position
     const int64_t *dom_off;        // [P'*8] word offset per orbit representative
     uint32_t *dom;
+    const int64_t *slot_base;      // [cap*8] bitmap word offset per (key slot, local position), -1 none
     // emission (PASS_EMIT)
     const int32_t *newid;          // [P'] id among frequent patterns, -1 otherwise
     int32_t *out_v;                // SoA [K][out_N]
     int32_t *out_pid;
     int64_t out_N;
     unsigned long long *out_cursor;
-    unsigned long long *stats;     // [0] joins tested, [1] joins accepted
+    unsigned long long *stats;     // [0] joins tested, [1] joins accepted, [2] pieces enumerated
     // fused pass: per-key bitmaps (offset + 1 into pool, 0 = none) and their pool
     unsigned long long *qp_dom;    // [cap * 8]
     uint32_t *pool;
@@ -225,11 +226,18 @@ __device__ __forceinline__ void flush_warp_counts(const ExtArgs &A, CountCache *
 }
 
 // One accepted join: act according to PASS.
-struct DomCache { uint32_t *w; uint32_t bits; };
+// Per-lane memory of bitmap words already set (PASS_DOMAIN, PASS_FUSED): the last word of a piece
+// vertex with its bits, and per position of s the last bitmap offset set for it (valid within
+// one unit: s and so its vertices' ranks are fixed there; -1 after a unit change).
+struct DomCache {
+    uint32_t *w;
+    uint32_t bits;
+    int64_t soff[FSM_MAXL];
+};
 
 template <int L, int PASS>
 __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCache &dc, uint64_t key,
-                                       const int32_t (&gid)[L + 2]) {
+                                       const int32_t (&gid)[L + 2], const int32_t (&rk)[L]) {
     constexpr int K = L + 2;
     if (PASS == PASS_COUNT) {
         const unsigned act = __activemask();
@@ -271,16 +279,23 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
     }
     int64_t slot = qp_find(A.qp, key);
     if (slot < 0) { atomicOr(A.err, FSM_ERR_QP_MISSING); return; }
-    const int32_t P = __ldg(A.qp.pattern + slot);
-    const uint32_t perm = __ldg(A.qp.perm + slot);
     if (PASS == PASS_DOMAIN) {
-        if (!__ldg(A.live + P)) return;
-        const uint64_t orb = __ldg(A.orbit + P);
+        // one load per position: the bitmap of the orbit this key's position h lands in
+        const int64_t *sb = A.slot_base + slot * 8;
+        if (__ldg(sb) < 0) return;   // pattern without domains
 #pragma unroll
-        for (int h = 0; h < K; ++h) {
-            const int c = (perm >> (3 * h)) & 7;
-            const int o = (int)(orb >> (8 * c)) & 0xff;
-            const int64_t off = __ldg(A.dom_off + (int64_t)P * 8 + o);
+        for (int h = 0; h < L; ++h) {
+            // a vertex of s: the same word for every join of this unit into the same orbit
+            const int64_t off = __ldg(sb + h);
+            if (off == dc.soff[h]) continue;
+            dc.soff[h] = off;
+            uint32_t *w = A.dom + off + (rk[h] >> 5);
+            const uint32_t bit = 1u << (rk[h] & 31);
+            if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+        }
+#pragma unroll
+        for (int h = L; h < K; ++h) {
+            const int64_t off = __ldg(sb + h);
             const int32_t r = __ldg(A.g.rank + gid[h]);
             uint32_t *w = A.dom + off + (r >> 5);
             const uint32_t bit = 1u << (r & 31);
@@ -289,7 +304,12 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
             if (w != dc.w) { dc.w = w; dc.bits = 0; }
             dc.bits |= bit;
         }
-    } else {  // PASS_EMIT
+        return;
+    }
+    const int32_t P = __ldg(A.qp.pattern + slot);
+    const uint32_t perm = __ldg(A.qp.perm + slot);
+    {
+        // PASS_EMIT
         const int32_t nid = __ldg(A.newid + P);
         if (nid < 0) return;
         const unsigned act = __activemask();
@@ -339,7 +359,7 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
                                            const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int shape,
                                            const int32_t (&pv)[3], const int (&pl)[3], Tally &tl,
                                            CountCache *cc, DomCache &dc, int32_t va, uint32_t ca, bool have_a,
-                                           uint32_t cb, bool have_b) {
+                                           uint32_t cb, bool have_b, const int32_t (&RK)[L]) {
     constexpr int K = L + 2;
     const uint32_t pidx = piece_index(shape, pl[0], pl[1], pl[2]);
     if (A.piece_freq && !__ldg(A.piece_freq + pidx)) return;
@@ -352,19 +372,6 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
     const int lx0 = pl[q0], lx1 = pl[q1];
     uint32_t tj0, tj1, txx;
     piece_join_edges(shape, jpos, tj0, tj1, txx);
-    if constexpr (L == 2) {
-        // Four-vertex joins: the greedy dissection from the smallest vertex m always succeeds
-        // (the one remaining vertex is adjacent to the 3-set), so the join survives only if m
-        // is in the piece and m's first greedy step stays in the piece.  Both are decided
-        // here, before any cross-adjacency test.
-        const int32_t w = S[1 - i];
-        const int32_t mt = min(v, min(x0, x1));
-        if (w < mt) return;                               // m = w: the 3-set contains w
-        if (mt == v) {                                    // m = v: its neighbours are w and the piece's
-            const int32_t first = tj1 ? min(x0, x1) : x0; // tj0 is always set
-            if (w < first) return;
-        }
-    }
 
     // cross adjacency between s \ {v} and {x0, x1}
     uint32_t avail = 0;
@@ -423,7 +430,7 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
         }
         if (keep) {
             ++tl.accepted;
-            accept<L, PASS>(A, cc, dc, make_key((uint32_t)pid, pidx, i, jpos, sub), gid);
+            accept<L, PASS>(A, cc, dc, make_key((uint32_t)pid, pidx, i, jpos, sub), gid, RK);
         }
         if (A.mode == 1 || sub == 0) break;
         sub = (sub - 1) & avail;
@@ -442,44 +449,26 @@ __device__ __forceinline__ uint32_t mask_bits(const uint32_t *mk, int32_t x) {
 template <int L, int PASS>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                          const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
-                                         CountCache *cc, DomCache &dc, const uint32_t *mk) {
+                                         CountCache *cc, DomCache &dc, const uint32_t *mk, const int32_t (&RK)[L]) {
     const DevGraph &g = A.g;
     const int32_t v = S[i];
     const int32_t rp = __ldg(g.prow + v);               // the lists pieces are drawn from
     const int32_t d = __ldg(g.prow + v + 1) - rp;
     const int64_t nc = (int64_t)d * (d - 1) / 2;
-    int32_t pv[3];
-    int pl[3];
-    if (lq < nc) {
+    // Decode the piece: a centre pair {a, b} of N(v), or an end piece v-a-b.  xa / xb are the
+    // positions of a / b in v's list when known (for the shared-memory masks), -1 otherwise.
+    const bool centre = lq < nc;
+    int32_t a, b, xa, xb;
+    if (centre) {
         // centre pair (x < y) with lq = y(y-1)/2 + x
         int32_t y = (int32_t)((1.0f + sqrtf(1.0f + 8.0f * (float)lq)) * 0.5f);
         while ((int64_t)y * (y - 1) / 2 > lq) --y;
         while ((int64_t)(y + 1) * y / 2 <= lq) ++y;
-        const int32_t x = (int32_t)(lq - (int64_t)y * (y - 1) / 2);
-        const int32_t a = __ldg(g.pcol + rp + x), b = __ldg(g.pcol + rp + y);
+        xa = (int32_t)(lq - (int64_t)y * (y - 1) / 2);
+        xb = y;
+        a = __ldg(g.pcol + rp + xa);
+        b = __ldg(g.pcol + rp + y);
         if (L == 1 && a < v) return;                 // size-3 subgraphs keyed at their smallest vertex
-        if (in_s<L>(S, a) || in_s<L>(S, b)) return;
-        const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
-        const bool tri = is_adj(g, a, b);
-        const bool hm = mk != nullptr;
-        const uint32_t ca = hm ? mask_bits<L>(mk, x) : 0u, cb = hm ? mask_bits<L>(mk, y) : 0u;
-        if (A.mode == 0 || !tri) {
-            pv[0] = v; pl[0] = SL[i];
-            if (lab_id_less(la, a, lb, b)) { pv[1] = a; pl[1] = la; pv[2] = b; pl[2] = lb; }
-            else { pv[1] = b; pl[1] = lb; pv[2] = a; pl[2] = la; }
-            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc, a, ca, hm, cb, hm);
-        }
-        if (tri) {
-            int32_t t0 = v, t1 = a, t2 = b;
-            int m0 = SL[i], m1 = la, m2 = lb, tl_;
-            int32_t tv;
-            if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
-            if (lab_id_less(m2, t2, m1, t1)) { tv = t1; t1 = t2; t2 = tv; tl_ = m1; m1 = m2; m2 = tl_; }
-            if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
-            pv[0] = t0; pv[1] = t1; pv[2] = t2;
-            pl[0] = m0; pl[1] = m1; pl[2] = m2;
-            join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_TRI, pv, pl, tl, cc, dc, a, ca, hm, cb, hm);
-        }
     } else {
         const int64_t lq2 = lq - nc;
         int32_t lo = 0, hi = d - 1;
@@ -487,28 +476,86 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             const int32_t mid = (lo + hi + 1) >> 1;
             if ((int64_t)__ldg(g.pend + rp + mid) <= lq2) lo = mid; else hi = mid - 1;
         }
-        const int32_t a = __ldg(g.pcol + rp + lo);
-        const int32_t b = __ldg(g.pcol + __ldg(g.prow + a) + (int32_t)(lq2 - __ldg(g.pend + rp + lo)));
+        xa = lo;
+        xb = -1;
+        a = __ldg(g.pcol + rp + lo);
+        b = __ldg(g.pcol + __ldg(g.prow + a) + (int32_t)(lq2 - __ldg(g.pend + rp + lo)));
         if (b == v) return;
         if (L == 1 && (a < v || b < v)) return;
-        if (in_s<L>(S, a) || in_s<L>(S, b)) return;
-        if (A.mode == 1 && is_adj(g, v, b)) return;  // the induced triple is the triangle (centre branch)
-        const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
-        pv[0] = a; pl[0] = la;
-        if (lab_id_less(SL[i], v, lb, b)) { pv[1] = v; pl[1] = SL[i]; pv[2] = b; pl[2] = lb; }
-        else { pv[1] = b; pl[1] = lb; pv[2] = v; pl[2] = SL[i]; }
-        const bool hm = mk != nullptr;
-        join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, PIECE_WEDGE, pv, pl, tl, cc, dc, a,
-                            hm ? mask_bits<L>(mk, lo) : 0u, hm, 0u, false);
+    }
+    if (in_s<L>(S, a) || in_s<L>(S, b)) return;
+    if constexpr (L == 2) {
+        // Four-vertex joins with w = S[1 - i]: the greedy dissection from the smallest vertex m
+        // always succeeds (the one vertex left is adjacent to the 3-set), so the join survives
+        // only if m is in the piece and m's first greedy step stays in it.  For a centre piece
+        // (v next to a and b) that fails exactly when w < min(a, b): either m = w, or m = v and
+        // w, the smallest neighbour of v, is taken before a and b.  For an end piece (v next to
+        // a only) it fails when w < min(v, a, b), or when v is that minimum and w < a.
+        const int32_t w = S[1 - i];
+        if (centre) {
+            if (w < min(a, b)) return;
+        } else {
+            const int32_t m = min(v, min(a, b));
+            if (w < m || (m == v && w < a)) return;
+        }
+    }
+    // closed triple: a centre pair with a ~ b (an end piece's b ~ v closes it as well, but that
+    // triangle is the centre pair {a, b} of v and is joined from there)
+    bool tri = false;
+    if (centre) tri = is_adj(g, a, b);
+    else if (A.mode == 1 && is_adj(g, v, b)) return;   // vertex-induced: only the triangle
+    const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
+    const bool hm = mk != nullptr;
+    const uint32_t ca = hm ? mask_bits<L>(mk, xa) : 0u;
+    const uint32_t cb = hm && centre ? mask_bits<L>(mk, xb) : 0u;
+    const bool have_b = hm && centre;
+    // One call site of join_piece (it is large): the wedge (edge-induced, or an open triple)
+    // and then the triangle of a closed centre pair.
+    const int j0 = (centre && tri && A.mode == 1) ? 1 : 0;
+    const int j1 = (centre && tri) ? 1 : 0;
+#pragma unroll 1
+    for (int jj = j0; jj <= j1; ++jj) {
+        int32_t pv[3];
+        int pl[3];
+        int shape = PIECE_WEDGE;
+        if (!centre) {
+            pv[0] = a; pl[0] = la;
+            if (lab_id_less(SL[i], v, lb, b)) { pv[1] = v; pl[1] = SL[i]; pv[2] = b; pl[2] = lb; }
+            else { pv[1] = b; pl[1] = lb; pv[2] = v; pl[2] = SL[i]; }
+        } else if (jj == 0) {
+            pv[0] = v; pl[0] = SL[i];
+            if (lab_id_less(la, a, lb, b)) { pv[1] = a; pl[1] = la; pv[2] = b; pl[2] = lb; }
+            else { pv[1] = b; pl[1] = lb; pv[2] = a; pl[2] = la; }
+        } else {
+            shape = PIECE_TRI;
+            int32_t t0 = v, t1 = a, t2 = b, tv;
+            int m0 = SL[i], m1 = la, m2 = lb, tl_;
+            if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
+            if (lab_id_less(m2, t2, m1, t1)) { tv = t1; t1 = t2; t2 = tv; tl_ = m1; m1 = m2; m2 = tl_; }
+            if (lab_id_less(m1, t1, m0, t0)) { tv = t0; t0 = t1; t1 = tv; tl_ = m0; m0 = m1; m1 = tl_; }
+            pv[0] = t0; pv[1] = t1; pv[2] = t2;
+            pl[0] = m0; pl[1] = m1; pl[2] = m2;
+        }
+        join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, shape, pv, pl, tl, cc, dc, a, ca, hm, cb, have_b, RK);
     }
 }
 
+// Resident blocks per SM asked of the compiler.  The kernel is bound by load latency, so
+// occupancy is bought with registers (what spills stays in L1).
+#define FSM_EXT_MINB_COUNT 6
+#define FSM_EXT_MINB_DOMAIN 8
+template <int PASS> struct ExtMinBlocks {
+    static constexpr int value = PASS == PASS_DOMAIN ? FSM_EXT_MINB_DOMAIN : FSM_EXT_MINB_COUNT;
+};
+
 template <int L, int PASS>
-__global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
+__global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(ExtArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t nunits = A.ne * L;
     Tally tl{0ull, 0ull};
-    DomCache dc{nullptr, 0u};
+    DomCache dc;
+    dc.w = nullptr;
+    dc.bits = 0u;
     __shared__ uint32_t mask_s[8 * (L > 1 ? L - 1 : 1) * FSM_MASK_WORDS];   // per warp, see below
     extern __shared__ unsigned long long dyn_smem[];   // CountCache in PASS_COUNT launches
     constexpr bool counts = PASS == PASS_COUNT || PASS == PASS_FUSED;
@@ -532,6 +579,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
         }
         nchunks = (total + chunk - 1) / chunk;
     }
+    if (A.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(A.stats + 2, (unsigned long long)total);
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) {
@@ -588,6 +636,7 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
         int32_t S[L];
         int SL[L];
         int2 SR[L];
+        int32_t RK[L];
         int32_t pid = 0;
         int i = 0;
         uint64_t srows = 0;
@@ -602,12 +651,15 @@ __global__ void __launch_bounds__(256) extend_kernel(ExtArgs A) {
                     S[p] = __ldg(A.fv + (int64_t)p * A.fN + e);
                     SL[p] = __ldg(A.g.labels + S[p]);
                     SR[p] = make_int2(__ldg(A.g.row_ptr + S[p]), __ldg(A.g.row_ptr + S[p] + 1));
+                    RK[p] = PASS == PASS_DOMAIN ? __ldg(A.g.rank + S[p]) : 0;
                 }
                 pid = __ldg(A.fpid + e);
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
                 ub = __ldg(A.unit_base + u);
+#pragma unroll
+                for (int p = 0; p < L; ++p) dc.soff[p] = -1;
             }
-            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk);
+            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK);
         }
         if (counts) flush_warp_counts(A, cc);
     }

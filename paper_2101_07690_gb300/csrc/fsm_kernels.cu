@@ -1286,6 +1286,36 @@ cudaError_t launch_merge_domains(int K, const int64_t *slots, int64_t nq, const 
     return cudaGetLastError();
 }
 
+namespace {
+__global__ void slot_bases_kernel(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                                  const uint32_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
+                                  const int64_t *dom_off, int64_t *slot_base) {
+    for (int64_t q = gtid(); q < nq; q += gstride()) {
+        const int64_t slot = slots[q];
+        const int32_t P = qp_pattern[slot];
+        for (int h = 0; h < 8; ++h) {
+            int64_t b = -1;
+            if (h < K && live[P]) {
+                const int c = (int)((qp_perm[slot] >> (3 * h)) & 7u);
+                const int o = (int)((orbit[P] >> (8 * c)) & 0xff);
+                b = dom_off[(int64_t)P * 8 + o];
+            }
+            slot_base[slot * 8 + h] = b;
+        }
+    }
+}
+} // namespace
+
+cudaError_t launch_slot_bases(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                              const uint32_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
+                              const int64_t *dom_off, int64_t *slot_base, cudaStream_t st) {
+    if (nq <= 0) return cudaSuccess;
+    LAUNCHED(1);
+    slot_bases_kernel<<<blocks_for(nq), kThreads, 0, st>>>(K, slots, nq, qp_pattern, qp_perm, live, orbit, dom_off,
+                                                           slot_base);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;

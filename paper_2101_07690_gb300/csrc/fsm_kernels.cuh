@@ -178,6 +178,13 @@ cudaError_t launch_merge_domains(int K, const int64_t *slots, int64_t nq, const 
                                  const uint8_t *live, const uint64_t *orbit, const int64_t *dom_off,
                                  const int64_t *words, uint32_t *dom, cudaStream_t st);
 
+// Domain pass helper: for every distinct key (slot) and local position h, the word offset of
+// the bitmap its vertex goes to (the orbit of canonical position perm[h] of its pattern), or -1
+// when the pattern has no domains.
+cudaError_t launch_slot_bases(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
+                              const uint32_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
+                              const int64_t *dom_off, int64_t *slot_base, cudaStream_t st);
+
 // ---- pieces: mark the frequent size-3 patterns by piece index
 cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st);

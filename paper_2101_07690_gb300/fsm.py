@@ -271,7 +271,7 @@ def fsm_mlp_free(m: int) -> None:
         load().fsm_mlp_free(m)
 
 
-STATS = ["k", "levels", "candidates", "embeddings", "final_embeddings", "quick_patterns", "patterns",
+STATS = ["k", "levels", "pieces", "candidates", "embeddings", "final_embeddings", "quick_patterns", "patterns",
          "live_patterns", "frontier_max", "kernel_launches", "time_ns", "final_level_ns",
          "count_ns", "domain_ns", "emit_ns", "count_launches", "domain_launches", "emit_launches",
          "count_bytes", "domain_bytes", "emit_bytes", "fused_ns", "fused_launches", "fused_bytes",
