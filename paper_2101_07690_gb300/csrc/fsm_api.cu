@@ -281,7 +281,7 @@ struct Miner {
             cudaGraphExec_t exec = nullptr;
             ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g.ppc, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
                 ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
                 bytes(r);
                 ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
@@ -302,7 +302,7 @@ struct Miner {
             ck(cudaGraphDestroy(graph), "graph destroy");
         } else {
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g.ppc, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
                 ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
                 const int64_t total = d2h(base + r.ne * L, st);
                 if (total == 0) continue;
@@ -368,7 +368,7 @@ struct Miner {
         int64_t *base = mem.get<int64_t>(nu + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(nu) + 16);
         unsigned long long *ctr = mem.get<unsigned long long>(1);
-        ck(launch_unit_counts(A.g.ppc, in.fv, in.N, 0, ne, L, cnt, st), "unit counts");
+        ck(launch_unit_counts(A.g, in.fv, in.N, 0, ne, L, cnt, st), "unit counts");
         ck(launch_scan_i64(cnt, base, nu, tmp, st), "unit scan");
         const int64_t total = d2h(base + nu, st);
         const int grid = grid_for(L, pass);

@@ -72,6 +72,25 @@ __device__ __forceinline__ bool is_adj(const DevGraph &g, int32_t u, int32_t w) 
 enum { PIECE_WEDGE = 0, PIECE_TRI = 1 };
 #define FSM_PIECE_SPACE (1 << 19)
 
+// Entries of the sorted list a[0, n) below x.
+FSM_HD int32_t count_below(const int32_t *a, int32_t n, int32_t x) {
+    int32_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Centre pairs a unit enumerates.  In general every pair x < y of the key vertex's list of
+// length d.  When s is one edge {v, w} (l = 2), the join survives dissection only if the piece
+// holds a vertex below w (see do_piece), so only pairs whose smaller end a (position x) is below
+// w are enumerated: x < c, c = entries of v's list below w.  Rows y < c hold y pairs, later rows
+// c pairs each.
+FSM_HD int64_t centre_pairs(int64_t d, int64_t c) {
+    return c * (c - 1) / 2 + (d - c) * c;
+}
+
 FSM_HD uint32_t piece_index(int shape, int l0, int l1, int l2) {
     return ((uint32_t)shape << 18) | ((uint32_t)l0 << 12) | ((uint32_t)l1 << 6) | (uint32_t)l2;
 }

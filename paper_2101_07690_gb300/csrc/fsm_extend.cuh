@@ -300,7 +300,7 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
             uint32_t *w = A.dom + off + (r >> 5);
             const uint32_t bit = 1u << (r & 31);
             if (w == dc.w && (dc.bits & bit)) continue;   // this lane set it already
-            if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+            atomicOr(w, bit);   // no pre-check: these words miss L2, and a reduction does not wait
             if (w != dc.w) { dc.w = w; dc.bits = 0; }
             dc.bits |= bit;
         }
@@ -449,22 +449,33 @@ __device__ __forceinline__ uint32_t mask_bits(const uint32_t *mk, int32_t x) {
 template <int L, int PASS>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                          const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
-                                         CountCache *cc, DomCache &dc, const uint32_t *mk, const int32_t (&RK)[L]) {
+                                         CountCache *cc, DomCache &dc, const uint32_t *mk, const int32_t (&RK)[L],
+                                         int32_t cpos) {
     const DevGraph &g = A.g;
     const int32_t v = S[i];
     const int32_t rp = __ldg(g.prow + v);               // the lists pieces are drawn from
     const int32_t d = __ldg(g.prow + v + 1) - rp;
-    const int64_t nc = (int64_t)d * (d - 1) / 2;
+    // centre pairs first: all pairs of v's list, or for l = 2 those with x < cpos
+    const int64_t nt = L == 2 ? (int64_t)cpos * (cpos - 1) / 2 : (int64_t)d * (d - 1) / 2;
+    const int64_t nc = L == 2 ? centre_pairs(d, cpos) : nt;
     // Decode the piece: a centre pair {a, b} of N(v), or an end piece v-a-b.  xa / xb are the
     // positions of a / b in v's list when known (for the shared-memory masks), -1 otherwise.
     const bool centre = lq < nc;
     int32_t a, b, xa, xb;
     if (centre) {
-        // centre pair (x < y) with lq = y(y-1)/2 + x
-        int32_t y = (int32_t)((1.0f + sqrtf(1.0f + 8.0f * (float)lq)) * 0.5f);
-        while ((int64_t)y * (y - 1) / 2 > lq) --y;
-        while ((int64_t)(y + 1) * y / 2 <= lq) ++y;
-        xa = (int32_t)(lq - (int64_t)y * (y - 1) / 2);
+        int32_t y;
+        if (lq < nt) {
+            // pair (x < y) of the triangle y < cpos (all of the list when l != 2), lq = y(y-1)/2 + x
+            y = (int32_t)((1.0f + sqrtf(1.0f + 8.0f * (float)lq)) * 0.5f);
+            while ((int64_t)y * (y - 1) / 2 > lq) --y;
+            while ((int64_t)(y + 1) * y / 2 <= lq) ++y;
+            xa = (int32_t)(lq - (int64_t)y * (y - 1) / 2);
+        } else {
+            // l = 2, rows y >= cpos: cpos pairs each
+            const int64_t r = lq - nt;
+            y = cpos + (int32_t)(r / cpos);
+            xa = (int32_t)(r % cpos);
+        }
         xb = y;
         a = __ldg(g.pcol + rp + xa);
         b = __ldg(g.pcol + rp + y);
@@ -491,10 +502,9 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         // (v next to a and b) that fails exactly when w < min(a, b): either m = w, or m = v and
         // w, the smallest neighbour of v, is taken before a and b.  For an end piece (v next to
         // a only) it fails when w < min(v, a, b), or when v is that minimum and w < a.
+        // The first case is already cut from the centre pairs' index space (x < cpos).
         const int32_t w = S[1 - i];
-        if (centre) {
-            if (w < min(a, b)) return;
-        } else {
+        if (!centre) {
             const int32_t m = min(v, min(a, b));
             if (w < m || (m == v && w < a)) return;
         }
@@ -542,8 +552,8 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
 
 // Resident blocks per SM asked of the compiler.  The kernel is bound by load latency, so
 // occupancy is bought with registers (what spills stays in L1).
-#define FSM_EXT_MINB_COUNT 6
-#define FSM_EXT_MINB_DOMAIN 8
+#define FSM_EXT_MINB_COUNT 4
+#define FSM_EXT_MINB_DOMAIN 4
 template <int PASS> struct ExtMinBlocks {
     static constexpr int value = PASS == PASS_DOMAIN ? FSM_EXT_MINB_DOMAIN : FSM_EXT_MINB_COUNT;
 };
@@ -633,6 +643,7 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
             }
         }
         int64_t cur = -1, ub = 0;
+        int32_t cpos = 0;   // l = 2: entries of the key vertex's list below the other vertex of s
         int32_t S[L];
         int SL[L];
         int2 SR[L];
@@ -656,10 +667,14 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
                 pid = __ldg(A.fpid + e);
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
                 ub = __ldg(A.unit_base + u);
+                if constexpr (L == 2) {
+                    const int32_t rb = __ldg(A.g.prow + S[i]);
+                    cpos = count_below(A.g.pcol + rb, __ldg(A.g.prow + S[i] + 1) - rb, S[1 - i]);
+                }
 #pragma unroll
                 for (int p = 0; p < L; ++p) dc.soff[p] = -1;
             }
-            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK);
+            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos);
         }
         if (counts) flush_warp_counts(A, cc);
     }

@@ -178,13 +178,21 @@ cudaError_t launch_prepare(const DevGraph &g, int64_t *piece_cnt, int32_t *end_o
 // ------------------------------------------------------------------ unit counts
 
 namespace {
-__global__ void unit_counts_kernel(const int64_t *piece_cnt, const int32_t *fv, int64_t fN, int64_t e0,
-                                   int64_t ne, int L, int64_t *cnt) {
+__global__ void unit_counts_kernel(const DevGraph g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
+                                   int64_t *cnt) {
     const int64_t nu = ne * L;
     for (int64_t u = gtid(); u < nu; u += gstride()) {
         const int64_t e = e0 + u / L;
         const int p = (int)(u % L);
-        cnt[u] = piece_cnt[fv[(int64_t)p * fN + e]];
+        const int32_t v = fv[(int64_t)p * fN + e];
+        int64_t c = g.ppc[v];
+        if (L == 2) {
+            // centre pairs restricted to those with an end below the other vertex of s
+            const int32_t w = fv[(int64_t)(1 - p) * fN + e];
+            const int32_t rb = g.prow[v], d = g.prow[v + 1] - rb;
+            c += centre_pairs(d, count_below(g.pcol + rb, d, w)) - (int64_t)d * (d - 1) / 2;
+        }
+        cnt[u] = c;
     }
 }
 
@@ -203,10 +211,10 @@ __global__ void qp_compact_kernel(const unsigned long long *keys, int64_t cap, i
 }
 } // namespace
 
-cudaError_t launch_unit_counts(const int64_t *piece_cnt, const int32_t *fv, int64_t fN, int64_t e0,
-                               int64_t ne, int L, int64_t *cnt, cudaStream_t st) {
+cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
+                               int64_t *cnt, cudaStream_t st) {
     LAUNCHED(1);
-    unit_counts_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(piece_cnt, fv, fN, e0, ne, L, cnt);
+    unit_counts_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(g, fv, fN, e0, ne, L, cnt);
     return cudaGetLastError();
 }
 

@@ -25,9 +25,10 @@ cudaError_t launch_prepare(const DevGraph &g, int64_t *piece_cnt, int32_t *end_o
 size_t scan_temp_bytes(int64_t n);
 cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *temp, cudaStream_t st);
 
-// ---- per-batch unit piece counts: cnt[u] = piece_cnt[fv[(u % L) * fN + e0 + u / L]]
-cudaError_t launch_unit_counts(const int64_t *piece_cnt, const int32_t *fv, int64_t fN, int64_t e0,
-                               int64_t ne, int L, int64_t *cnt, cudaStream_t st);
+// ---- per-batch unit piece counts: cnt[u] = g.ppc[v] for the key vertex v = fv[(u % L) * fN + e0 + u / L],
+//      with the centre pairs cut to centre_pairs(d, c) when L == 2 (see fsm_device.cuh)
+cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
+                               int64_t *cnt, cudaStream_t st);
 
 // algorithmic bytes of one batch of units, added to *sum: per unit 4 * (d(v) + end pieces of v)
 // (the key list and every end list read once) plus 4 * (L + 1) per embedding (vertices + id)
