@@ -450,7 +450,7 @@ template <int L, int PASS>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                          const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
                                          CountCache *cc, DomCache &dc, const uint32_t *mk, const int32_t (&RK)[L],
-                                         int32_t cpos) {
+                                         int32_t cpos, int32_t &ecur) {
     const DevGraph &g = A.g;
     const int32_t v = S[i];
     const int32_t rp = __ldg(g.prow + v);               // the lists pieces are drawn from
@@ -482,11 +482,23 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         if (L == 1 && a < v) return;                 // size-3 subgraphs keyed at their smallest vertex
     } else {
         const int64_t lq2 = lq - nc;
-        int32_t lo = 0, hi = d - 1;
-        while (lo < hi) {
-            const int32_t mid = (lo + hi + 1) >> 1;
-            if ((int64_t)__ldg(g.pend + rp + mid) <= lq2) lo = mid; else hi = mid - 1;
+        // the end list holding lq2: largest lo with pend[lo] <= lq2.  A lane walks a unit's
+        // pieces in increasing order, so it starts from its previous answer (ecur) and usually
+        // stays there or moves one list on; otherwise it searches the rest of the range.
+        int32_t lo = ecur;
+        if (lo >= d || (int64_t)__ldg(g.pend + rp + lo) > lq2) lo = 0;
+        if (lo + 1 < d && (int64_t)__ldg(g.pend + rp + lo + 1) <= lq2) {
+            ++lo;
+            if (lo + 1 < d && (int64_t)__ldg(g.pend + rp + lo + 1) <= lq2) {
+                int32_t hi = d - 1;
+                ++lo;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi + 1) >> 1;
+                    if ((int64_t)__ldg(g.pend + rp + mid) <= lq2) lo = mid; else hi = mid - 1;
+                }
+            }
         }
+        ecur = lo;
         xa = lo;
         xb = -1;
         a = __ldg(g.pcol + rp + lo);
@@ -644,6 +656,7 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
         }
         int64_t cur = -1, ub = 0;
         int32_t cpos = 0;   // l = 2: entries of the key vertex's list below the other vertex of s
+        int32_t ecur = 0;   // end list of this lane's last end piece in the unit
         int32_t S[L];
         int SL[L];
         int2 SR[L];
@@ -667,6 +680,7 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
                 pid = __ldg(A.fpid + e);
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
                 ub = __ldg(A.unit_base + u);
+                ecur = 0;
                 if constexpr (L == 2) {
                     const int32_t rb = __ldg(A.g.prow + S[i]);
                     cpos = count_below(A.g.pcol + rb, __ldg(A.g.prow + S[i] + 1) - rb, S[1 - i]);
@@ -674,7 +688,7 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
 #pragma unroll
                 for (int p = 0; p < L; ++p) dc.soff[p] = -1;
             }
-            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos);
+            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos, ecur);
         }
         if (counts) flush_warp_counts(A, cc);
     }
