@@ -132,6 +132,8 @@ struct fsm_graph {
     int32_t *row_ptr = nullptr, *col = nullptr, *labels = nullptr, *rank = nullptr, *cls_size = nullptr,
             *end_off = nullptr;
     int64_t *piece_cnt = nullptr;
+    int64_t *tri_off = nullptr;   // neighbour-adjacency matrices of high-degree vertices
+    uint32_t *tri_bits = nullptr;
     int *err = nullptr;
     unsigned long long *stats = nullptr;   // [0] tested, [1] accepted, [2..] scratch counters
     DevGraph dg() const {
@@ -148,6 +150,8 @@ struct fsm_graph {
         g.pcol = col;
         g.pend = end_off;
         g.ppc = piece_cnt;
+        g.tri_off = tri_off;
+        g.tri_bits = tri_bits;
         return g;
     }
 };
@@ -445,6 +449,8 @@ struct Miner {
             A.g.pcol = pcol;
             A.g.pend = pend;
             A.g.ppc = ppc;
+            A.g.tri_off = nullptr;   // the matrices index the full lists
+            A.g.tri_bits = nullptr;
             rs.sampled_edges = kept;
         }
         const int64_t t_live = sampled ? 1 : t;   // sampled counts say nothing about reaching t
@@ -992,6 +998,32 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
         const int ew = d2h(g->err, st);
         if (ew) fail(FSM_EINVAL, "malformed CSR: rows must be sorted, symmetric, without self-loops or duplicates, labels in range");
         ck(launch_prepare(g->dg(), g->piece_cnt, g->end_off, g->rank, g->cls_size, st), "prepare");
+        {
+            // Neighbour-adjacency matrices for the triangle test of centre pairs, for vertices
+            // of degree >= dmin; dmin doubles until they fit the budget.
+            int64_t *words = nullptr, *off = nullptr;
+            void *tmp = nullptr;
+            dalloc((void **)&words, sizeof(int64_t) * std::max<int64_t>(n, 1));
+            dalloc((void **)&off, sizeof(int64_t) * (n + 1));
+            dalloc(&tmp, scan_temp_bytes(n) + 16);
+            int32_t dmin = FSM_TRI_DMIN;
+            int64_t total = 0;
+            for (;;) {
+                ck(launch_tri_words(g->dg(), dmin, words, st), "matrix sizes");
+                ck(launch_scan_i64(words, off, n, tmp, st), "matrix offsets");
+                total = d2h(off + n, st);
+                if (total * 4 <= FSM_TRI_BUDGET || dmin > (1 << 30) / 2) break;
+                dmin *= 2;
+            }
+            if (total * 4 > FSM_TRI_BUDGET) total = 0, dmin = 0x7fffffff;
+            dalloc((void **)&g->tri_off, sizeof(int64_t) * std::max<int64_t>(n, 1));
+            dalloc((void **)&g->tri_bits, sizeof(uint32_t) * std::max<int64_t>(total, 1));
+            ck(cudaMemsetAsync(g->tri_bits, 0, sizeof(uint32_t) * std::max<int64_t>(total, 1), st), "memset");
+            ck(launch_tri_bits(g->dg(), dmin, off, g->tri_off, g->tri_bits, st), "neighbour matrices");
+            cudaFreeAsync(words, st);
+            cudaFreeAsync(off, st);
+            cudaFreeAsync(tmp, st);
+        }
         dalloc((void **)&g->by_rank, sizeof(int32_t) * n);
         dalloc((void **)&g->cls_off, sizeof(int64_t) * 65);
         ck(launch_by_rank(g->dg(), num_labels, g->cls_size, g->cls_off, g->by_rank, st), "rank table");
@@ -1249,7 +1281,7 @@ void fsm_free_result(fsm_result *r) { delete r; }
 void fsm_free_graph(fsm_graph *g) {
     if (!g) return;
     cudaStream_t st = g->stream ? g->stream : g->own_stream;
-    void *ps[] = {g->row_ptr, g->col, g->labels, g->rank, g->cls_size, g->end_off, g->piece_cnt, g->err, g->stats,
+    void *ps[] = {g->row_ptr, g->col, g->labels, g->rank, g->cls_size, g->end_off, g->piece_cnt, g->tri_off, g->tri_bits, g->err, g->stats,
                   g->by_rank, g->cls_off};
     for (void *p : ps)
         if (p) cudaFreeAsync(p, st);

@@ -45,6 +45,12 @@ struct DevGraph {
     // adjacency tests always use row_ptr / col.
     const int32_t *prow, *pcol, *pend;
     const int64_t *ppc;
+    // Neighbour adjacency of high-degree vertices: for v with tri_off[v] >= 0, bit y of row x
+    // (x < y < d(v)) of a d(v) x ceil(d(v)/32)-word matrix at word tri_off[v] of tri_bits says
+    // whether the x-th and y-th neighbours of v are adjacent.  Indexed by positions in the
+    // graph's own lists, so it is NULL while pieces come from other lists (sampled level).
+    const int64_t *tri_off;
+    const uint32_t *tri_bits;
 };
 
 // Is w a neighbour of u?  Binary search in the shorter of the two sorted lists.

@@ -524,7 +524,13 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
     // closed triple: a centre pair with a ~ b (an end piece's b ~ v closes it as well, but that
     // triangle is the centre pair {a, b} of v and is joined from there)
     bool tri = false;
-    if (centre) tri = is_adj(g, a, b);
+    if (centre) {
+        const int64_t moff = g.tri_off ? __ldg(g.tri_off + v) : -1;
+        if (moff >= 0)   // v's neighbour matrix: bit (xa, xb), xa < xb
+            tri = (__ldg(g.tri_bits + moff + (int64_t)xa * ((d + 31) >> 5) + (xb >> 5)) >> (xb & 31)) & 1u;
+        else
+            tri = is_adj(g, a, b);
+    }
     else if (A.mode == 1 && is_adj(g, v, b)) return;   // vertex-induced: only the triangle
     const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
     const bool hm = mk != nullptr;

@@ -67,6 +67,41 @@ __global__ void prepare_kernel(DevGraph g, int64_t *piece_cnt, int32_t *end_off,
     }
 }
 
+// Neighbour-adjacency matrices (see DevGraph::tri_off).  Words per vertex: d * ceil(d / 32) for
+// d >= dmin, else 0.
+__global__ void tri_words_kernel(DevGraph g, int32_t dmin, int64_t *words) {
+    for (int64_t v = gtid(); v < g.n; v += gstride()) {
+        const int64_t d = g.row_ptr[v + 1] - g.row_ptr[v];
+        words[v] = d >= dmin ? d * ((d + 31) / 32) : 0;
+    }
+}
+// One warp per vertex with a matrix: for its x-th neighbour a, every neighbour c of a that is
+// also the y-th neighbour of v (y > x, found by binary search in v's sorted list) sets bit
+// (x, y).
+__global__ void tri_bits_kernel(DevGraph g, int32_t dmin, const int64_t *off, int64_t *tri_off, uint32_t *bits) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = gtid() >> 5; v < g.n; v += gstride() >> 5) {
+        const int32_t rv = g.row_ptr[v], d = g.row_ptr[v + 1] - rv;
+        if (d < dmin) {
+            if (lane == 0) tri_off[v] = -1;
+            continue;
+        }
+        const int64_t base = off[v];
+        const int32_t stride = (d + 31) >> 5;
+        if (lane == 0) tri_off[v] = base;
+        for (int32_t x = 0; x + 1 < d; ++x) {
+            const int32_t a = g.col[rv + x];
+            const int32_t ra = g.row_ptr[a], da = g.row_ptr[a + 1] - ra;
+            for (int32_t j = lane; j < da; j += 32) {
+                const int32_t c = g.col[ra + j];
+                const int32_t y = count_below(g.col + rv, d, c);
+                if (y > x && y < d && g.col[rv + y] == c)
+                    atomicOr(bits + base + (int64_t)x * stride + (y >> 5), 1u << (y & 31));
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ scan (exclusive, int64)
 
 constexpr int kScanThreads = 1024;
@@ -210,6 +245,19 @@ __global__ void qp_compact_kernel(const unsigned long long *keys, int64_t cap, i
     }
 }
 } // namespace
+
+cudaError_t launch_tri_words(const DevGraph &g, int32_t dmin, int64_t *words, cudaStream_t st) {
+    LAUNCHED(1);
+    tri_words_kernel<<<blocks_for(g.n), kThreads, 0, st>>>(g, dmin, words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tri_bits(const DevGraph &g, int32_t dmin, const int64_t *off, int64_t *tri_off, uint32_t *bits,
+                            cudaStream_t st) {
+    LAUNCHED(1);
+    tri_bits_kernel<<<blocks_for(g.n * 32), kThreads, 0, st>>>(g, dmin, off, tri_off, bits);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
                                int64_t *cnt, cudaStream_t st) {

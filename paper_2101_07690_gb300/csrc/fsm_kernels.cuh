@@ -21,6 +21,15 @@ cudaError_t launch_validate(const DevGraph &g, int32_t num_labels, int *err, cud
 cudaError_t launch_prepare(const DevGraph &g, int64_t *piece_cnt, int32_t *end_off, int32_t *rank,
                            int32_t *cls_size, cudaStream_t st);
 
+// ---- neighbour-adjacency matrices of vertices of degree >= dmin (DevGraph::tri_off):
+//      words[v] = d * ceil(d / 32) or 0; then, with off = exclusive prefix of words, the bits
+//      and tri_off (-1 for vertices without a matrix); bits must be zeroed first
+#define FSM_TRI_DMIN 32
+#define FSM_TRI_BUDGET ((int64_t)512 << 20)   // bytes
+cudaError_t launch_tri_words(const DevGraph &g, int32_t dmin, int64_t *words, cudaStream_t st);
+cudaError_t launch_tri_bits(const DevGraph &g, int32_t dmin, const int64_t *off, int64_t *tri_off, uint32_t *bits,
+                            cudaStream_t st);
+
 // ---- scans (exclusive, out has n+1 entries, out[n] = total)
 size_t scan_temp_bytes(int64_t n);
 cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *temp, cudaStream_t st);

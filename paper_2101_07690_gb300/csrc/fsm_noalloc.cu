@@ -113,6 +113,8 @@ extern "C" int fsm_edge_supports_noalloc(const int32_t *d_row_ptr, const int32_t
     g.labels = d_labels;
     g.rank = rank;
     g.piece_cnt = nullptr;
+    g.tri_off = nullptr;
+    g.tri_bits = nullptr;
     g.end_off = nullptr;
     e = fsm::launch_validate(g, num_labels, errw, st);
     int bad = 0;
