@@ -152,6 +152,31 @@ __device__ __forceinline__ bool in_s(const int32_t (&S)[L], int32_t x) {
 
 struct Tally { unsigned long long tested, accepted; };
 
+// Local vertex of smallest id among the bits of m (four vertices).
+FSM_HD int argmin4(uint32_t m, const int32_t (&gid)[4]) {
+    int b = -1;
+#pragma unroll
+    for (int h = 0; h < 4; ++h)
+        if ((m >> h & 1u) && (b < 0 || gid[h] < gid[b])) b = h;
+    return b;
+}
+
+// Algorithm 1 for a four-vertex join (s = local 0, 1 with key position i; piece vertices 2, 3),
+// as a closed form.  The greedy round from the smallest vertex m always succeeds for four
+// vertices (the one vertex left is adjacent to the connected 3-set), so the dissection is that
+// round: the 3-set {m, n1, n2}, n1 the smallest neighbour of m and n2 the smallest further
+// neighbour of {m, n1}, joined at its smallest vertex adjacent to the fourth.  The join is kept
+// when that 3-set is the piece and the join vertex is s[i] -- what dissect3 returns, without
+// its loops.
+FSM_HD bool dissect4_keeps(const int32_t (&gid)[4], const uint32_t (&adj)[4], int i) {
+    const int m = argmin4(15u, gid);
+    const int n1 = argmin4(adj[m], gid);
+    const int n2 = argmin4((adj[m] | adj[n1]) & ~((1u << m) | (1u << n1)), gid);
+    const uint32_t l = (1u << m) | (1u << n1) | (1u << n2);
+    if (l != ((1u << i) | 12u)) return false;
+    return argmin4(adj[1 - i] & l, gid) == i;
+}
+
 // neighbour-adjacency masks of single-unit chunks: key vertices of degree up to 32 * this
 #define FSM_MASK_WORDS 64
 
@@ -165,8 +190,10 @@ struct Tally { unsigned long long tested, accepted; };
 struct CountCache {
     unsigned long long key[8][FSM_WARP_SLOTS];
     unsigned long long cnt[8][FSM_WARP_SLOTS];
-    long long slot[8][FSM_WARP_SLOTS];   // global slot of the key, -1 until resolved
+    long long slot[8][FSM_WARP_SLOTS];   // global slot of the key, -1 until resolved (PASS_FUSED)
 };
+// PASS_COUNT launches allocate only key and cnt: more of the SM's shared storage stays L1.
+#define FSM_COUNT_SMEM (2 * 8 * FSM_WARP_SLOTS * sizeof(unsigned long long))
 
 // Count n more joins of key through the warp's table; returns the key's global slot (resolved
 // once per table entry; a race resolves it twice to the same value).
@@ -209,18 +236,19 @@ __device__ __forceinline__ void count_key(const ExtArgs &A, CountCache *cc, uint
 }
 
 // warp-synchronous: every lane of the warp calls it
+template <bool SLOTS>
 __device__ __forceinline__ void flush_warp_counts(const ExtArgs &A, CountCache *cc) {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncwarp();
     for (int x = lane; x < FSM_WARP_SLOTS; x += 32) {
         const unsigned long long key = cc->key[w][x];
         if (key == FSM_EMPTY_KEY) continue;
-        int64_t slot = cc->slot[w][x];
+        int64_t slot = SLOTS ? cc->slot[w][x] : -1;
         if (slot < 0) slot = qp_insert(A.qp, key, A.err);
         if (slot >= 0) atomicAdd(A.qp.count + slot, cc->cnt[w][x]);
         cc->key[w][x] = FSM_EMPTY_KEY;
         cc->cnt[w][x] = 0ull;
-        cc->slot[w][x] = -1;
+        if (SLOTS) cc->slot[w][x] = -1;
     }
     __syncwarp();
 }
@@ -423,10 +451,14 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
             // smallest-vertex-first dissection must return exactly (t, s)
             uint32_t adjK[K];
             join_graph(L, srows, i, tj0, tj1, txx, sub, adjK);
-            uint32_t lm = 0;
-            int jn = -1;
-            dissect3(K, gid, adjK, lm, jn);
-            keep = (lm == ((1u << i) | (1u << L) | (1u << (L + 1)))) && jn == i;
+            if constexpr (L == 2) {
+                keep = dissect4_keeps(gid, adjK, i);
+            } else {
+                uint32_t lm = 0;
+                int jn = -1;
+                dissect3(K, gid, adjK, lm, jn);
+                keep = (lm == ((1u << i) | (1u << L) | (1u << (L + 1)))) && jn == i;
+            }
         }
         if (keep) {
             ++tl.accepted;
@@ -592,7 +624,7 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
         for (int x = threadIdx.x; x < 8 * FSM_WARP_SLOTS; x += blockDim.x) {
             cc->key[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = FSM_EMPTY_KEY;
             cc->cnt[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = 0ull;
-            cc->slot[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = -1;
+            if (PASS == PASS_FUSED) cc->slot[x / FSM_WARP_SLOTS][x % FSM_WARP_SLOTS] = -1;
         }
         __syncthreads();
     }
@@ -696,7 +728,7 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
             }
             do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos, ecur);
         }
-        if (counts) flush_warp_counts(A, cc);
+        if (counts) flush_warp_counts<PASS == PASS_FUSED>(A, cc);
     }
 
     // per-warp totals, one atomic per warp

@@ -5,12 +5,12 @@ namespace fsm {
 
 cudaError_t launch_extend_count(int L, const ExtArgs &A, int grid, cudaStream_t st) {
     switch (L) {
-    case 1: extend_kernel<1, PASS_COUNT><<<grid, 256, sizeof(CountCache), st>>>(A); break;
-    case 2: extend_kernel<2, PASS_COUNT><<<grid, 256, sizeof(CountCache), st>>>(A); break;
-    case 3: extend_kernel<3, PASS_COUNT><<<grid, 256, sizeof(CountCache), st>>>(A); break;
-    case 4: extend_kernel<4, PASS_COUNT><<<grid, 256, sizeof(CountCache), st>>>(A); break;
-    case 5: extend_kernel<5, PASS_COUNT><<<grid, 256, sizeof(CountCache), st>>>(A); break;
-    case 6: extend_kernel<6, PASS_COUNT><<<grid, 256, sizeof(CountCache), st>>>(A); break;
+    case 1: extend_kernel<1, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
+    case 2: extend_kernel<2, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
+    case 3: extend_kernel<3, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
+    case 4: extend_kernel<4, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
+    case 5: extend_kernel<5, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
+    case 6: extend_kernel<6, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -18,12 +18,12 @@ cudaError_t launch_extend_count(int L, const ExtArgs &A, int grid, cudaStream_t 
 
 cudaError_t occupancy_extend_count(int L, int *blocks_per_sm) {
     switch (L) {
-    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<1, PASS_COUNT>, 256, sizeof(CountCache));
-    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<2, PASS_COUNT>, 256, sizeof(CountCache));
-    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<3, PASS_COUNT>, 256, sizeof(CountCache));
-    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<4, PASS_COUNT>, 256, sizeof(CountCache));
-    case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<5, PASS_COUNT>, 256, sizeof(CountCache));
-    case 6: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<6, PASS_COUNT>, 256, sizeof(CountCache));
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<1, PASS_COUNT>, 256, FSM_COUNT_SMEM);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<2, PASS_COUNT>, 256, FSM_COUNT_SMEM);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<3, PASS_COUNT>, 256, FSM_COUNT_SMEM);
+    case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<4, PASS_COUNT>, 256, FSM_COUNT_SMEM);
+    case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<5, PASS_COUNT>, 256, FSM_COUNT_SMEM);
+    case 6: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<6, PASS_COUNT>, 256, FSM_COUNT_SMEM);
     default: return cudaErrorInvalidValue;
     }
 }
