@@ -77,7 +77,10 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                in a CUDA graph (falls back to 0 above 2^27 units); 2 = one launch per frontier
  *                pattern (the frontier grouped by pattern id), captured in one CUDA graph.  All
  *                modes give identical results.
- *   "autotune"   1 = on the first call per level, time the domain pass on an eighth of the
+ *   "group"      with launch 1: 1 = group the frontier by pattern id before each level (as
+ *                launch 2 does), 0 = keep emission order, 2 = group frontiers of size >= 3 and
+ *                keep the order of edges (default).  Results are identical.
+ *   "autotune"   1 = on the first call per level, time the domain pass on 1/32 of the
  *                frontier for chunk sizes 256, 1024, 4096, 16384 and keep the fastest for later
  *                passes and calls (reported as stat "chunk_l<l>"); 0 = forget tuned values.
  *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).

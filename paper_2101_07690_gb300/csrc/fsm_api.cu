@@ -118,6 +118,7 @@ struct fsm_graph {
     int sms = 0;
     int64_t qp_hint[FSM_MAXL + 1] = {};   // distinct quick patterns seen at each level last time
     int autotune = 0;
+    int group = 2;   // persistent launch: frontier grouped by pattern id first (1), never (0), from l = 3 (2)
     int fused = 0;
     unsigned long long pool_hint[FSM_MAXL + 1] = {};   // pool words the fused pass used last time
     unsigned long long pool_force = 0;                 // option "fused_pool": fixed pool size
@@ -337,9 +338,12 @@ struct Miner {
     // Frontier grouped by pattern id (launch mode 2): returns host offsets, P+1 entries.
     std::vector<int64_t> group_by_pattern(LevelSet &in) {
         std::vector<int64_t> off;
-        // per-pattern launches need the frontier grouped; the persistent launch keeps the emission
-        // order, whose consecutive units share key vertices (measured faster than grouping)
-        if (G->launch != 2 || in.N == 0 || in.P == 0) return off;
+        // Per-pattern launches need the frontier grouped.  The persistent launch groups it from
+        // size 3 on (option "group" = 2): consecutive units then share the pattern, so the count
+        // pass's warp tables hit (k = 5 on the 3.7M-vertex graph: count pass -12 %).  Edges keep
+        // emission order, whose consecutive units share key vertices (measured faster there).
+        const bool grouped = G->launch == 2 || (G->launch == 1 && (G->group == 1 || (G->group == 2 && in.L >= 3)));
+        if (!grouped || in.N == 0 || in.P == 0) return off;
         int64_t *cnt = mem.get<int64_t>(in.P);
         int64_t *doff = mem.get<int64_t>(in.P + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(in.P) + 16);
@@ -366,7 +370,7 @@ struct Miner {
     void tune_chunk(const LevelSet &in, ExtArgs A, int pass = PASS_DOMAIN) {
         const int L = in.L;
         if (!G->autotune || G->chunk > 0 || G->tuned_chunk[L] > 0 || in.N == 0) return;
-        const int64_t ne = std::min<int64_t>(in.N, std::max<int64_t>(1024, in.N / 8));
+        const int64_t ne = std::min<int64_t>(in.N, std::max<int64_t>(1024, in.N / 32));
         const int64_t nu = ne * L;
         int64_t *cnt = mem.get<int64_t>(nu);
         int64_t *base = mem.get<int64_t>(nu + 1);
@@ -1067,6 +1071,9 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
         } else if (k == "launch") {
             if (value < 0 || value > 2) fail(FSM_EINVAL, "launch must be 0, 1 or 2");
             g->launch = (int)value;
+        } else if (k == "group") {
+            if (value < 0 || value > 2) fail(FSM_EINVAL, "group must be 0, 1 or 2");
+            g->group = (int)value;
         } else if (k == "autotune") {
             if (value != 0 && value != 1) fail(FSM_EINVAL, "autotune must be 0 or 1");
             g->autotune = (int)value;

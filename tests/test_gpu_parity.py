@@ -108,7 +108,8 @@ def test_chunking_and_batching_do_not_change_results(fsm):
     g = gg.workload("cl100k", scale=0.005, cap=30)
     ref = check(fsm, g, 4, 6)
     for opts in ({"chunk": 32}, {"chunk": 65536}, {"batch": 1024}, {"batch": 1024, "chunk": 64},
-                 {"autotune": 1}, {"autotune": 1, "launch": 1}, {"fused": 0}, {"fused": 0, "launch": 2},
+                 {"autotune": 1}, {"autotune": 1, "launch": 1}, {"launch": 1, "group": 1},
+                 {"fused": 0}, {"fused": 0, "launch": 2},
                  {"fused_pool": 64}, {"fused_pool": 4096, "launch": 1}):
         G = fsm.Graph.from_graphgen(g)
         for key, val in opts.items():
@@ -200,6 +201,9 @@ def test_launch_modes_identical(fsm, launch):
         check(fsm, g, k, t, "edge", opts)
         check(fsm, g, k, t, "edge", dict(opts, batch=1024, chunk=64))
         check(fsm, g, k, t, "vertex", opts)
+        if launch == 1:
+            check(fsm, g, k, t, "edge", dict(opts, group=1))
+            check(fsm, g, k, t, "edge", dict(opts, group=0))
 
 
 def test_autotune_picks_a_candidate_and_keeps_results(fsm):
