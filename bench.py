@@ -162,6 +162,20 @@ def traffic_for(kernel_pass: str):
 
 # ----------------------------------------------------------------------------- our arm
 
+def replica_totals(total_ms: float, embeddings: int, world: int, device: str):
+    """Whole-job time and work of `world` independent replicas (one per GPU, no data-path
+    collective): the slowest rank's timed milliseconds and the embeddings of all ranks."""
+    if world <= 1:
+        return float(total_ms), float(embeddings)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor([float(embeddings)], device=device, dtype=torch.float64)
+    dist.all_reduce(e)
+    return float(t.item()), float(e.item())
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2101_07690_gb300 import build, fsm
@@ -213,17 +227,7 @@ def run_ours(args, rank, world, local_rank):
             agg = tot if agg is None else {k2: agg[k2] + tot[k2] for k2 in agg}
     torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = sum(times)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        e = torch.tensor([float(agg["embeddings"])], device="cuda", dtype=torch.float64)
-        dist.all_reduce(e)
-        emb_all = float(e.item())
-    else:
-        emb_all = float(agg["embeddings"])
+    total_ms, emb_all = replica_totals(sum(times), agg["embeddings"], world, "cuda")
     value = emb_all / (total_ms / 1e3)
 
     # end to end through the C ABI from pinned host buffers

@@ -178,8 +178,9 @@ int fsm_result_features(const fsm_result *r, float *features);
  *   whole call, CUDA events), "final_level_ns" (device time of the last level); with the
  *   "profile" option also, per extension pass P in {count, domain, emit}: "P_ns" (summed
  *   launch durations), "P_launches", "P_bytes" (algorithmic bytes: 4 * (d(v) + end pieces of v)
- *   per (embedding, key position) unit, 4 * (l + 1) per embedding read, and for emit
- *   4 * (l + 3) per embedding written), and the same per extended level size l as
+ *   per (embedding, key position) unit, 4 * (l + 1) per embedding read, for domain also
+ *   4 * (l + 2) per accepted join of a pattern given a domain (one bitmap word per position),
+ *   and for emit 4 * (l + 3) per embedding written), and the same per extended level size l as
  *   "P_ns_l<l>", "P_launches_l<l>", "P_bytes_l<l>" (l = 1..6); "chunk_l<l>" (autotuned chunk
  *   size of level l, 0 if none).  In launch modes 1 and 2 a pass's time covers its CUDA graph
  *   (the prefix-sum kernels included).

@@ -592,15 +592,13 @@ struct Miner {
         uint32_t *dom = mem.get<uint32_t>(nwords);
         ck(cudaMemsetAsync(dom, 0, sizeof(uint32_t) * std::max<int64_t>(nwords, 1), st), "memset");
         rs.patterns = np;
-        {
-            // live pattern count (for statistics)
-            std::vector<uint8_t> hl((size_t)np);
-            if (np) {
-                ck(cudaMemcpyAsync(hl.data(), live, (size_t)np, cudaMemcpyDeviceToHost, st), "copy");
-                ck(cudaStreamSynchronize(st), "sync");
-            }
-            rs.live = std::count(hl.begin(), hl.end(), (uint8_t)1);
+        // live pattern count (for statistics)
+        std::vector<uint8_t> hl((size_t)np);
+        if (np) {
+            ck(cudaMemcpyAsync(hl.data(), live, (size_t)np, cudaMemcpyDeviceToHost, st), "copy");
+            ck(cudaStreamSynchronize(st), "sync");
         }
+        rs.live = std::count(hl.begin(), hl.end(), (uint8_t)1);
         // ---- pass 2: MNI domains (Definition 2)
         A.qp.pattern = qpat;
         A.qp.perm = qperm;
@@ -619,6 +617,18 @@ struct Miner {
             } else {
                 tune_chunk(in, A);
                 run_pass(PASS_DOMAIN, in, A, pat_off);
+                if (G->profile) {
+                    // algorithmic bytes of the domain updates: one 4-byte bitmap word per position
+                    // of every accepted join of a live pattern (the list reads are in run_pass)
+                    std::vector<unsigned long long> hc((size_t)np);
+                    ck(cudaMemcpyAsync(hc.data(), pcount, sizeof(unsigned long long) * np, cudaMemcpyDeviceToHost, st),
+                       "copy");
+                    ck(cudaStreamSynchronize(st), "sync");
+                    int64_t joins = 0;
+                    for (int64_t P = 0; P < np; ++P)
+                        if (hl[(size_t)P]) joins += (int64_t)hc[(size_t)P];
+                    rs.pass_bytes[L][PASS_DOMAIN] += joins * 4 * K;
+                }
             }
         }
         if (pool) {
