@@ -503,10 +503,17 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             while ((int64_t)(y + 1) * y / 2 <= lq) ++y;
             xa = (int32_t)(lq - (int64_t)y * (y - 1) / 2);
         } else {
-            // l = 2, rows y >= cpos: cpos pairs each
+            // l = 2, rows y >= cpos: cpos pairs each (32-bit division when it fits: a 64-bit
+            // one is a long subroutine, and this runs once per pair)
             const int64_t r = lq - nt;
-            y = cpos + (int32_t)(r / cpos);
-            xa = (int32_t)(r % cpos);
+            if (r <= 0xffffffffll) {
+                const uint32_t r32 = (uint32_t)r, c32 = (uint32_t)cpos, qd = r32 / c32;
+                y = cpos + (int32_t)qd;
+                xa = (int32_t)(r32 - qd * c32);
+            } else {
+                y = cpos + (int32_t)(r / cpos);
+                xa = (int32_t)(r % cpos);
+            }
         }
         xb = y;
         a = __ldg(g.pcol + rp + xa);
