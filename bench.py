@@ -137,6 +137,51 @@ def oracle_sample(g, k: int, target_s: float):
             "seconds": dt, "embeddings": emb}
 
 
+def _oracle_worker(row_ptr, col, labels, k, roots, target_s, barrier, out):
+    """One process of the parallel oracle sample: calibrate, wait for the others, time."""
+    import types
+    sys.path.insert(0, ROOT)
+    import oracle
+    g = types.SimpleNamespace(row_ptr=row_ptr, col=col, labels=labels, n=len(row_ptr) - 1)
+    E = 5000
+    t0 = time.perf_counter()
+    oracle.mine(g, k, 1, roots=roots, max_embeddings=E)
+    rate = E / max(time.perf_counter() - t0, 1e-3)
+    E = max(E, int(rate * target_s))
+    barrier.wait()
+    t0 = time.perf_counter()
+    o = oracle.mine(g, k, 1, roots=roots, max_embeddings=E)
+    out.put((int(o["count"].sum()), time.perf_counter() - t0))
+
+
+def oracle_sample_parallel(g, k: int, target_s: float, workers: int | None = None):
+    """The oracle (as it stands) on every host core at once: worker j enumerates ESU from the
+    lowest ids of its own contiguous range of root vertices (the connected sets whose smallest
+    vertex lies there), stopped after about target_s seconds.  Throughput = all workers'
+    embeddings / the slowest worker's time, the workers started together."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    W = workers or len(os.sched_getaffinity(0))
+    ctx = mp.get_context("spawn")   # safe after the GPU is initialised
+    barrier, out = ctx.Barrier(W), ctx.Queue()
+    bounds = [g.n * j // W for j in range(W + 1)]
+    procs = [ctx.Process(target=_oracle_worker, args=(g.row_ptr, g.col, g.labels, k, (bounds[j], bounds[j + 1]),
+                                                      target_s, barrier, out)) for j in range(W)]
+    for pr in procs:
+        pr.start()
+    res = [out.get() for _ in range(W)]
+    for pr in procs:
+        pr.join()
+    emb = sum(r[0] for r in res)
+    dt = max(r[1] for r in res)
+    return {"value": emb / dt, "unit": "embeddings/s", "cores": W, "kind": "oracle",
+            "sample": f"{W} processes, one per host core, each ESU from the lowest vertex ids of its 1/{W} of "
+                      f"the root range of the same graph (edge-induced, every pattern), stopped after about "
+                      f"{target_s:.0f} s; {emb} connected {k}-vertex embeddings in {dt:.2f} s",
+            "seconds": dt, "embeddings": emb}
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -272,8 +317,10 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(g, args.k, args.cpu_seconds)
+        cpu = oracle_sample_parallel(g, args.k, args.cpu_seconds)
+        one = oracle_sample(g, args.k, args.cpu_seconds / 2)
         cpu = {k2: cpu[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
+        cpu["one_core"] = {"value": round(one["value"], 1), "sample": one["sample"]}
 
     G.close()
     if rank == 0:
@@ -301,7 +348,7 @@ def run_reference(args, rank, world):
         pass   # the oracle has no warm state worth priming beyond its first compile
     cfg = None
     for _ in range(args.steps):
-        s = oracle_sample(g, args.k, args.cpu_seconds / 2)
+        s = oracle_sample_parallel(g, args.k, args.cpu_seconds / 2)
         samples.append(s)
     value = sum(s["embeddings"] for s in samples) / sum(s["seconds"] for s in samples)
     ms = 1e3 * sum(s["seconds"] for s in samples) / len(samples)
@@ -310,8 +357,8 @@ def run_reference(args, rank, world):
             "value": round(value, 1), "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": dict(cfg, parallelism="cpu"),
-            "cpu_baseline": {"value": round(value, 1), "unit": "embeddings/s", "cores": 1, "kind": "oracle",
-                             "sample": samples[-1]["sample"]},
+            "cpu_baseline": {"value": round(value, 1), "unit": "embeddings/s", "cores": samples[-1]["cores"],
+                             "kind": "oracle", "sample": samples[-1]["sample"]},
             "e2e": {"value": round(value, 1), "unit": "embeddings/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
