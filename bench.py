@@ -356,7 +356,8 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": "embeddings extended per second (exact edge-induced FSM, MNI support)",
             "value": round(value, 1), "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": dict(cfg, parallelism="cpu"),
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": dict(cfg, parallelism=f"cpu{samples[-1]['cores']}", l2="not applicable (host cores)"),
             "cpu_baseline": {"value": round(value, 1), "unit": "embeddings/s", "cores": samples[-1]["cores"],
                              "kind": "oracle", "sample": samples[-1]["sample"]},
             "e2e": {"value": round(value, 1), "unit": "embeddings/s", "h2d_bytes_per_step": 0,
