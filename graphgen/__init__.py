@@ -245,7 +245,8 @@ def relabel_vertices(g: Graph, perm: np.ndarray) -> Graph:
 
 # ---------------------------------------------------------------- named workloads
 
-# Degree caps are recorded parameters of the Chung-Lu construction.
+# Degree caps are parameters of the Chung-Lu construction, given per call (``cap=``).  A cap
+# changes the mining work by orders of magnitude, so every measurement records the one it used.
 WORKLOADS = {
     # ER G(n=1000, avg degree 6), 4 uniform labels; k <= 3 at t = 30.
     "er1000": dict(family="er", n=1000, avg_degree=6.0, seed=0, num_labels=4, label_law="uniform"),
