@@ -74,7 +74,10 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *   "launch"     0 = one launch per frontier batch of at most "batch" embeddings, sized on
  *                the host (default); 1 = one persistent work-stealing launch per pass over the
  *                whole frontier, all sizes kept on the device, captured with its prefix kernels
- *                in a CUDA graph (falls back to 0 above 2^27 units); 2 = one launch per frontier
+ *                in a CUDA graph (its per-unit piece prefix takes 8 bytes per embedding and key
+ *                position; a frontier whose prefix would exceed a quarter of the free device
+ *                memory is split into the fewest equal ranges that fit, one launch each, in the
+ *                same graph); 2 = one launch per frontier
  *                pattern (the frontier grouped by pattern id), captured in one CUDA graph.  All
  *                modes give identical results.
  *   "group"      with launch 1: 1 = group the frontier by pattern id before each level (as
@@ -240,15 +243,19 @@ int fsm_debug_dissect(int32_t k, const int32_t *ids, const uint32_t *adj, uint32
  * that runs inside an allocator's own callback, or a process whose device memory is fully
  * reserved by another framework's pool.
  *   d_row_ptr, d_col, d_labels  DEVICE pointers to a CSR in the layout of fsm_load_graph
- *                              (validated on the device; malformed input gives FSM_EINVAL).
+ *                              (validated on the device before any other read: row_ptr[0]
+ *                              = 0, every row range inside [0, row_ptr[n]] and nondecreasing,
+ *                              rows sorted and symmetric, labels in range; malformed input
+ *                              gives FSM_EINVAL).  d_col must hold row_ptr[n] entries.
  *   n >= 1, 1 <= num_labels <= 64.
  *   d_support, d_count          DEVICE uint64[num_labels * num_labels] written by the call:
  *                              entry lo * num_labels + hi (lo <= hi) holds the MNI support and
  *                              the edge count of the pattern with labels (lo, hi); entries with
  *                              hi < lo are 0.  fsm_mine(k = 2) returns the same supports and
  *                              counts for the pairs whose support reaches its threshold.
- *   stream                      cudaStream_t to run on (NULL = the default stream); the call
- *                              synchronises it before returning.
+ *   stream                      cudaStream_t to run on (NULL = the default stream).  Every
+ *                              call copies row_ptr[n] and the validation flag back to the host
+ *                              and synchronises this stream, twice, before it returns.
  * Scratch: one static device array of 64 MiB, reserved when the library's device code is
  * loaded on a GPU and kept until the process exits; no cudaMalloc, cudaFree or allocating
  * library routine is called.  A graph whose scratch need, about 4 * (n + num_labels *

@@ -60,6 +60,13 @@ def _load():
             lib.oracle_result_copy_sampled.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64)]
             lib.oracle_dissect.restype = ctypes.c_uint32
             lib.oracle_dissect.argtypes = [ctypes.c_int32, P(ctypes.c_uint32)]
+            lib.oracle_dissect_join.restype = ctypes.c_uint32
+            lib.oracle_dissect_join.argtypes = [ctypes.c_int32, P(ctypes.c_uint32), P(ctypes.c_int32)]
+            lib.oracle_edge_kept.restype = ctypes.c_int
+            lib.oracle_edge_kept.argtypes = [ctypes.c_uint64, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]
+            lib.oracle_kept.restype = ctypes.c_int
+            lib.oracle_kept.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_uint32), ctypes.c_uint64,
+                                        ctypes.c_double]
             lib.oracle_result_count.restype = ctypes.c_int64
             lib.oracle_result_count.argtypes = [ctypes.c_void_p]
             lib.oracle_result_copy.restype = None
@@ -159,3 +166,29 @@ def dissect(adj_rows) -> int:
 def pattern_edges(adj: int, k: int) -> list[tuple[int, int]]:
     """Canonical edge list (i < j) of an ``adj`` word."""
     return [(i, j) for i in range(k) for j in range(i + 1, k) if (int(adj) >> (i * k + j)) & 1]
+
+
+def dissect_join(adj_rows) -> tuple[int, int]:
+    """(3-vertex part as a bit mask, join vertex) of the dissection of a connected graph whose
+    positions are its vertex ids; (0, -1) when none exists."""
+    rows = np.ascontiguousarray(adj_rows, dtype=np.uint32)
+    j = ctypes.c_int32()
+    m = int(_load().oracle_dissect_join(len(rows), _ptr(rows, ctypes.c_uint32), ctypes.byref(j)))
+    return m, int(j.value)
+
+
+def edge_kept(seed: int, p: float, x: int, y: int) -> bool:
+    """Sampled mining's rule for one directed edge x -> y at rate p (kept at rate sqrt(p))."""
+    return bool(_load().oracle_edge_kept(int(seed) & ((1 << 64) - 1), float(p), int(x), int(y)))
+
+
+def kept(u, adj_rows, seed: int, p: float) -> bool:
+    """Whether sampled mining at rate p keeps the embedding with ascending vertex ids u and
+    adjacency rows over positions (k >= 3)."""
+    uu = np.ascontiguousarray(u, dtype=np.int32)
+    rows = np.ascontiguousarray(adj_rows, dtype=np.uint32)
+    r = _load().oracle_kept(len(uu), _ptr(uu, ctypes.c_int32), _ptr(rows, ctypes.c_uint32),
+                            int(seed) & ((1 << 64) - 1), float(p))
+    if r < 0:
+        raise ValueError("kept needs 3 <= k <= 8")
+    return bool(r)

@@ -720,3 +720,35 @@ uint32_t oracle_dissect(int32_t k, const uint32_t *adjrow) {
     if (k < 3 || k > OR_MAXK) return 0;
     return dissect_three(k, adjrow);
 }
+
+/* Test hooks (the pins call these directly):
+ *   oracle_dissect_join  the dissection of a connected graph on positions 0..k-1 (positions are
+ *                        the ids): 3-vertex part as a mask, its join vertex in *join;
+ *   oracle_edge_kept     the sampling rule of one directed edge x -> y at rate p (kept at rate
+ *                        sqrt(p), so a 3-vertex part made of two kept edges survives at rate p);
+ *   oracle_kept          whether an embedding (vertex ids u[0..k) ascending, adjacency rows
+ *                        over positions) is kept by sampled mining at rate p. */
+uint32_t oracle_dissect_join(int32_t k, const uint32_t *adjrow, int32_t *join) {
+    int j = -1;
+    uint32_t l = (k >= 3 && k <= OR_MAXK) ? dissect_three_join(k, adjrow, &j) : 0;
+    *join = j;
+    return l;
+}
+
+int oracle_edge_kept(uint64_t seed, double p, int32_t x, int32_t y) {
+    oracle_t o;
+    memset(&o, 0, sizeof(o));
+    o.seed = seed;
+    o.thr = (uint64_t)(sqrt(p) * 18446744073709551616.0);
+    return edge_kept(&o, x, y);
+}
+
+int oracle_kept(int32_t k, const int32_t *u, const uint32_t *adjrow, uint64_t seed, double p) {
+    if (k < 3 || k > OR_MAXK) return -1;
+    oracle_t o;
+    memset(&o, 0, sizeof(o));
+    o.k = k;
+    o.seed = seed;
+    o.thr = (uint64_t)(sqrt(p) * 18446744073709551616.0);
+    return kept(&o, u, adjrow);
+}

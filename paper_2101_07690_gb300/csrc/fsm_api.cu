@@ -100,6 +100,36 @@ T d2h(const T *dptr, cudaStream_t st) {
     return v;
 }
 
+// A CUDA graph captured from a stream.  If an exception leaves the capture open, the
+// destructor ends it (so the stream leaves capture mode and later calls see the original error,
+// not capture errors) and destroys whatever was captured or instantiated.
+struct CapturedGraph {
+    cudaStream_t st;
+    bool capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    explicit CapturedGraph(cudaStream_t s) : st(s) {}
+    void begin() {
+        ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+        capturing = true;
+    }
+    void end() {
+        capturing = false;
+        ck(cudaStreamEndCapture(st, &graph), "end capture");
+        ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+    }
+    ~CapturedGraph() {
+        if (capturing) {
+            cudaGraph_t partial = nullptr;
+            cudaStreamEndCapture(st, &partial);
+            if (partial) cudaGraphDestroy(partial);
+            cudaGetLastError();
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+};
+
 } // namespace
 
 namespace fsm {
@@ -226,7 +256,10 @@ struct Miner {
     // Run one pass of the extension kernel over the frontier.
     //   launch 0: batches of at most `batch` embeddings, each sized on the host;
     //   launch 1: one persistent work-stealing launch over the whole frontier (sizes stay on the
-    //             device), captured with its prefix kernels into a CUDA graph;
+    //             device), captured with its prefix kernels into a CUDA graph.  The per-unit piece
+    //             prefix takes 8 bytes per (embedding, key position); only when a quarter of the
+    //             free device memory cannot hold it is the frontier split into the fewest equal
+    //             ranges that fit, each one launch of the same graph;
     //   launch 2: one launch per frontier pattern (the frontier grouped by pattern id), all
     //             captured into one CUDA graph.
     void run_pass(int pass, const LevelSet &in, ExtArgs A, const std::vector<int64_t> &pat_off) {
@@ -240,8 +273,13 @@ struct Miner {
                 for (int64_t e0 = pat_off[p]; e0 < pat_off[p + 1]; e0 += B)
                     ranges.push_back({e0, std::min(B, pat_off[p + 1] - e0)});
             device_total = true;
-        } else if (G->launch == 1 && in.N * L <= ((int64_t)1 << 27)) {
-            ranges.push_back({0, in.N});
+        } else if (G->launch == 1) {
+            size_t fr = 0, tot = 0;
+            ck(cudaMemGetInfo(&fr, &tot), "memory info");
+            const int64_t fit = std::max<int64_t>(1 << 20, (int64_t)(fr / 4 / sizeof(int64_t)) / L);   // embeddings
+            const int64_t parts = (in.N + fit - 1) / fit;
+            const int64_t per = (in.N + parts - 1) / parts;
+            for (int64_t e0 = 0; e0 < in.N; e0 += per) ranges.push_back({e0, std::min(per, in.N - e0)});
             device_total = true;
         } else {
             for (int64_t e0 = 0; e0 < in.N; e0 += B) ranges.push_back({e0, std::min(B, in.N - e0)});
@@ -249,7 +287,7 @@ struct Miner {
         int64_t maxne = 0;
         for (auto &r : ranges) maxne = std::max(maxne, r.ne);
         const int64_t maxu = maxne * L;
-        int64_t *cnt = mem.get<int64_t>(maxu);
+        // per-unit piece counts, then their exclusive prefix in place (one extra entry: the total)
         int64_t *base = mem.get<int64_t>(maxu + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(maxu) + 16);
         unsigned long long *ctr = mem.get<unsigned long long>(1);
@@ -282,12 +320,11 @@ struct Miner {
             return prof_ev.size() - 1;
         };
         if (device_total) {
-            cudaGraph_t graph = nullptr;
-            cudaGraphExec_t exec = nullptr;
-            ck(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+            CapturedGraph cg(st);
+            cg.begin();
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
-                ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, base, st), "unit counts");
+                ck(launch_scan_i64(base, base, r.ne * L, tmp, st), "unit scan");
                 bytes(r);
                 ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
                 A.e0 = r.e0;
@@ -297,18 +334,15 @@ struct Miner {
                 A.chunk = chunk_for(L);
                 launch_ext();
             }
-            ck(cudaStreamEndCapture(st, &graph), "end capture");
-            ck(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate");
+            cg.end();
             size_t ei = prof ? new_ev() : 0;
             if (prof) ck(cudaEventRecord(prof_ev[ei].a, st), "event record");
-            ck(cudaGraphLaunch(exec, st), "graph launch");
+            ck(cudaGraphLaunch(cg.exec, st), "graph launch");
             if (prof) ck(cudaEventRecord(prof_ev[ei].b, st), "event record");
-            ck(cudaGraphExecDestroy(exec), "graph destroy");
-            ck(cudaGraphDestroy(graph), "graph destroy");
         } else {
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, cnt, st), "unit counts");
-                ck(launch_scan_i64(cnt, base, r.ne * L, tmp, st), "unit scan");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, base, st), "unit counts");
+                ck(launch_scan_i64(base, base, r.ne * L, tmp, st), "unit scan");
                 const int64_t total = d2h(base + r.ne * L, st);
                 if (total == 0) continue;
                 bytes(r);
@@ -329,7 +363,6 @@ struct Miner {
                 if (prof) ck(cudaEventRecord(prof_ev[ei].b, st), "event record");
             }
         }
-        mem.release(cnt);
         mem.release(base);
         mem.release(tmp);
         mem.release(ctr);

@@ -33,18 +33,21 @@ __global__ void validate_kernel(DevGraph g, int32_t num_labels, int *err) {
     for (int64_t v = gtid(); v < g.n; v += gstride()) {
         const int32_t rb = g.row_ptr[v], re = g.row_ptr[v + 1];
         const int32_t lab = g.labels[v];
-        bool bad = rb > re || rb < 0 || (int64_t)re > g.nnz || lab < 0 || lab >= num_labels;
+        bool bad = rb > re || rb < 0 || (int64_t)re > g.nnz || lab < 0 || lab >= num_labels || (v == 0 && rb != 0);
         if (!bad) {
             for (int32_t j = rb; j < re && !bad; ++j) {
                 const int32_t w = g.col[j];
                 if (w < 0 || w >= g.n || w == (int32_t)v || (j > rb && g.col[j - 1] >= w)) { bad = true; break; }
+                // w's row is searched below: its bounds must be sane before any col read
+                const int32_t wb = g.row_ptr[w], we = g.row_ptr[w + 1];
+                if (wb < 0 || wb > we || (int64_t)we > g.nnz) { bad = true; break; }
                 // symmetry: v must appear in N(w)
-                int32_t lo = g.row_ptr[w], hi = g.row_ptr[w + 1];
+                int32_t lo = wb, hi = we;
                 while (lo < hi) {
                     const int32_t mid = (lo + hi) >> 1;
                     if (g.col[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
                 }
-                if (lo >= g.row_ptr[w + 1] || g.col[lo] != (int32_t)v) bad = true;
+                if (lo >= we || g.col[lo] != (int32_t)v) bad = true;
             }
         }
         if (bad) atomicOr(err, FSM_ERR_CSR);

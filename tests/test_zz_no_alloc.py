@@ -77,3 +77,34 @@ def test_noalloc_rejects_graphs_beyond_its_scratch(env):
         fsm.fsm_edge_supports_noalloc(1, 1, 1, 2 ** 30, 64, 1, 1, 0)
     assert e.value.code == fsm.FSM_EUNSUPPORTED
     assert "static array" in str(e.value)
+
+
+# Malformed row_ptr arrays (path 0-1-2-3, nnz = 6) that the device validation must reject
+# before reading outside col: a row that ends before it starts, a row that ends past nnz, a
+# row that starts below zero, and a first row that does not start at 0.
+BAD_ROW_PTRS = {
+    "decreasing": [0, 4, 3, 5, 6],
+    "past_nnz": [0, 1, 9, 5, 6],
+    "negative": [0, -1, 3, 5, 6],
+    "first_not_zero": [1, 1, 3, 5, 6],
+}
+
+
+@pytest.mark.parametrize("name", list(BAD_ROW_PTRS))
+def test_noalloc_rejects_malformed_row_ptr(env, name):
+    fsm, torch = env
+    dev = torch.device("cuda")
+    rp = torch.tensor(BAD_ROW_PTRS[name], dtype=torch.int32, device=dev)
+    col = torch.tensor([1, 0, 2, 1, 3, 2], dtype=torch.int32, device=dev)
+    lab = torch.zeros(4, dtype=torch.int32, device=dev)
+    sup = torch.zeros(1, dtype=torch.int64, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    with pytest.raises(fsm.FsmError) as e:
+        fsm.fsm_edge_supports_noalloc(rp.data_ptr(), col.data_ptr(), lab.data_ptr(), 4, 1, sup.data_ptr(),
+                                      cnt.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert e.value.code == fsm.FSM_EINVAL
+    # the context is still usable: a valid call on the same path graph succeeds afterwards
+    rp_ok = torch.tensor([0, 1, 3, 5, 6], dtype=torch.int32, device=dev)
+    fsm.fsm_edge_supports_noalloc(rp_ok.data_ptr(), col.data_ptr(), lab.data_ptr(), 4, 1, sup.data_ptr(),
+                                  cnt.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert int(sup.item()) == 4 and int(cnt.item()) == 3
