@@ -1,16 +1,19 @@
 #!/usr/bin/env python
 """Benchmark: exact frequent subgraph mining (two-vertex exploration) on one GB300.
 
-Workload (default): Chung-Lu power-law graph, 100k vertices, 1.1M undirected edges, degree
-exponent 2.1, 29 vertex labels drawn Zipf(s=1.2), int32 CSR, seed 1 (MiCo-shaped, synthetic);
-exact edge-induced FSM of size k=4 under MNI support at thresholds 300, 1000 and 3000.
-One step = the three fsm_mine calls on the resident graph.
+Workload (default): Chung-Lu power-law graph, 3.7M vertices, 16.5M undirected edges, degree
+exponent 2.3, 37 vertex labels drawn Zipf(s=1.0), int32 CSR, seed 2, expected-degree cap 20
+(a recorded parameter: the mining work grows by orders of magnitude with it); exact
+edge-induced FSM of size k=5 under MNI support at threshold 20000.  One step = one fsm_mine
+call on the resident graph (levels 1 -> 3 -> 5).
 
 Printed (rank 0, one JSON line): value = embeddings extended per second over the whole job
 (accepted joins of every level / device time), e2e = the same metric through the C ABI from
 host buffers (graph upload, mining, result download inside the timed region), roofline of the
-dominant extension-kernel pass, the CPU oracle on a bounded sample, clocks during the timed
-region.  ``--impl reference`` times the CPU oracle alone on the same workload.
+dominant extension-kernel pass, the persistent launch against one launch per pattern on the
+same graph, the CPU oracle on a bounded sample and its time to solution on a small graph of the
+same family, clocks during the timed region.  ``--impl reference`` times the CPU oracle alone
+on the same workload.
 """
 from __future__ import annotations
 
@@ -36,11 +39,15 @@ def parse_args():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="cl100k")
-    p.add_argument("--k", type=int, default=4)
-    p.add_argument("--thresholds", default="300,1000,3000")
-    p.add_argument("--cap", type=float, default=300.0,
-                   help="Chung-Lu expected-degree cap (default 300; 0 = the structural cutoff sqrt(2m))")
+    p.add_argument("--workload", default="cl3700k")
+    p.add_argument("--k", type=int, default=5)
+    p.add_argument("--thresholds", default="20000")
+    p.add_argument("--cap", type=float, default=20.0,
+                   help="Chung-Lu expected-degree cap (default 20; 0 = the structural cutoff sqrt(2m))")
+    p.add_argument("--e2e-steps", type=int, default=2, help="end-to-end iterations (graph upload included)")
+    p.add_argument("--no-compare-launch", action="store_true",
+                   help="skip the one-launch-per-pattern comparison mine")
+    p.add_argument("--no-tts", action="store_true", help="skip the oracle's time to solution on a small graph")
     p.add_argument("--mode", choices=["edge", "vertex"], default="edge")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -205,6 +212,33 @@ def traffic_for(kernel_pass: str):
     return ent.get("dram_bytes_per_full_launch")
 
 
+def issue_roof(dom, ns: float, nl: int, pieces: int):
+    """Second roof of the dominant pass, which does its work in L1/L2 rather than HBM: warp
+    instructions issued per second against the issue peak of 152 SMs x 4 schedulers x one warp
+    instruction per cycle at the maximum SM clock (MEASURED_PEAKS.json, else 2070 MHz).  The
+    instructions per enumerated piece come from one ncu capture of the same kernel and pass on
+    a scaled graph (profiles/extend_issue.json), valid only for the source it was taken on."""
+    path = os.path.join(ROOT, "profiles", "extend_issue.json")
+    if not os.path.exists(path) or nl == 0 or ns <= 0 or pieces <= 0:
+        return None
+    d = json.load(open(path))
+    src = os.path.join(ROOT, "paper_2101_07690_gb300", "csrc", "fsm_extend.cuh")
+    if d.get("source_sha") != hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]:
+        return None
+    ent = d.get(f"{dom[0]}_l{dom[1]}")
+    if not ent:
+        return None
+    mhz = 2070.0
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        mhz = float(json.load(open(pk)).get("sm_max_mhz", mhz))
+    peak = 152 * 4 * mhz * 1e6
+    achieved = ent["warp_inst_per_piece"] * (pieces / nl) / (ns / nl * 1e-9)
+    return {"bound": "issue", "achieved": round(achieved / 1e12, 4), "peak": round(peak / 1e12, 4),
+            "unit": "warp Tinst/s", "frac": round(achieved / peak, 4),
+            "warp_inst_per_piece": ent["warp_inst_per_piece"], "from": ent.get("capture")}
+
+
 # ----------------------------------------------------------------------------- our arm
 
 def replica_totals(total_ms: float, embeddings: int, world: int, device: str):
@@ -221,7 +255,34 @@ def replica_totals(total_ms: float, embeddings: int, world: int, device: str):
     return float(t.item()), float(e.item())
 
 
+def time_to_solution(args, fsm):
+    """The oracle (as it stands, one host core) and the GPU library solving the same whole
+    problem on a small graph of the workload's family (1/10000 of its vertices and edges, the
+    threshold scaled alike), with the outputs compared bit for bit."""
+    import graphgen as gg
+    import numpy as np
+    import oracle
+    oracle.build()
+    scale = 1e-4
+    g = gg.workload(args.workload, scale=scale, cap=args.cap if args.cap else None)
+    t = max(2, int(round(int(args.thresholds.split(",")[0]) * scale)))
+    t0 = time.perf_counter()
+    o = oracle.mine(g, args.k, t, args.mode)
+    o_s = time.perf_counter() - t0
+    G = fsm.Graph.from_graphgen(g, args.mode)
+    G.mine(args.k, t)   # first call: lazy set-up
+    t0 = time.perf_counter()
+    r = G.mine(args.k, t)
+    g_s = time.perf_counter() - t0
+    G.close()
+    same = all(np.array_equal(r[key], o[key]) for key in ("labels", "adj", "support", "count"))
+    return {"graph": f"{args.workload} at scale {scale}: n={g.n} m={g.m} d_max={int(g.degrees().max())}",
+            "k": args.k, "threshold": t, "patterns": int(len(o["support"])), "oracle_s": round(o_s, 3),
+            "oracle_cores": 1, "gpu_s": round(g_s, 4), "identical": bool(same)}
+
+
 def run_ours(args, rank, world, local_rank):
+    import numpy as np
     import torch
     from paper_2101_07690_gb300 import build, fsm
 
@@ -236,14 +297,17 @@ def run_ours(args, rank, world, local_rank):
     G.set_option("launch", args.launch)
     G.set_option("autotune", args.autotune)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
+    last = {}
 
     def step(profile: bool):
         G.set_option("profile", 1 if profile else 0)
         tot = {"embeddings": 0, "kernel_launches": 0, "patterns_out": 0, "final_embeddings": 0}
         tot.update({f"{p}_{f}_l{l}": 0 for p in ("count", "domain", "emit", "fused") for f in ("ns", "launches", "bytes")
                     for l in range(1, 7)})
+        tot.update({f"pieces_l{l}": 0 for l in range(1, 7)})
         for t in ths:
             r = G.mine(args.k, t, stats=True)
+            last[t] = r
             s = r["stats"]
             for key in tot:
                 if key in s:
@@ -275,6 +339,24 @@ def run_ours(args, rank, world, local_rank):
     total_ms, emb_all = replica_totals(sum(times), agg["embeddings"], world, "cuda")
     value = emb_all / (total_ms / 1e3)
 
+    # the same mining with one launch per frontier pattern (option launch = 2), untimed by the
+    # step clock: its device time and launches against the timed steps, and its output
+    launch_cmp = None
+    if not args.no_compare_launch and args.launch != 2:
+        G.set_option("profile", 0)
+        G.set_option("launch", 2)
+        with torch.cuda.stream(stream):
+            pp = {t: G.mine(args.k, t, stats=True) for t in ths}
+        G.set_option("launch", args.launch)
+        same = all(np.array_equal(pp[t][key], last[t][key]) for t in ths for key in ("labels", "adj", "support", "count"))
+        launch_cmp = {"launch": {0: "batched", 1: "persistent"}[args.launch],
+                      "ms_per_step": round(total_ms / args.steps, 3),
+                      "extension_launches_per_step": int(sum(agg[f"{p}_launches_l{l}"] for p in ("count", "domain", "emit", "fused")
+                                                             for l in range(1, 7)) // args.steps),
+                      "per_pattern_ms_per_step": round(sum(pp[t]["stats"]["time_ns"] for t in ths) / 1e6, 3),
+                      "per_pattern_kernel_launches": int(sum(pp[t]["stats"]["kernel_launches"] for t in ths)),
+                      "identical": bool(same)}
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -283,7 +365,8 @@ def run_ours(args, rank, world, local_rank):
         lb = torch.from_numpy(g.labels).pin_memory()
         h2d = (rp.numel() + cl.numel() + lb.numel()) * 4
         d2h, emb_e2e, t_e2e = 0, 0, 0.0
-        for it in range(args.steps):
+        n_e2e = max(1, args.e2e_steps)
+        for it in range(n_e2e):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = fsm.fsm_load_graph(rp.data_ptr(), cl.data_ptr(), lb.data_ptr(), g.n, g.num_labels)
@@ -298,7 +381,7 @@ def run_ours(args, rank, world, local_rank):
             fsm.fsm_free_graph(h)
             t_e2e += time.perf_counter() - t0
         e2e = {"value": emb_e2e / t_e2e, "unit": "embeddings/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h // args.steps, "ms_per_step": 1e3 * t_e2e / args.steps}
+               "d2h_bytes_per_step": d2h // n_e2e, "ms_per_step": 1e3 * t_e2e / n_e2e, "steps": n_e2e}
 
     # roofline of the dominant extension pass (launch durations from CUDA events in the library)
     passes = {(p, l): (agg[f"{p}_ns_l{l}"], agg[f"{p}_bytes_l{l}"], agg[f"{p}_launches_l{l}"])
@@ -309,18 +392,23 @@ def run_ours(args, rank, world, local_rank):
     achieved = (byts / nl) / (ns / nl) if ns > 0 and nl > 0 else 0.0   # bytes per ns == GB/s
     roofline = {"bound": "hbm", "kernel": f"extend_kernel<{dom[1]}, PASS_{dom[0].upper()}>",
                 "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                "frac": round(achieved / peak, 5), "peak_source": f"{peak_kind} hbm_gbs",
                 "traffic": traffic_for(f"{dom[0]}_l{dom[1]}"), "launches": nl, "avg_launch_ms": round(ns / nl / 1e6, 3) if nl else None,
                 "algorithmic_bytes_per_launch": byts / nl if nl else None,
                 "share_of_step": round(ns / 1e6 / total_ms, 3) if total_ms else None,
                 "pass_ms": {f"{p}_l{l}": round(v[0] / 1e6 / args.steps, 2) for (p, l), v in passes.items() if v[2]}}
+    issue = issue_roof(dom, ns, nl, agg.get(f"pieces_l{dom[1]}", 0))
+    if issue:
+        roofline["issue_roof"] = issue
 
-    cpu = None
+    cpu = tts = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = oracle_sample_parallel(g, args.k, args.cpu_seconds)
         one = oracle_sample(g, args.k, args.cpu_seconds / 2)
         cpu = {k2: cpu[k2] for k2 in ("value", "unit", "cores", "kind", "sample")}
         cpu["one_core"] = {"value": round(one["value"], 1), "sample": one["sample"]}
+    if rank == 0 and world == 1 and not args.no_tts:
+        tts = time_to_solution(args, fsm)
 
     G.close()
     if rank == 0:
@@ -328,14 +416,15 @@ def run_ours(args, rank, world, local_rank):
                 "value": round(value, 1), "unit": "embeddings/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
-                "data": "synthetic (seeded Chung-Lu stand-in for the paper's MiCo graph)",
+                "data": "synthetic (seeded Chung-Lu graph of the named shape)",
                 "config": dict(workload_config(args, g), parallelism=f"replicas{world}",
                                launch={0: "batched", 1: "persistent", 2: "per-pattern"}[args.launch],
                                autotune=bool(args.autotune)),
                 "e2e": e2e, "gpu_launches": int(agg["kernel_launches"]),
                 "embeddings_per_step": int(agg["embeddings"] // args.steps),
                 "patterns_per_step": int(agg["patterns_out"] // args.steps),
-                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk}
+                "roofline": roofline, "launch_compare": launch_cmp, "cpu_baseline": cpu,
+                "time_to_solution": tts, "clocks": clk}
         print(json.dumps(line), flush=True)
 
 

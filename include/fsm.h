@@ -88,6 +88,10 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                passes and calls (reported as stat "chunk_l<l>"); 0 = forget tuned values.
  *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
  *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
+ *   "qp_capacity" slots of the first quick-pattern hash table of every level (power of two,
+ *                64..2^30; 0 = at least 2^20, sized from the previous call).  A table that fills
+ *                past half is grown x4 and its pass repeated (stat "qp_grows"); results are
+ *                identical.
  *   "fused"      1 = the last level counts quick patterns and fills MNI domains in one pass,
  *                into per-key bitmaps merged per pattern afterwards; 0 = a count pass then a
  *                domain pass (default: measured faster, as per-key bitmaps multiply the bit
@@ -172,9 +176,11 @@ int fsm_result_features(const fsm_result *r, float *features);
 
 /*
  * fsm_result_stat -- a run counter of the mining call that made r:
- *   "k", "levels", "pieces" (size-3 pieces enumerated by the count passes), "candidates" (joins
+ *   "k", "levels", "pieces" (size-3 pieces enumerated by the count passes; "pieces_l<l>" per
+ *   extended level size l = 1..6), "candidates" (joins
  *   tested), "embeddings" (accepted joins, all levels),
- *   "final_embeddings" (accepted joins of the last level), "quick_patterns" (distinct index
+ *   "final_embeddings" (accepted joins of the last level), "qp_grows" (quick-pattern table
+ *   overflows, each a grown table and a repeated pass), "quick_patterns" (distinct index
  *   based quick patterns, i.e. canonicalisations, all levels), "patterns" (distinct patterns
  *   of the last level), "live_patterns" (last-level patterns given a domain),
  *   "frontier_max" (largest stored level), "kernel_launches", "time_ns" (device time of the

@@ -58,6 +58,9 @@ def _load():
                                                                            ctypes.c_double]
             lib.oracle_result_copy_sampled.restype = None
             lib.oracle_result_copy_sampled.argtypes = [ctypes.c_void_p, P(ctypes.c_int64), P(ctypes.c_int64)]
+            lib.oracle_result_copy_sampled_domains.restype = None
+            lib.oracle_result_copy_sampled_domains.argtypes = [ctypes.c_void_p, P(ctypes.c_int64),
+                                                               P(ctypes.c_double)]
             lib.oracle_dissect.restype = ctypes.c_uint32
             lib.oracle_dissect.argtypes = [ctypes.c_int32, P(ctypes.c_uint32)]
             lib.oracle_dissect_join.restype = ctypes.c_uint32
@@ -101,7 +104,8 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
     edges are kept by a splitmix64 rule at rate sqrt(p), and an embedding is kept when the
     3-vertex part of its smallest-vertex-first dissection is made of kept edges as seen from
     the join vertex; ``ssupport`` and ``scount`` are the MNI support and embedding count over
-    kept embeddings.
+    kept embeddings, ``spop[P, c]`` the size of canonical position c's sampled image set and
+    ``sdeg[P, c]`` the sum of log(1 + degree) over it.
     Returns a dict of numpy arrays: labels (P, k) int32, adj (P,) uint64, support (P,) int64,
     count (P,) int64 (number of embeddings of each pattern)."""
     lib = _load()
@@ -127,9 +131,13 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
         if sample is not None:
             out["ssupport"] = np.zeros(npat, np.int64)
             out["scount"] = np.zeros(npat, np.int64)
+            out["spop"] = np.zeros((npat, k), np.int64)
+            out["sdeg"] = np.zeros((npat, k), np.float64)
             if npat:
                 lib.oracle_result_copy_sampled(res, _ptr(out["ssupport"], ctypes.c_int64),
                                                _ptr(out["scount"], ctypes.c_int64))
+                lib.oracle_result_copy_sampled_domains(res, _ptr(out["spop"], ctypes.c_int64),
+                                                       _ptr(out["sdeg"], ctypes.c_double))
     finally:
         lib.oracle_free(res)
     return out

@@ -456,6 +456,8 @@ typedef struct {
     uint64_t *adj;       /* bit (i*k + j) set for canonical edge i < j */
     int64_t *support, *count;
     int64_t *ssupport, *scount;   /* sampled mode: min_c |sampled images|, kept embeddings */
+    int64_t *spop;                /* sampled mode: |sampled images of position c|, npat x k */
+    double *sdeg;                 /* sampled mode: sum of log(1 + degree) over those images, npat x k */
 } oracle_result_t;
 
 static int code_sort_k;
@@ -540,6 +542,8 @@ oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const in
     r->count = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     r->ssupport = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     r->scount = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
+    r->spop = (int64_t *)calloc((size_t)(nk * k + 1), sizeof(int64_t));
+    r->sdeg = (double *)calloc((size_t)(nk * k + 1), sizeof(double));
     for (int64_t q = 0; q < nk; q++) {
         const pattern_t *p = &o.pat[keep[q]];
         int64_t sigma = -1;
@@ -564,6 +568,14 @@ oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const in
         }
         r->ssupport[q] = p->scount ? ss : 0;
         r->scount[q] = p->scount;
+        for (int c = 0; c < k; c++) {
+            const vset_t *d = &p->sdom[c];
+            r->spop[q * k + c] = d->size;
+            double sd = 0.0;
+            for (int64_t x = 0; x < d->cap; x++)
+                if (d->slot[x] >= 0) sd += log1p((double)(row_ptr[d->slot[x] + 1] - row_ptr[d->slot[x]]));
+            r->sdeg[q * k + c] = sd;
+        }
     }
     free(keep);
     for (int64_t p = 0; p < o.npat; p++)
@@ -589,9 +601,18 @@ void oracle_result_copy_sampled(const oracle_result_t *r, int64_t *ssupport, int
     memcpy(scount, r->scount, sizeof(int64_t) * (size_t)r->npat);
 }
 
+/* sampled mode: per pattern and canonical position, the size of the sampled image set and the
+ * sum of log(1 + degree) over it (both npat x k, row-major) */
+void oracle_result_copy_sampled_domains(const oracle_result_t *r, int64_t *spop, double *sdeg) {
+    if (!r) return;
+    memcpy(spop, r->spop, sizeof(int64_t) * (size_t)(r->npat * r->k));
+    memcpy(sdeg, r->sdeg, sizeof(double) * (size_t)(r->npat * r->k));
+}
+
 void oracle_free(oracle_result_t *r) {
     if (!r) return;
-    free(r->labels); free(r->adj); free(r->support); free(r->count); free(r->ssupport); free(r->scount); free(r);
+    free(r->labels); free(r->adj); free(r->support); free(r->count); free(r->ssupport); free(r->scount);
+    free(r->spop); free(r->sdeg); free(r);
 }
 
 /* ------------------------------------------------------------------ one pattern at a time */

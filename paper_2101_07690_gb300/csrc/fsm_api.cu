@@ -147,6 +147,9 @@ struct fsm_graph {
     int64_t batch = 0;
     int sms = 0;
     int64_t qp_hint[FSM_MAXL + 1] = {};   // distinct quick patterns seen at each level last time
+    int64_t qp_initial = 0;               // option "qp_capacity": first quick-pattern table size (0 = 2^20)
+    int explore = 0;                      // option "explore": 0 two-vertex (the method), 1 single-vertex
+    int quick_pattern = 0;                // option "quick_pattern": 0 index-based, 1 edge list
     int autotune = 0;
     int group = 2;   // persistent launch: frontier grouped by pattern id first (1), never (0), from l = 3 (2)
     int fused = 0;
@@ -216,6 +219,8 @@ struct RunStats {
             final_accepted = 0, launches = 0;
     // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
     int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0, sampled_edges = 0;
+    int64_t qp_grows = 0;                  // quick-pattern table overflows (table grown x4, pass repeated)
+    int64_t pieces_l[FSM_MAXL + 1] = {};   // pieces enumerated by the count pass, per extended level size
     double pass_ns[FSM_MAXL + 1][4] = {};
     int64_t pass_launches[FSM_MAXL + 1][4] = {}, pass_bytes[FSM_MAXL + 1][4] = {};
 };
@@ -226,13 +231,14 @@ struct Miner {
     Arena &mem;
     int64_t t;
     RunStats &rs;
+    int V = FSM_EXPLORE_TV;   // exploration variant of this call (FSM_EXPLORE_*)
 
     int grid_for(int L, int pass) {
         int bps = 0;
-        cudaError_t e = pass == PASS_COUNT ? occupancy_extend_count(L, &bps)
-                      : pass == PASS_DOMAIN ? occupancy_extend_domain(L, &bps)
+        cudaError_t e = pass == PASS_COUNT ? occupancy_extend_count(L, V, &bps)
+                      : pass == PASS_DOMAIN ? occupancy_extend_domain(L, V, &bps)
                       : pass == PASS_FUSED ? occupancy_extend_fused(L, &bps)
-                                            : occupancy_extend_emit(L, &bps);
+                                            : occupancy_extend_emit(L, V, &bps);
         ck(e, "occupancy query");
         if (bps < 1) bps = 1;
         return G->sms * bps;
@@ -300,16 +306,16 @@ struct Miner {
         A.unit_base = base;
         A.chunk_ctr = ctr;
         auto launch_ext = [&]() {
-            cudaError_t e = pass == PASS_COUNT ? launch_extend_count(L, A, grid, st)
-                          : pass == PASS_DOMAIN ? launch_extend_domain(L, A, grid, st)
+            cudaError_t e = pass == PASS_COUNT ? launch_extend_count(L, V, A, grid, st)
+                          : pass == PASS_DOMAIN ? launch_extend_domain(L, V, A, grid, st)
                           : pass == PASS_FUSED ? launch_extend_fused(L, A, grid, st)
-                                                : launch_extend_emit(L, A, grid, st);
+                                                : launch_extend_emit(L, V, A, grid, st);
             ck(e, "extension kernel");
             rs.launches += 1;
             rs.pass_launches[L][pass] += 1;
         };
         auto bytes = [&](const Range &r) {
-            if (prof) ck(launch_unit_bytes(A.g.prow, A.g.ppc, in.fv, in.N, r.e0, r.ne, L,
+            if (prof) ck(launch_unit_bytes(A.g.prow, A.g.ppc, in.fv, in.N, r.e0, r.ne, L, V,
                                            prof_bytes + L * 4 + pass, st), "unit bytes");
         };
         auto new_ev = [&]() {
@@ -323,7 +329,7 @@ struct Miner {
             CapturedGraph cg(st);
             cg.begin();
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, base, st), "unit counts");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, V, base, st), "unit counts");
                 ck(launch_scan_i64(base, base, r.ne * L, tmp, st), "unit scan");
                 bytes(r);
                 ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
@@ -341,7 +347,7 @@ struct Miner {
             if (prof) ck(cudaEventRecord(prof_ev[ei].b, st), "event record");
         } else {
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, base, st), "unit counts");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, V, base, st), "unit counts");
                 ck(launch_scan_i64(base, base, r.ne * L, tmp, st), "unit scan");
                 const int64_t total = d2h(base + r.ne * L, st);
                 if (total == 0) continue;
@@ -409,7 +415,7 @@ struct Miner {
         int64_t *base = mem.get<int64_t>(nu + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(nu) + 16);
         unsigned long long *ctr = mem.get<unsigned long long>(1);
-        ck(launch_unit_counts(A.g, in.fv, in.N, 0, ne, L, cnt, st), "unit counts");
+        ck(launch_unit_counts(A.g, in.fv, in.N, 0, ne, L, V, cnt, st), "unit counts");
         ck(launch_scan_i64(cnt, base, nu, tmp, st), "unit scan");
         const int64_t total = d2h(base + nu, st);
         const int grid = grid_for(L, pass);
@@ -432,7 +438,7 @@ struct Miner {
             A.nchunks = (total + chunk - 1) / chunk;
             ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
             ck(cudaEventRecord(a, st), "event record");
-            ck(pass == PASS_FUSED ? launch_extend_fused(L, A, grid, st) : launch_extend_domain(L, A, grid, st),
+            ck(pass == PASS_FUSED ? launch_extend_fused(L, A, grid, st) : launch_extend_domain(L, V, A, grid, st),
                "extension kernel");
             ck(cudaEventRecord(b, st), "event record");
             ck(cudaEventSynchronize(b), "event sync");
@@ -456,7 +462,7 @@ struct Miner {
                     double p = 1.0, const uint8_t *piece_sel = nullptr) {
         LevelSet in = in_level;
         const std::vector<int64_t> pat_off = group_by_pattern(in);
-        const int L = in.L, K = L + 2;
+        const int L = in.L, K = L + (V == FSM_EXPLORE_SV ? 1 : 2);
         LevelSet out;
         out.L = K;
         ExtArgs A;
@@ -493,12 +499,13 @@ struct Miner {
         const int64_t t_live = sampled ? 1 : t;   // sampled counts say nothing about reaching t
         // ---- pass 1: quick patterns and their embedding counts (last level: fused with the
         // domains, into per-key bitmaps from a pool, when the pool can be had)
-        int64_t cap = (int64_t)1 << 20;
-        while (cap < 4 * G->qp_hint[L] && cap < ((int64_t)1 << 30)) cap <<= 1;
+        int64_t cap = G->qp_initial > 0 ? G->qp_initial : (int64_t)1 << 20;
+        if (G->qp_initial == 0)
+            while (cap < 4 * G->qp_hint[L] && cap < ((int64_t)1 << 30)) cap <<= 1;
         unsigned long long *keys = nullptr, *qcount = nullptr, *used = nullptr, *qdom = nullptr, *ptop = nullptr;
         uint32_t *pool = nullptr;
         unsigned long long pool_words = 0;
-        bool fused = final && G->fused;
+        bool fused = final && G->fused && V == FSM_EXPLORE_TV;
         if (fused) {
             size_t fr = 0, tot = 0;
             ck(cudaMemGetInfo(&fr, &tot), "memory info");
@@ -564,6 +571,7 @@ struct Miner {
                 if (qdom) mem.release(qdom);
                 if (cap >= ((int64_t)1 << 31)) fail(FSM_EUNSUPPORTED, "more than 2^30 distinct quick patterns in one level");
                 cap <<= 2;
+                rs.qp_grows += 1;
                 continue;
             }
             if (ew & ~FSM_ERR_POOL) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
@@ -582,6 +590,7 @@ struct Miner {
         rs.tested += (int64_t)st2[0];
         rs.accepted += (int64_t)st2[1];
         rs.pieces += (int64_t)st2[2];
+        rs.pieces_l[L] += (int64_t)st2[2];
         if (final) rs.final_accepted = (int64_t)st2[1];
         // ---- distinct quick patterns -> canonical codes -> pattern ids
         int64_t *slots = mem.get<int64_t>(cap);
@@ -596,7 +605,7 @@ struct Miner {
         int64_t M = 1;
         while (M < nq) M <<= 1;
         CodeRec *recs = mem.get<CodeRec>(M);
-        ck(launch_qp_canon(L, keys, slots, nq, in.lab8, in.adj8, recs, qperm, st), "canonicalise");
+        ck(launch_qp_canon(L, V, keys, slots, nq, in.lab8, in.adj8, recs, qperm, st), "canonicalise");
         ck(launch_sort_codes(recs, nq, st), "sort codes");
         int64_t *flag = mem.get<int64_t>(nq + 1);
         int64_t *ids = mem.get<int64_t>(nq + 1);
@@ -1125,6 +1134,16 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
         } else if (k == "chunk") {
             if (value != 0 && (value < 32 || value > 65536 || (value & (value - 1)))) fail(FSM_EINVAL, "chunk must be 0 or a power of two in [32, 65536]");
             g->chunk = (int32_t)value;
+        } else if (k == "explore") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "explore must be 0 (two-vertex) or 1 (single-vertex)");
+            g->explore = (int)value;
+        } else if (k == "quick_pattern") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "quick_pattern must be 0 (index-based) or 1 (edge list)");
+            g->quick_pattern = (int)value;
+        } else if (k == "qp_capacity") {
+            if (value != 0 && (value < 64 || value > ((int64_t)1 << 30) || (value & (value - 1))))
+                fail(FSM_EINVAL, "qp_capacity must be 0 or a power of two in [64, 2^30]");
+            g->qp_initial = value;
         } else if (k == "batch") {
             if (value != 0 && value < 1024) fail(FSM_EINVAL, "batch must be 0 or >= 1024");
             g->batch = value;
@@ -1147,6 +1166,12 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         if (min_support < 1) fail(FSM_EINVAL, "min_support must be >= 1");
         if (!(sample_rate > 0.0 && sample_rate <= 1.0)) fail(FSM_EINVAL, "sample_rate must be in (0, 1]");
         const bool sampled = sample_rate < 1.0 && k >= 3;   // levels 1 and 2 join no pieces
+        const int V = g->explore == 1 ? FSM_EXPLORE_SV : g->quick_pattern == 1 ? FSM_EXPLORE_TV_EDGELIST : FSM_EXPLORE_TV;
+        if (g->explore == 1 && g->quick_pattern == 1)
+            fail(FSM_EUNSUPPORTED, "edge-list quick patterns are built for two-vertex exploration only");
+        if (V != FSM_EXPLORE_TV && sampled)
+            fail(FSM_EUNSUPPORTED, "sampled mining runs with two-vertex exploration and index-based quick patterns only");
+        if (V != FSM_EXPLORE_TV && k > 7) fail(FSM_EUNSUPPORTED, "the exploration ablations support k <= 7");
         ck(cudaSetDevice(g->device), "cudaSetDevice");
         cudaStream_t st = g->stream;
         cudaEvent_t ev0, ev1, evf;
@@ -1160,6 +1185,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         {
             Arena mem(st);
             Miner m{g, st, mem, min_support, rs};
+            m.V = V;
             if (g->profile) {
                 m.prof_bytes = mem.get<unsigned long long>((FSM_MAXL + 1) * 4);
                 ck(cudaMemsetAsync(m.prof_bytes, 0, sizeof(unsigned long long) * (FSM_MAXL + 1) * 4, st), "memset");
@@ -1168,6 +1194,15 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
             if (k == 1) {
                 res = m.level1(false);
                 ck(cudaEventRecord(evf, st), "event record");
+            } else if (V == FSM_EXPLORE_SV) {
+                // single-vertex exploration: levels 1 -> 2 -> ... -> k, no size-3 pruning table
+                LevelSet cur = m.level1(true);
+                while (cur.L < k) {
+                    const bool fin = cur.L + 1 == k;
+                    if (fin) ck(cudaEventRecord(evf, st), "event record");
+                    cur = m.extend(cur, nullptr, fin);
+                }
+                res = cur;
             } else if (k == 2) {
                 res = m.level2(false);
                 ck(cudaEventRecord(evf, st), "event record");
@@ -1247,7 +1282,9 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["recount_patterns"] = rs.recount_patterns;
         r->stats["recount_frontier"] = rs.recount_frontier;
         r->stats["sampled_edges"] = rs.sampled_edges;
+        r->stats["qp_grows"] = rs.qp_grows;
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["chunk_l" + std::to_string(L)] = g->tuned_chunk[L];
+        for (int L = 1; L <= FSM_MAXL; ++L) r->stats["pieces_l" + std::to_string(L)] = rs.pieces_l[L];
         const char *pn[4] = {"count", "domain", "emit", "fused"};
         for (int p = 0; p < 4; ++p) {
             double ns = 0;

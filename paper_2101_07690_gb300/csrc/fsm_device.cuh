@@ -17,6 +17,11 @@
 
 #define FSM_MAXK 8
 #define FSM_MAXL 6               // largest stored level that is still extended (k <= 8)
+
+// exploration variants of the extension kernel (option "explore" and "quick_pattern")
+#define FSM_EXPLORE_TV 0           // two-vertex exploration, index-based quick patterns (the method)
+#define FSM_EXPLORE_SV 1           // single-vertex exploration (l -> l+1), index-based quick patterns
+#define FSM_EXPLORE_TV_EDGELIST 2  // two-vertex exploration, edge-list quick patterns
 #define FSM_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
 #define FSM_HD __host__ __device__ __forceinline__
 

@@ -263,10 +263,9 @@ struct DomCache {
     int64_t soff[FSM_MAXL];
 };
 
-template <int L, int PASS>
+template <int L, int K, int PASS>
 __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCache &dc, uint64_t key,
-                                       const int32_t (&gid)[L + 2], const int32_t (&rk)[L]) {
-    constexpr int K = L + 2;
+                                       const int32_t (&gid)[K], const int32_t (&rk)[L]) {
     if (PASS == PASS_COUNT) {
         const unsigned act = __activemask();
         const unsigned grp = __match_any_sync(act, key);
@@ -357,6 +356,71 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
     }
 }
 
+// Edge-list quick pattern (the quick pattern of earlier systems that Section 6 compares the
+// index-based one against): the joined subgraph's labels and edges listed with its vertices in
+// ascending id order.  Bits 6h..6h+5 hold the label of the h-th smallest vertex; bit 42 + q holds
+// pair q of (0,1), (0,2), ..., (K-2,K-1) over that order (K <= 7, so bit 63 stays clear and no
+// key equals FSM_EMPTY_KEY).  sg receives the vertices in that order.
+template <int K>
+__device__ __forceinline__ uint64_t edge_list_key(const int32_t (&gid)[K], const int (&lab)[K], const uint32_t *adj,
+                                                  int32_t (&sg)[K]) {
+    int ord[K];
+#pragma unroll
+    for (int h = 0; h < K; ++h) ord[h] = h;
+#pragma unroll
+    for (int a = 1; a < K; ++a)
+        for (int b = a; b > 0 && gid[ord[b - 1]] > gid[ord[b]]; --b) { const int t = ord[b]; ord[b] = ord[b - 1]; ord[b - 1] = t; }
+    uint64_t key = 0;
+    int bit = 42;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        key |= (uint64_t)lab[ord[a]] << (6 * a);
+        sg[a] = gid[ord[a]];
+#pragma unroll
+        for (int b = a + 1; b < K; ++b, ++bit)
+            if ((adj[ord[a]] >> ord[b]) & 1u) key |= 1ull << bit;
+    }
+    return key;
+}
+
+// An accepted join under edge-list quick patterns: local position h is the h-th smallest vertex
+// (sg), so domain and emission take their per-position data from sg directly.
+template <int K, int PASS>
+__device__ __forceinline__ void accept_sorted(const ExtArgs &A, CountCache *cc, uint64_t key, const int32_t (&sg)[K]) {
+    if (PASS == PASS_COUNT) {
+        const unsigned act = __activemask();
+        const unsigned grp = __match_any_sync(act, key);
+        const int lane = threadIdx.x & 31;
+        if (lane == __ffs(grp) - 1) count_key(A, cc, key, __popc(grp));
+        return;
+    }
+    const int64_t slot = qp_find(A.qp, key);
+    if (slot < 0) { atomicOr(A.err, FSM_ERR_QP_MISSING); return; }
+    if (PASS == PASS_DOMAIN) {
+        const int64_t *sb = A.slot_base + slot * 8;
+        if (__ldg(sb) < 0) return;
+#pragma unroll
+        for (int h = 0; h < K; ++h) {
+            const int32_t r = __ldg(A.g.rank + sg[h]);
+            uint32_t *w = A.dom + __ldg(sb + h) + (r >> 5);
+            const uint32_t bit = 1u << (r & 31);
+            if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+        }
+        return;
+    }
+    if (PASS == PASS_EMIT) {
+        const int32_t P = __ldg(A.qp.pattern + slot);
+        const uint32_t perm = __ldg(A.qp.perm + slot);
+        const int32_t nid = __ldg(A.newid + P);
+        if (nid < 0) return;
+        const unsigned long long pos = atomicAdd(A.out_cursor, 1ull);
+        if ((int64_t)pos >= A.out_N) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
+#pragma unroll
+        for (int h = 0; h < K; ++h) A.out_v[(int64_t)((perm >> (3 * h)) & 7) * A.out_N + (int64_t)pos] = sg[h];
+        A.out_pid[pos] = nid;
+    }
+}
+
 // Join s (vertices S, pattern pid, key position i) with one piece.  Piece vertices pv[0..2]
 // are in the piece's own order, pl their labels; shape is PIECE_WEDGE (centre pv[0]) or
 // PIECE_TRI.
@@ -382,7 +446,7 @@ __device__ __forceinline__ uint32_t cross_bits(const ExtArgs &A, const int32_t (
 // are in the piece's own order, pl their labels; shape is PIECE_WEDGE (centre pv[0]) or
 // PIECE_TRI.  The piece's two non-key vertices are va and vb; their cross bits ca / cb are
 // already known when have_a / have_b is set.
-template <int L, int PASS>
+template <int L, int PASS, int V>
 __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                            const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int shape,
                                            const int32_t (&pv)[3], const int (&pl)[3], Tally &tl,
@@ -447,10 +511,10 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
                 }
             }
         }
+        uint32_t adjK[K];
+        if (keep && (L >= 2 || V == FSM_EXPLORE_TV_EDGELIST)) join_graph(L, srows, i, tj0, tj1, txx, sub, adjK);
         if (keep && L >= 2) {
             // smallest-vertex-first dissection must return exactly (t, s)
-            uint32_t adjK[K];
-            join_graph(L, srows, i, tj0, tj1, txx, sub, adjK);
             if constexpr (L == 2) {
                 keep = dissect4_keeps(gid, adjK, i);
             } else {
@@ -462,7 +526,18 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
         }
         if (keep) {
             ++tl.accepted;
-            accept<L, PASS>(A, cc, dc, make_key((uint32_t)pid, pidx, i, jpos, sub), gid, RK);
+            if constexpr (V == FSM_EXPLORE_TV_EDGELIST) {
+                int labK[K];
+#pragma unroll
+                for (int h = 0; h < L; ++h) labK[h] = SL[h];
+                labK[L] = lx0;
+                labK[L + 1] = lx1;
+                int32_t sg[K];
+                const uint64_t key = edge_list_key<K>(gid, labK, adjK, sg);
+                accept_sorted<K, PASS>(A, cc, key, sg);
+            } else {
+                accept<L, K, PASS>(A, cc, dc, make_key((uint32_t)pid, pidx, i, jpos, sub), gid, RK);
+            }
         }
         if (A.mode == 1 || sub == 0) break;
         sub = (sub - 1) & avail;
@@ -478,7 +553,7 @@ __device__ __forceinline__ uint32_t mask_bits(const uint32_t *mk, int32_t x) {
     return c;
 }
 
-template <int L, int PASS>
+template <int L, int PASS, int V>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                          const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
                                          CountCache *cc, DomCache &dc, const uint32_t *mk, const int32_t (&RK)[L],
@@ -603,7 +678,66 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             pv[0] = t0; pv[1] = t1; pv[2] = t2;
             pl[0] = m0; pl[1] = m1; pl[2] = m2;
         }
-        join_piece<L, PASS>(A, S, SL, SR, srows, pid, i, shape, pv, pl, tl, cc, dc, a, ca, hm, cb, have_b, RK);
+        join_piece<L, PASS, V>(A, S, SL, SR, srows, pid, i, shape, pv, pl, tl, cc, dc, a, ca, hm, cb, have_b, RK);
+    }
+}
+
+// Single-vertex exploration (Section 6's ablation, l -> l+1): join s with one neighbour a of
+// the key vertex v = s[i] (lq = a's position in v's list).  The new embedding s' = s + a holds
+// the edge v-a and, edge-induced, any subset C of a's other edges into s (vertex-induced: all
+// of them).  It is kept only when
+//   (1) v is the smallest-id vertex of s that a is joined to in s', so one key position makes
+//       it, and
+//   (2) a is the largest-id vertex of s' whose removal leaves s' connected, so one parent makes
+//       it: s' minus that vertex, which is connected and, by anti-monotonicity, frequent.
+// Its quick pattern is <pid(s), label(a), i, C> (join code 3 marks the single-vertex form).
+// There is no joining-point pruning: no size-3 table is computed in this mode.
+template <int L, int PASS>
+__device__ __forceinline__ void do_edge(const ExtArgs &A, const int32_t (&S)[L], const int2 (&SR)[L], uint64_t srows,
+                                        int32_t pid, int i, int64_t lq, Tally &tl, CountCache *cc, DomCache &dc,
+                                        const uint32_t *mk, const int32_t (&RK)[L]) {
+    constexpr int K = L + 1;
+    const int32_t v = S[i];
+    const int32_t a = __ldg(A.g.pcol + __ldg(A.g.prow + v) + (int32_t)lq);
+    if (in_s<L>(S, a)) return;
+    uint32_t avail = 0;   // bit p' (p != i, p' = p minus one if p > i): a ~ s[p]
+    if constexpr (L >= 2) avail = mk ? mask_bits<L>(mk, (int32_t)lq) : cross_bits<L>(A, S, SR, i, a);
+    uint32_t above = 0;   // the same bits for the vertices of s with a larger id than v
+#pragma unroll
+    for (int p = 0; p < L; ++p)
+        if (p != i && S[p] > v) above |= 1u << (p < i ? p : p - 1);
+    if (A.mode == 1 && (avail & ~above)) return;   // vertex-induced: a smaller neighbour of a keys it
+    const uint32_t cand = avail & above;
+    const int la = __ldg(A.g.labels + a);
+    int32_t gid[K];
+#pragma unroll
+    for (int h = 0; h < L; ++h) gid[h] = S[h];
+    gid[L] = a;
+    const uint32_t all = (1u << K) - 1u;
+    uint32_t sub = cand;
+    for (;;) {
+        ++tl.tested;
+        uint32_t adjK[K];
+#pragma unroll
+        for (int h = 0; h < L; ++h) adjK[h] = (uint32_t)(srows >> (8 * h)) & 0xffu;
+        adjK[L] = 1u << i;
+        adjK[i] |= 1u << L;
+#pragma unroll
+        for (int p = 0; p < L; ++p) {
+            if (p == i || !((sub >> (p < i ? p : p - 1)) & 1u)) continue;
+            adjK[p] |= 1u << L;
+            adjK[L] |= 1u << p;
+        }
+        bool keep = true;
+#pragma unroll
+        for (int h = 0; h < L; ++h)
+            if (keep && S[h] > a && mask_connected(all & ~(1u << h), adjK, K)) keep = false;
+        if (keep) {
+            ++tl.accepted;
+            accept<L, K, PASS>(A, cc, dc, make_key((uint32_t)pid, (uint32_t)la, i, 3, sub), gid, RK);
+        }
+        if (A.mode == 1 || sub == 0) break;
+        sub = (sub - 1) & cand;
     }
 }
 
@@ -615,7 +749,7 @@ template <int PASS> struct ExtMinBlocks {
     static constexpr int value = PASS == PASS_DOMAIN ? FSM_EXT_MINB_DOMAIN : FSM_EXT_MINB_COUNT;
 };
 
-template <int L, int PASS>
+template <int L, int PASS, int V = FSM_EXPLORE_TV>
 __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(ExtArgs A) {
     const int lane = threadIdx.x & 31;
     const int64_t nunits = A.ne * L;
@@ -726,14 +860,17 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;
                 ub = __ldg(A.unit_base + u);
                 ecur = 0;
-                if constexpr (L == 2) {
+                if constexpr (L == 2 && V != FSM_EXPLORE_SV) {
                     const int32_t rb = __ldg(A.g.prow + S[i]);
                     cpos = count_below(A.g.pcol + rb, __ldg(A.g.prow + S[i] + 1) - rb, S[1 - i]);
                 }
 #pragma unroll
                 for (int p = 0; p < L; ++p) dc.soff[p] = -1;
             }
-            do_piece<L, PASS>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos, ecur);
+            if constexpr (V == FSM_EXPLORE_SV)
+                do_edge<L, PASS>(A, S, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK);
+            else
+                do_piece<L, PASS, V>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos, ecur);
         }
         if (counts) flush_warp_counts<PASS == PASS_FUSED>(A, cc);
     }
@@ -751,14 +888,20 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
     }
 }
 
-// Host launchers, one translation unit per pass.
-cudaError_t launch_extend_count(int L, const ExtArgs &A, int grid, cudaStream_t st);
-cudaError_t launch_extend_domain(int L, const ExtArgs &A, int grid, cudaStream_t st);
-cudaError_t launch_extend_emit(int L, const ExtArgs &A, int grid, cudaStream_t st);
+// Host launchers, one translation unit per pass.  V picks the exploration variant
+// (FSM_EXPLORE_*); the fused pass exists for two-vertex exploration with index-based keys only.
+cudaError_t launch_extend_count(int L, int V, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t launch_extend_domain(int L, int V, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t launch_extend_emit(int L, int V, const ExtArgs &A, int grid, cudaStream_t st);
 cudaError_t launch_extend_fused(int L, const ExtArgs &A, int grid, cudaStream_t st);
 cudaError_t occupancy_extend_fused(int L, int *blocks_per_sm);
-cudaError_t occupancy_extend_count(int L, int *blocks_per_sm);
-cudaError_t occupancy_extend_domain(int L, int *blocks_per_sm);
-cudaError_t occupancy_extend_emit(int L, int *blocks_per_sm);
+cudaError_t occupancy_extend_count(int L, int V, int *blocks_per_sm);
+cudaError_t occupancy_extend_domain(int L, int V, int *blocks_per_sm);
+cudaError_t occupancy_extend_emit(int L, int V, int *blocks_per_sm);
+// the variants' launchers (pass = PASS_COUNT, PASS_DOMAIN or PASS_EMIT)
+cudaError_t launch_extend_sv(int pass, int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t occupancy_extend_sv(int pass, int L, int *blocks_per_sm);
+cudaError_t launch_extend_edgelist(int pass, int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t occupancy_extend_edgelist(int pass, int L, int *blocks_per_sm);
 
 } // namespace fsm

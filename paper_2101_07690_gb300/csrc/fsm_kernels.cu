@@ -217,12 +217,16 @@ cudaError_t launch_prepare(const DevGraph &g, int64_t *piece_cnt, int32_t *end_o
 
 namespace {
 __global__ void unit_counts_kernel(const DevGraph g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
-                                   int64_t *cnt) {
+                                   int V, int64_t *cnt) {
     const int64_t nu = ne * L;
     for (int64_t u = gtid(); u < nu; u += gstride()) {
         const int64_t e = e0 + u / L;
         const int p = (int)(u % L);
         const int32_t v = fv[(int64_t)p * fN + e];
+        if (V == FSM_EXPLORE_SV) {   // single-vertex exploration: one candidate per neighbour of v
+            cnt[u] = g.prow[v + 1] - g.prow[v];
+            continue;
+        }
         int64_t c = g.ppc[v];
         if (L == 2) {
             // centre pairs restricted to those with an end below the other vertex of s
@@ -263,22 +267,23 @@ cudaError_t launch_tri_bits(const DevGraph &g, int32_t dmin, const int64_t *off,
 }
 
 cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
-                               int64_t *cnt, cudaStream_t st) {
+                               int V, int64_t *cnt, cudaStream_t st) {
     LAUNCHED(1);
-    unit_counts_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(g, fv, fN, e0, ne, L, cnt);
+    unit_counts_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(g, fv, fN, e0, ne, L, V, cnt);
     return cudaGetLastError();
 }
 
 namespace {
 __global__ void unit_bytes_kernel(const int32_t *row_ptr, const int64_t *piece_cnt, const int32_t *fv, int64_t fN,
-                                  int64_t e0, int64_t ne, int L, unsigned long long *sum) {
+                                  int64_t e0, int64_t ne, int L, int V, unsigned long long *sum) {
     const int64_t nu = ne * L;
     unsigned long long s = 0;
     for (int64_t u = gtid(); u < nu; u += gstride()) {
         const int64_t e = e0 + u / L;
         const int32_t v = fv[(int64_t)(u % L) * fN + e];
         const int64_t d = row_ptr[v + 1] - row_ptr[v];
-        const int64_t ends = piece_cnt[v] - d * (d - 1) / 2;
+        // single-vertex exploration reads only the key vertex's list
+        const int64_t ends = V == FSM_EXPLORE_SV ? 0 : piece_cnt[v] - d * (d - 1) / 2;
         s += 4ull * (unsigned long long)(d + ends);
         if (u % L == 0) s += 4ull * (unsigned long long)(L + 1);
     }
@@ -289,9 +294,9 @@ __global__ void unit_bytes_kernel(const int32_t *row_ptr, const int64_t *piece_c
 } // namespace
 
 cudaError_t launch_unit_bytes(const int32_t *row_ptr, const int64_t *piece_cnt, const int32_t *fv, int64_t fN,
-                              int64_t e0, int64_t ne, int L, unsigned long long *sum, cudaStream_t st) {
+                              int64_t e0, int64_t ne, int L, int V, unsigned long long *sum, cudaStream_t st) {
     LAUNCHED(1);
-    unit_bytes_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(row_ptr, piece_cnt, fv, fN, e0, ne, L, sum);
+    unit_bytes_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(row_ptr, piece_cnt, fv, fN, e0, ne, L, V, sum);
     return cudaGetLastError();
 }
 
@@ -408,27 +413,61 @@ __device__ void canonicalise(int K, const int *lab, const uint32_t *adj, unsigne
     inv = iv;
 }
 
-__global__ void qp_canon_kernel(int L, const unsigned long long *keys, const int64_t *slots, int64_t nq,
+// The labeled graph a quick-pattern key denotes, in the key's local vertex order (the order the
+// extension kernel's accept step uses for that key's positions).
+__device__ void key_graph(int V, int L, uint64_t key, const uint64_t *pat_lab8, const uint64_t *pat_adj8, int &K,
+                          int *labH, uint32_t *adjH) {
+    if (V == FSM_EXPLORE_TV_EDGELIST) {
+        // labels and edges listed over the vertices in ascending id order
+        K = L + 2;
+        int bit = 42;
+        for (int a = 0; a < K; ++a) adjH[a] = 0;
+        for (int a = 0; a < K; ++a) {
+            labH[a] = (int)(key >> (6 * a)) & 63;
+            for (int b = a + 1; b < K; ++b, ++bit)
+                if ((key >> bit) & 1ull) { adjH[a] |= 1u << b; adjH[b] |= 1u << a; }
+        }
+        return;
+    }
+    uint32_t pid, pidx, cross;
+    int i, jpos;
+    split_key(key, pid, pidx, i, jpos, cross);
+    const uint64_t lab8 = pat_lab8[pid], srows = pat_adj8[pid];
+    for (int h = 0; h < L; ++h) labH[h] = (int)(lab8 >> (8 * h)) & 0xff;
+    if (V == FSM_EXPLORE_SV) {
+        // <pid(s), label(a), i, cross bits>: a joined to s[i] and to the cross positions
+        K = L + 1;
+        for (int h = 0; h < L; ++h) adjH[h] = (uint32_t)(srows >> (8 * h)) & 0xffu;
+        labH[L] = (int)(pidx & 63);
+        adjH[L] = 1u << i;
+        adjH[i] |= 1u << L;
+        for (int p = 0; p < L; ++p) {
+            if (p == i || !((cross >> (p < i ? p : p - 1)) & 1u)) continue;
+            adjH[p] |= 1u << L;
+            adjH[L] |= 1u << p;
+        }
+        return;
+    }
+    K = L + 2;
+    const int shape = (int)(pidx >> 18);
+    const int pl[3] = {(int)(pidx >> 12) & 63, (int)(pidx >> 6) & 63, (int)pidx & 63};
+    const int q0 = jpos == 0 ? 1 : 0;
+    const int q1 = jpos == 2 ? 1 : 2;
+    labH[L] = pl[q0];
+    labH[L + 1] = pl[q1];
+    uint32_t tj0, tj1, txx;
+    piece_join_edges(shape, jpos, tj0, tj1, txx);
+    join_graph(L, srows, i, tj0, tj1, txx, cross, adjH);
+}
+
+__global__ void qp_canon_kernel(int L, int V, const unsigned long long *keys, const int64_t *slots, int64_t nq,
                                 const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
                                 uint32_t *perm_out) {
-    const int K = L + 2;
     for (int64_t q = gtid(); q < nq; q += gstride()) {
         const int64_t slot = slots[q];
-        uint32_t pid, pidx, cross;
-        int i, jpos;
-        split_key(keys[slot], pid, pidx, i, jpos, cross);
-        const uint64_t lab8 = pat_lab8[pid], srows = pat_adj8[pid];
-        const int shape = (int)(pidx >> 18);
-        const int pl[3] = {(int)(pidx >> 12) & 63, (int)(pidx >> 6) & 63, (int)pidx & 63};
-        const int q0 = jpos == 0 ? 1 : 0;
-        const int q1 = jpos == 2 ? 1 : 2;
-        int labH[FSM_MAXK];
-        for (int h = 0; h < L; ++h) labH[h] = (int)(lab8 >> (8 * h)) & 0xff;
-        labH[L] = pl[q0];
-        labH[L + 1] = pl[q1];
-        uint32_t tj0, tj1, txx, adjH[FSM_MAXK];
-        piece_join_edges(shape, jpos, tj0, tj1, txx);
-        join_graph(L, srows, i, tj0, tj1, txx, cross, adjH);
+        int K, labH[FSM_MAXK];
+        uint32_t adjH[FSM_MAXK];
+        key_graph(V, L, keys[slot], pat_lab8, pat_adj8, K, labH, adjH);
         unsigned long long cl;
         uint32_t ca, inv;
         canonicalise(K, labH, adjH, cl, ca, inv);
@@ -614,12 +653,12 @@ __global__ void sum_frequent_kernel(const int32_t *newid, const unsigned long lo
 
 } // namespace
 
-cudaError_t launch_qp_canon(int L, const unsigned long long *keys, const int64_t *slots, int64_t nq,
+cudaError_t launch_qp_canon(int L, int V, const unsigned long long *keys, const int64_t *slots, int64_t nq,
                             const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
                             uint32_t *perm, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     LAUNCHED(1);
-    qp_canon_kernel<<<blocks_for(nq, 128), 128, 0, st>>>(L, keys, slots, nq, pat_lab8, pat_adj8, recs, perm);
+    qp_canon_kernel<<<blocks_for(nq, 128), 128, 0, st>>>(L, V, keys, slots, nq, pat_lab8, pat_adj8, recs, perm);
     return cudaGetLastError();
 }
 

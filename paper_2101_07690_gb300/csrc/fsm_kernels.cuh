@@ -35,14 +35,16 @@ size_t scan_temp_bytes(int64_t n);
 cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *temp, cudaStream_t st);
 
 // ---- per-batch unit piece counts: cnt[u] = g.ppc[v] for the key vertex v = fv[(u % L) * fN + e0 + u / L],
-//      with the centre pairs cut to centre_pairs(d, c) when L == 2 (see fsm_device.cuh)
-cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
+//      with the centre pairs cut to centre_pairs(d, c) when L == 2 (see fsm_device.cuh); with
+//      V = FSM_EXPLORE_SV (single-vertex exploration) cnt[u] = d(v)
+cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L, int V,
                                int64_t *cnt, cudaStream_t st);
 
 // algorithmic bytes of one batch of units, added to *sum: per unit 4 * (d(v) + end pieces of v)
-// (the key list and every end list read once) plus 4 * (L + 1) per embedding (vertices + id)
+// (the key list and every end list read once; single-vertex exploration: 4 * d(v)) plus
+// 4 * (L + 1) per embedding (vertices + id)
 cudaError_t launch_unit_bytes(const int32_t *row_ptr, const int64_t *piece_cnt, const int32_t *fv, int64_t fN,
-                              int64_t e0, int64_t ne, int L, unsigned long long *sum, cudaStream_t st);
+                              int64_t e0, int64_t ne, int L, int V, unsigned long long *sum, cudaStream_t st);
 
 // Group a stored frontier by pattern id: offsets = exclusive prefix of counts[P] (P+1 entries),
 // then every embedding is copied to off[pid] + (arrival order within its pattern).
@@ -55,7 +57,7 @@ cudaError_t launch_fill_u64(unsigned long long *p, unsigned long long v, int64_t
 cudaError_t launch_qp_compact(const unsigned long long *keys, int64_t cap, int64_t *slots,
                               unsigned long long *n_out, cudaStream_t st);
 // canonical code of each distinct key; writes recs[q] (idx = q) and perm[slot]
-cudaError_t launch_qp_canon(int L, const unsigned long long *keys, const int64_t *slots, int64_t nq,
+cudaError_t launch_qp_canon(int L, int V, const unsigned long long *keys, const int64_t *slots, int64_t nq,
                             const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
                             uint32_t *perm, cudaStream_t st);
 // sort recs[0..n) ascending by (lab, adj, idx); recs must have room for next_pow2(n) entries

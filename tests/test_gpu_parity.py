@@ -244,3 +244,72 @@ def test_config_shaped_graphs_k5(fsm, shape):
     g = gg.workload(name, scale=scale, cap=cap)
     for t in (2, 4):
         check(fsm, g, 5, t, "edge", {"launch": 1})
+
+
+def _hub_graph():
+    """600 vertices, 1200 edges, degree cap 48 (beta 2.1, 3 Zipf labels): 13 vertices of degree
+    >= 32, so five-vertex joins from stored triples meet the paths the full-size workloads take
+    on hub key vertices -- neighbour matrices for the triangle test and shared-memory cross
+    masks of single-unit chunks -- while the oracle still finishes in seconds."""
+    return gg.chung_lu(600, 1200, 2.1, 2, cap=48, num_labels=3, label_law="zipf", zipf_s=1.2)
+
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+def test_hub_graph_k5(fsm, mode):
+    g = _hub_graph()
+    assert int((g.degrees() >= 32).sum()) >= 10
+    for t in (1, 40):
+        for opts in ({"launch": 1}, {"launch": 0, "chunk": 32}, {"launch": 2}, {"launch": 1, "chunk": 4096}):
+            check(fsm, g, 5, t, mode, opts)
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_quick_pattern_table_overflow_and_retry(fsm, k):
+    """A 64-slot first table overflows at once: every level grows it x4 and repeats its count
+    pass until it fits, with the oracle's result."""
+    g = gg.workload("cl100k", scale=0.005, cap=30)
+    G = fsm.Graph.from_graphgen(g)
+    G.set_option("qp_capacity", 64)
+    got = G.mine(k, 6, stats=True)
+    G.close()
+    assert got["stats"]["qp_grows"] >= 2
+    _same(got, oracle_at(g, k, 6), f"qp_capacity=64 k={k}")
+
+
+@pytest.mark.parametrize("opts", [{"explore": 1}, {"quick_pattern": 1}])
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+def test_exploration_ablations_match_oracle(fsm, opts, mode):
+    """Section 6's ablations -- single-vertex exploration (l -> l+1) and edge-list quick
+    patterns -- compute the same exact result as the method itself, in every launch mode."""
+    cases = [(gg.random_small(10, 0.35, 2, 3), range(2, 7), 1),
+             (gg.workload("er1000"), (2, 3, 4, 5), 10),
+             (gg.workload("cl100k", scale=0.005, cap=30), (3, 4), 6),
+             (_hub_graph(), (4, 5), 40)]
+    for g, ks, t in cases:
+        for k in ks:
+            check(fsm, g, k, t, mode, dict(opts, launch=1))
+    g = gg.workload("er1000")
+    for launch in (0, 2):
+        check(fsm, g, 4, 10, mode, dict(opts, launch=launch))
+
+
+def test_ablation_counters(fsm):
+    """Edge-list quick patterns canonicalise more distinct keys than index-based ones for the
+    same output; single-vertex exploration runs one level per added vertex."""
+    g = gg.workload("cl100k", scale=0.005, cap=30)
+    G = fsm.Graph.from_graphgen(g)
+    ref = G.mine(4, 6, stats=True)
+    G.set_option("quick_pattern", 1)
+    el = G.mine(4, 6, stats=True)
+    G.set_option("quick_pattern", 0)
+    G.set_option("explore", 1)
+    sv = G.mine(4, 6, stats=True)
+    with pytest.raises(fsm.FsmError) as e:
+        G.mine(4, 6, sample_rate=0.5)
+    assert e.value.code == fsm.FSM_EUNSUPPORTED
+    G.close()
+    for r in (el, sv):
+        for key in ("labels", "adj", "support", "count"):
+            assert np.array_equal(r[key], ref[key])
+    assert el["stats"]["quick_patterns"] > ref["stats"]["quick_patterns"]
+    assert ref["stats"]["levels"] == 2 and sv["stats"]["levels"] == 3

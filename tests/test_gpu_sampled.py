@@ -10,6 +10,8 @@
 * Sampled mining with a trained network: exactly recounted supports are exact, and the
   network's decisions beat the plain estimator on held-out graphs.
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -66,6 +68,51 @@ def test_sampled_candidates_match_oracle(fsm, case):
     assert checked > 0
     assert np.all(got["exact"] == 0)
     assert got["features"].shape == (len(got["support"]), 32) and np.all(np.isfinite(got["features"]))
+    # the 32 features of every exactly frequent candidate, element by element, from the oracle's
+    # sampled image sets (integer-derived entries exactly, the others within float32 rounding)
+    cls = np.bincount(g.labels, minlength=g.num_labels)
+    nfeat = 0
+    for i, q in enumerate(_keys(got, k)):
+        j = okeys[q]
+        if o["support"][j] < t:
+            continue
+        f = got["features"][i].astype(np.float64)
+        lab = [int(x) for x in o["labels"][j]]
+        edges = oracle.pattern_edges(o["adj"][j], k)
+        orbits, aut = _orbits(k, lab, edges)
+        pop = o["spop"][j]
+        for orb in orbits:
+            assert len({int(pop[c]) for c in orb}) == 1, (q, orb, pop)
+        pcs = sorted(int(pop[orb[0]]) for orb in orbits)
+        assert [int(round(np.expm1(x))) for x in f[:len(pcs)]] == pcs, q
+        assert np.all(f[len(pcs):8] == 0)
+        tol = dict(rtol=1e-4, atol=1e-4)
+        assert np.allclose(f[8:8 + k], [np.log(cls[l] / g.n) for l in lab], **tol) and np.all(f[8 + k:16] == 0)
+        mean_deg = [o["sdeg"][j][c] / pop[c] if pop[c] else 0.0 for c in range(k)]
+        assert np.allclose(f[16:16 + k], mean_deg, **tol) and np.all(f[16 + k:24] == 0), q
+        assert f[24] == k and f[25] == len(edges)
+        assert int(round(np.expm1(f[27]))) == int(o["scount"][j])
+        assert int(round(np.exp(f[29]))) == aut
+        assert np.allclose(f[[26, 28, 30, 31]], [np.log(p), np.log(t / g.n), np.log((min(pcs) + 1) / p), np.log(g.n)],
+                           **tol)
+        nfeat += 1
+    assert nfeat == checked
+
+
+def _orbits(k, lab, edges):
+    """Orbits of a pattern's positions under its label-preserving automorphisms, and their
+    number, by trying every permutation."""
+    es = {frozenset(e) for e in edges}
+    auts = [f for f in itertools.permutations(range(k))
+            if all(lab[c] == lab[f[c]] for c in range(k)) and all(frozenset((f[a], f[b])) in es for a, b in edges)]
+    seen, orbits = set(), []
+    for c in range(k):
+        if c in seen:
+            continue
+        orb = sorted({f[c] for f in auts})
+        seen.update(orb)
+        orbits.append(orb)
+    return orbits, len(auts)
 
 
 def _random_net(fsm, seed):
@@ -149,10 +196,13 @@ def test_learned_sampling_recounts_exactly_and_beats_the_plain_estimator(fsm):
             G.set_option("delta_milli", 700)
             learned = G.mine(k, t, sample_rate=p)
             G.close()
-            # exactly recounted supports are the exact ones
-            for q, s, e in zip(_keys(learned, k), learned["support"], learned["exact"]):
-                if e:
-                    assert exact.get(q) == int(s)
+            # exactly recounted supports and counts are the oracle's (its one-pattern matcher,
+            # on up to 150 recounted patterns, the smallest supports first)
+            rec = [(int(s), i) for i, (s, e) in enumerate(zip(learned["support"], learned["exact"])) if e]
+            for s_, i in sorted(rec)[:150]:
+                sup, cnt = oracle.pattern_support(g, learned["labels"][i], int(learned["adj"][i]))
+                assert (sup, cnt) == (s_, int(learned["count"][i]))
+                assert exact.get(_keys(learned, k)[i]) == s_
             stats["model"].append(learn.compare(exact, learn.frequent_set(learned, k)))
             stats["plain"].append(learn.compare(exact, learn.frequent_set(plain, k)))
         rec_m = np.mean([s["recall"] for s in stats["model"]])

@@ -295,3 +295,7 @@ def test_sampled_statistics_match_independent_count(mode, k, seed):
     assert total == int(o["count"].sum())
     assert list(o["scount"]) == scount
     assert list(o["ssupport"]) == [min(len(s) for s in im) for im in images]
+    deg = g.degrees()
+    for q, im in enumerate(images):
+        assert list(o["spop"][q]) == [len(s) for s in im]
+        assert np.allclose(o["sdeg"][q], [sum(math.log1p(deg[v]) for v in s) for s in im], rtol=1e-12, atol=1e-12)
