@@ -88,6 +88,28 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                passes and calls (reported as stat "chunk_l<l>"); 0 = forget tuned values.
  *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
  *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
+ *   "explore"    0 = two-vertex exploration (default, Section 4.1); 1 = single-vertex
+ *                exploration, l -> l+1 (the ablation Section 6 compares against): every level
+ *                joins each stored embedding with one neighbour of a key vertex, a new embedding
+ *                is kept when its new vertex is the largest-id vertex whose removal leaves it
+ *                connected and its key vertex is that vertex's smallest-id neighbour in the
+ *                embedding; no size-3 pruning table.  Exact results, identical to 0; k <= 7.
+ *   "quick_pattern" 0 = index-based quick patterns (default, Section 4.4); 1 = edge-list quick
+ *                patterns (the baseline Section 6 compares against): each accepted join is keyed
+ *                by its labels and edges listed over its vertices in ascending id order, so more
+ *                distinct keys are canonicalised (stat "quick_patterns").  Identical results;
+ *                k <= 7.
+ *   "join_quota" ST x of Section 5 (0 = off, default): every join l -> l+2 runs at most x^2
+ *                candidate pieces per key group (stored embedding s, key vertex v) and, when
+ *                edges are joined (l = 2), at most x edges per key vertex; candidates are drawn
+ *                by an affine progression seeded from option "seed" and the ids of s and v (see
+ *                the quota notes in the library's device header).  Supports and counts are those
+ *                of the drawn embeddings, lower bounds of the exact ones (fsm_result_exact = 0),
+ *                and every level keeps the patterns whose drawn support reaches t.
+ *   "match_quota" M.ST of Section 5 (0 = off, default): the size-3 level runs at most this many
+ *                candidate pieces per vertex (candidates whose smallest vertex is not that
+ *                vertex are dropped after the draw).  Quotas exclude "explore" = 1,
+ *                "quick_pattern" = 1 and sample_rate < 1.
  *   "qp_capacity" slots of the first quick-pattern hash table of every level (power of two,
  *                64..2^30; 0 = at least 2^20, sized from the previous call).  A table that fills
  *                past half is grown x4 and its pass repeated (stat "qp_grows"); results are

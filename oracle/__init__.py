@@ -63,6 +63,13 @@ def _load():
                                                                P(ctypes.c_double)]
             lib.oracle_dissect.restype = ctypes.c_uint32
             lib.oracle_dissect.argtypes = [ctypes.c_int32, P(ctypes.c_uint32)]
+            lib.oracle_mine_quota.restype = ctypes.c_void_p
+            lib.oracle_mine_quota.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                                              P(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                              ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
+            lib.oracle_quota_draw.restype = None
+            lib.oracle_quota_draw.argtypes = [ctypes.c_uint64, ctypes.c_uint64, P(ctypes.c_uint64),
+                                              P(ctypes.c_uint64)]
             lib.oracle_dissect_join.restype = ctypes.c_uint32
             lib.oracle_dissect_join.argtypes = [ctypes.c_int32, P(ctypes.c_uint32), P(ctypes.c_int32)]
             lib.oracle_edge_kept.restype = ctypes.c_int
@@ -200,3 +207,38 @@ def kept(u, adj_rows, seed: int, p: float) -> bool:
     if r < 0:
         raise ValueError("kept needs 3 <= k <= 8")
     return bool(r)
+
+
+def mine_quota(g, k: int, t: int, mode: str = "edge", seed: int = 0, join_quota: int = 0,
+               match_quota: int = 0) -> dict:
+    """Patterns of exactly k vertices (3 <= k <= 8) whose MNI support over the embeddings drawn
+    under Section 5's sampling quotas reaches t, by the method's own level-wise steps: size-3
+    matching with at most ``match_quota`` candidate pieces per vertex, then joins l -> l+2 with at
+    most ``join_quota``^2 candidate pieces per key group and, joining edges, ``join_quota`` edges
+    per key vertex (0 = all).  Quotas 0 give exact mining.  Same dict layout as ``mine``."""
+    lib = _load()
+    row_ptr = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(g.col, dtype=np.int32)
+    labels = np.ascontiguousarray(g.labels, dtype=np.int32)
+    res = lib.oracle_mine_quota(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                _ptr(labels, ctypes.c_int32), k, MODES[mode], int(t), int(seed) & ((1 << 64) - 1),
+                                int(join_quota), int(match_quota))
+    if not res:
+        raise ValueError("oracle_mine_quota rejected its arguments")
+    try:
+        npat = lib.oracle_result_count(res)
+        out = {"labels": np.zeros((npat, k), np.int32), "adj": np.zeros(npat, np.uint64),
+               "support": np.zeros(npat, np.int64), "count": np.zeros(npat, np.int64)}
+        if npat:
+            lib.oracle_result_copy(res, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
+                                   _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64))
+    finally:
+        lib.oracle_free(res)
+    return out
+
+
+def quota_draw(h: int, c: int) -> tuple[int, int]:
+    """(a, b) of the quota draw for hash h and modulus c >= 2: candidates (a j + b) mod c."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _load().oracle_quota_draw(int(h) & ((1 << 64) - 1), int(c), ctypes.byref(a), ctypes.byref(b))
+    return int(a.value), int(b.value)

@@ -773,3 +773,422 @@ int oracle_kept(int32_t k, const int32_t *u, const uint32_t *adjrow, uint64_t se
     o.thr = (uint64_t)(sqrt(p) * 18446744073709551616.0);
     return kept(&o, u, adjrow);
 }
+
+/* ================================================================== quota-sampled mining
+ *
+ * Section 5's subgraph sampling with fixed iteration counts, taken through the method's own
+ * steps (an approximation has no plain definition to compute), slowly and directly:
+ *   1. size 1: the frequent labels;
+ *   2. size 3 ("matching"): every vertex v with a frequent label runs its candidate pieces
+ *      (numbered as below), at most match_quota of them when match_quota > 0; a candidate
+ *      becomes a size-3 embedding only if v is its smallest vertex;
+ *   3. even k: size 2, every edge, exactly;
+ *   4. joins l -> l+2: every stored frequent size-l embedding s and every vertex v of s (the
+ *      key group of v) runs the candidate pieces keyed at v -- at most join_quota^2 of them --
+ *      and, when l = 2, only join_quota edges per key vertex are joined; each candidate piece t
+ *      (disjoint from s but for v, of a frequent size-3 pattern) is joined with every subset of
+ *      the cross edges (edge-induced) or all of them (vertex-induced), pruned when a connected
+ *      triple {v, s[p], t[q]} has an infrequent size-3 pattern (Section 4.5), and kept when the
+ *      smallest-vertex-first dissection of the result returns exactly (t, v) (Algorithm 1);
+ *   5. every level keeps the embeddings of patterns whose MNI support over the drawn
+ *      embeddings reaches t; the last level's patterns are the output.
+ * Candidate pieces of key vertex v with neighbour list N (length d): first the centre pairs
+ * {N[x], N[y]}, x < y, numbered y(y-1)/2 + x -- except when joining an edge {v, w}, where only
+ * pairs with x < c, c = |{z in N : z < w}|, are candidates (the others never survive the
+ * dissection): rows y < c numbered as before, then row y >= c, column x at
+ * c(c-1)/2 + (y - c) c + x -- then the end pieces v - a - b, a = N[j], b = N(a)[r], numbered
+ * (sum of d(N[j']) over j' < j) + r.  A centre pair is a wedge centred at v, plus (edge-induced)
+ * a triangle when a ~ b, or (vertex-induced) only that triangle; an end piece is the wedge
+ * centred at a (none when b = v, or vertex-induced when b ~ v).
+ * Draws: a unit with c candidates and quota Q < c runs candidates (a j + b) mod c, j < Q, with
+ * h = H(... H(H(seed) ^ x_0) ... ^ x_{l-1}) then H(h ^ (2^32 + v)) over the ascending ids x of
+ * s (H = one splitmix64 step), a = the first integer coprime to c at or after 1 + (h mod (c-1))
+ * (wrapping from c - 1 to 1), b = H(h) mod c; an edge {v, w} at position pos of v's list runs
+ * when d(v) <= X or (a_v pos + b_v) mod d(v) < X, (a_v, b_v) drawn likewise from
+ * H(H(seed) ^ (2^33 + v)) with modulus d(v). */
+
+static uint64_t q_gcd(uint64_t x, uint64_t y) { while (y) { uint64_t r = x % y; x = y; y = r; } return x; }
+
+static void q_draw(uint64_t h, uint64_t c, uint64_t *a, uint64_t *b) {
+    uint64_t x = 1 + h % (c - 1);
+    while (q_gcd(x, c) != 1) x = (x + 1 == c) ? 1 : x + 1;
+    *a = x;
+    *b = smix(h) % c;
+}
+
+typedef struct { int l; int64_t n, cap; int32_t *v; uint32_t *adj; int32_t *pat; } estore_t;
+
+static void es_push(estore_t *e, const int32_t *v, const uint32_t *adj, int32_t pat) {
+    if (e->n == e->cap) {
+        e->cap = e->cap ? e->cap * 2 : 1024;
+        e->v = (int32_t *)realloc(e->v, sizeof(int32_t) * (size_t)(e->cap * e->l));
+        e->adj = (uint32_t *)realloc(e->adj, sizeof(uint32_t) * (size_t)(e->cap * e->l));
+        e->pat = (int32_t *)realloc(e->pat, sizeof(int32_t) * (size_t)e->cap);
+    }
+    memcpy(e->v + e->n * e->l, v, sizeof(int32_t) * (size_t)e->l);
+    memcpy(e->adj + e->n * e->l, adj, sizeof(uint32_t) * (size_t)e->l);
+    e->pat[e->n++] = pat;
+}
+
+static void es_free(estore_t *e) { free(e->v); free(e->adj); free(e->pat); }
+
+static void q_ctx_init(oracle_t *o, int k, const int32_t *row_ptr, const int32_t *col, const int32_t *labels,
+                       int32_t n, int mode) {
+    memset(o, 0, sizeof(*o));
+    o->k = k; o->mode = mode; o->row_ptr = row_ptr; o->col = col; o->labels = labels; o->n = n;
+    o->cx.k = k;
+    gen_perms(&o->cx);
+}
+
+static void q_ctx_free(oracle_t *o) {
+    for (int64_t p = 0; p < o->npat; p++)
+        for (int c = 0; c < OR_MAXK; c++) { free(o->pat[p].dom[c].slot); free(o->pat[p].sdom[c].slot); }
+    free(o->pat); free(o->pat_slot); free(o->memo); free(o->pool); free(o->cx.perms);
+}
+
+/* record one embedding (vertex ids u in any order, adjacency rows over the same positions):
+ * its pattern, count and images; returns the pattern index */
+static int32_t q_record(oracle_t *o, const int32_t *u, const uint32_t *adjrow) {
+    int32_t lab[OR_MAXK];
+    for (int i = 0; i < o->k; i++) lab[i] = o->labels[u[i]];
+    memo_t *m = canonical(o, lab, adjrow);
+    pattern_t *p = &o->pat[m->pattern];
+    p->count++;
+    const uint8_t *perm = o->pool + m->perm_off;
+    for (int32_t q = 0; q < m->nopt; q++, perm += o->k)
+        for (int c = 0; c < o->k; c++) vset_insert(&p->dom[c], u[perm[c]]);
+    return m->pattern;
+}
+
+static int64_t q_sigma(const pattern_t *p, int k) {
+    int64_t s = -1;
+    for (int c = 0; c < k; c++) if (s < 0 || p->dom[c].size < s) s = p->dom[c].size;
+    return s;
+}
+
+/* embeddings of the patterns of o with support >= t (positions ascending by id) */
+static void q_keep_frequent(const oracle_t *o, const estore_t *all, int64_t t, estore_t *out) {
+    out->l = all->l;
+    for (int64_t e = 0; e < all->n; e++)
+        if (q_sigma(&o->pat[all->pat[e]], o->k) >= t) es_push(out, all->v + e * all->l, all->adj + e * all->l, all->pat[e]);
+}
+
+/* is the size-3 graph (ids u, rows adj over 3 positions) of a frequent size-3 pattern of o3? */
+static int q_frequent3(oracle_t *o3, const int32_t *u, const uint32_t *adj, int64_t t) {
+    int32_t lab[3] = {o3->labels[u[0]], o3->labels[u[1]], o3->labels[u[2]]};
+    memo_t *m = canonical(o3, lab, adj);
+    return q_sigma(&o3->pat[m->pattern], 3) >= t;
+}
+
+/* decode candidate idx of key vertex v (list N, length d); cpos >= 0: joining the edge {v, w}
+ * with cpos entries of N below w.  Returns 1 for a centre pair, 0 for an end piece. */
+static int q_decode(const int32_t *row_ptr, const int32_t *col, int32_t v, int64_t idx, int64_t cpos, int32_t *a,
+                    int32_t *b) {
+    const int32_t *N = col + row_ptr[v];
+    const int64_t d = row_ptr[v + 1] - row_ptr[v];
+    const int64_t tri = cpos >= 0 ? cpos * (cpos - 1) / 2 : d * (d - 1) / 2;
+    const int64_t nc = cpos >= 0 ? tri + (d - cpos) * cpos : tri;
+    if (idx < nc) {
+        int64_t x, y;
+        if (idx < tri) {
+            y = 1;
+            while ((y + 1) * y / 2 <= idx) y++;
+            x = idx - y * (y - 1) / 2;
+        } else {
+            const int64_t r = idx - tri;
+            y = cpos + r / cpos;
+            x = r % cpos;
+        }
+        *a = N[x]; *b = N[y];
+        return 1;
+    }
+    int64_t r = idx - nc;
+    for (int64_t j = 0; j < d; j++) {
+        const int64_t dj = row_ptr[N[j] + 1] - row_ptr[N[j]];
+        if (r < dj) { *a = N[j]; *b = col[row_ptr[N[j]] + r]; return 0; }
+        r -= dj;
+    }
+    *a = *b = -1;
+    return 0;
+}
+
+static int q_pos_of(const int32_t *u, int l, int32_t x) {
+    for (int i = 0; i < l; i++) if (u[i] == x) return i;
+    return -1;
+}
+
+/* one join level: s (size l) -> next (size l+2), recorded in o (k = l+2) and stored in all */
+static void q_join(oracle_t *o, oracle_t *o3, int64_t t, const estore_t *s, uint64_t seed, int64_t X, estore_t *all) {
+    const int l = s->l, K = l + 2;
+    const int32_t *row_ptr = o->row_ptr, *col = o->col;
+    const int64_t Q = X * X;
+    all->l = K;
+    for (int64_t e = 0; e < s->n; e++) {
+        const int32_t *u = s->v + e * l;      /* ascending ids */
+        const uint32_t *sa = s->adj + e * l;
+        for (int i = 0; i < l; i++) {
+            const int32_t v = u[i];
+            const int64_t d = row_ptr[v + 1] - row_ptr[v];
+            int64_t cpos = -1;
+            if (l == 2) {
+                const int32_t w = u[1 - i];
+                cpos = 0;
+                while (cpos < d && col[row_ptr[v] + cpos] < w) cpos++;
+                if (X > 0 && d > X) {   /* edge quota of the key vertex */
+                    uint64_t av, bv;
+                    q_draw(smix(smix(seed) ^ ((1ULL << 33) + (uint64_t)(uint32_t)v)), (uint64_t)d, &av, &bv);
+                    if ((av * (uint64_t)cpos + bv) % (uint64_t)d >= (uint64_t)X) continue;
+                }
+            }
+            int64_t c = cpos >= 0 ? cpos * (cpos - 1) / 2 + (d - cpos) * cpos : d * (d - 1) / 2;
+            for (int64_t j = 0; j < d; j++) { int32_t a = col[row_ptr[v] + j]; c += row_ptr[a + 1] - row_ptr[a]; }
+            uint64_t qa = 1, qb = 0;
+            int64_t runs = c;
+            if (Q > 0 && c > Q) {
+                uint64_t h = smix(seed);
+                for (int q = 0; q < l; q++) h = smix(h ^ (uint64_t)(uint32_t)u[q]);
+                h = smix(h ^ ((1ULL << 32) + (uint64_t)(uint32_t)v));
+                q_draw(h, (uint64_t)c, &qa, &qb);
+                runs = Q;
+            }
+            for (int64_t jj = 0; jj < runs; jj++) {
+                const int64_t idx = runs == c ? jj : (int64_t)((qa * (uint64_t)jj + qb) % (uint64_t)c);
+                int32_t a, b;
+                const int centre = q_decode(row_ptr, col, v, idx, cpos, &a, &b);
+                if (a < 0 || b == v || q_pos_of(u, l, a) >= 0 || q_pos_of(u, l, b) >= 0) continue;
+                const int closed = adjacent(row_ptr, col, a, b);
+                /* the piece's edge sets over (v, a, b): bit 0 v-a, bit 1 v-b, bit 2 a-b */
+                int shapes[2], ns = 0;
+                if (centre) {
+                    if (o->mode == 1) shapes[ns++] = closed ? 7 : 3;
+                    else { shapes[ns++] = 3; if (closed) shapes[ns++] = 7; }
+                } else {
+                    if (o->mode == 1 && adjacent(row_ptr, col, v, b)) continue;
+                    shapes[ns++] = 5;
+                }
+                for (int si = 0; si < ns; si++) {
+                    const int sh = shapes[si];
+                    /* the piece's own pattern must be frequent */
+                    int32_t pu[3] = {v, a, b};
+                    uint32_t pr[3] = {0, 0, 0};
+                    if (sh & 1) { pr[0] |= 2; pr[1] |= 1; }
+                    if (sh & 2) { pr[0] |= 4; pr[2] |= 1; }
+                    if (sh & 4) { pr[1] |= 4; pr[2] |= 2; }
+                    if (!q_frequent3(o3, pu, pr, t)) continue;
+                    /* cross edges between s \ {v} and {a, b} */
+                    int cp[2 * OR_MAXK], cx[2 * OR_MAXK], nav = 0;
+                    for (int p = 0; p < l; p++) {
+                        if (p == i) continue;
+                        if (adjacent(row_ptr, col, u[p], a)) { cp[nav] = p; cx[nav] = 0; nav++; }
+                        if (adjacent(row_ptr, col, u[p], b)) { cp[nav] = p; cx[nav] = 1; nav++; }
+                    }
+                    const uint32_t full = (1u << nav) - 1u;
+                    for (uint32_t sub = (o->mode == 1 ? full : 0);; sub++) {
+                        /* joining-point pruning */
+                        int pruned = 0;
+                        for (int p = 0; p < l && !pruned; p++) {
+                            if (p == i) continue;
+                            for (int q = 0; q < 2 && !pruned; q++) {
+                                const int32_t xq = q ? b : a;
+                                const int e1 = (sa[i] >> p) & 1u;
+                                const int e2 = q ? ((sh >> 1) & 1) : (sh & 1);
+                                int e3 = 0;
+                                for (int z = 0; z < nav; z++) if (((sub >> z) & 1u) && cp[z] == p && cx[z] == q) e3 = 1;
+                                if (e1 + e2 + e3 < 2) continue;
+                                int32_t tu[3] = {v, u[p], xq};
+                                uint32_t tr[3] = {0, 0, 0};
+                                if (e1) { tr[0] |= 2; tr[1] |= 1; }
+                                if (e2) { tr[0] |= 4; tr[2] |= 1; }
+                                if (e3) { tr[1] |= 4; tr[2] |= 2; }
+                                if (!q_frequent3(o3, tu, tr, t)) pruned = 1;
+                            }
+                        }
+                        if (!pruned) {
+                            /* the joined subgraph, positions ascending by id */
+                            int32_t ids[OR_MAXK];
+                            for (int p = 0; p < l; p++) ids[p] = u[p];
+                            ids[l] = a; ids[l + 1] = b;
+                            uint32_t rows[OR_MAXK] = {0};
+                            for (int p = 0; p < l; p++) rows[p] = sa[p];
+                            if (sh & 1) { rows[i] |= 1u << l; rows[l] |= 1u << i; }
+                            if (sh & 2) { rows[i] |= 1u << (l + 1); rows[l + 1] |= 1u << i; }
+                            if (sh & 4) { rows[l] |= 1u << (l + 1); rows[l + 1] |= 1u << l; }
+                            for (int z = 0; z < nav; z++)
+                                if ((sub >> z) & 1u) {
+                                    const int h2 = l + cx[z];
+                                    rows[cp[z]] |= 1u << h2; rows[h2] |= 1u << cp[z];
+                                }
+                            int ord[OR_MAXK];
+                            for (int h = 0; h < K; h++) ord[h] = h;
+                            for (int x = 1; x < K; x++)
+                                for (int y = x; y > 0 && ids[ord[y - 1]] > ids[ord[y]]; y--) { int tt = ord[y]; ord[y] = ord[y - 1]; ord[y - 1] = tt; }
+                            int at[OR_MAXK];
+                            for (int h = 0; h < K; h++) at[ord[h]] = h;
+                            int32_t su[OR_MAXK];
+                            uint32_t srow[OR_MAXK] = {0};
+                            for (int h = 0; h < K; h++) {
+                                su[at[h]] = ids[h];
+                                for (int h2 = 0; h2 < K; h2++) if ((rows[h] >> h2) & 1u) srow[at[h]] |= 1u << at[h2];
+                            }
+                            int jn;
+                            const uint32_t lm = dissect_three_join(K, srow, &jn);
+                            const uint32_t want = (1u << at[i]) | (1u << at[l]) | (1u << at[l + 1]);
+                            if (lm == want && jn == at[i]) {
+                                const int32_t pat = q_record(o, su, srow);
+                                es_push(all, su, srow, pat);
+                            }
+                        }
+                        if (o->mode == 1 || sub == full) break;
+                    }
+                }
+            }
+        }
+    }
+}
+
+static oracle_result_t *q_result(const oracle_t *o, int k, int64_t t) {
+    oracle_result_t *r = (oracle_result_t *)calloc(1, sizeof(oracle_result_t));
+    r->k = k;
+    int64_t *keep = (int64_t *)malloc(sizeof(int64_t) * (size_t)(o->npat + 1));
+    int64_t nk = 0;
+    for (int64_t p = 0; p < o->npat; p++) if (q_sigma(&o->pat[p], k) >= t) keep[nk++] = p;
+    code_sort_k = k; code_sort_base = o->pat;
+    qsort(keep, (size_t)nk, sizeof(int64_t), idx_cmp);
+    r->npat = nk;
+    r->labels = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nk * k + 1));
+    r->adj = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk + 1));
+    r->support = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
+    r->count = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
+    for (int64_t q = 0; q < nk; q++) {
+        const pattern_t *p = &o->pat[keep[q]];
+        for (int c = 0; c < k; c++) r->labels[q * k + c] = p->code.lab[c];
+        uint64_t bits = 0;
+        int np = k * (k - 1) / 2, idx = 0;
+        for (int i = 0; i < k; i++)
+            for (int j = i + 1; j < k; j++, idx++)
+                if ((p->code.adj >> (np - 1 - idx)) & 1u) bits |= 1ULL << (i * k + j);
+        r->adj[q] = bits;
+        r->support[q] = q_sigma(p, k);
+        r->count[q] = p->count;
+    }
+    free(keep);
+    return r;
+}
+
+/*
+ * oracle_mine_quota: the patterns of exactly k vertices (3 <= k <= 8) whose MNI support over
+ * the embeddings drawn under Section 5's quotas reaches t, with those supports and counts (see
+ * the steps above).  join_quota = 0 and match_quota = 0 draw everything, which is exact mining
+ * by the method's own steps.
+ */
+oracle_result_t *oracle_mine_quota(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *labels,
+                                   int32_t k, int32_t mode, int64_t t, uint64_t seed, int64_t join_quota,
+                                   int64_t match_quota) {
+    if (k < 3 || k > OR_MAXK || n < 0 || (mode != 0 && mode != 1) || join_quota < 0 || match_quota < 0) return NULL;
+    int64_t cls[256] = {0};
+    for (int32_t v = 0; v < n; v++) cls[labels[v] & 0xff]++;
+    /* size 3 by matching from each vertex with a frequent label */
+    oracle_t o3;
+    q_ctx_init(&o3, 3, row_ptr, col, labels, n, mode);
+    estore_t all3 = {3, 0, 0, NULL, NULL, NULL};
+    for (int32_t v = 0; v < n; v++) {
+        if (cls[labels[v] & 0xff] < t) continue;
+        const int64_t d = row_ptr[v + 1] - row_ptr[v];
+        int64_t c = d * (d - 1) / 2;
+        for (int64_t j = 0; j < d; j++) { int32_t a = col[row_ptr[v] + j]; c += row_ptr[a + 1] - row_ptr[a]; }
+        uint64_t qa = 1, qb = 0;
+        int64_t runs = c;
+        if (match_quota > 0 && c > match_quota) {
+            uint64_t h = smix(smix(seed) ^ (uint64_t)(uint32_t)v);
+            h = smix(h ^ ((1ULL << 32) + (uint64_t)(uint32_t)v));
+            q_draw(h, (uint64_t)c, &qa, &qb);
+            runs = match_quota;
+        }
+        for (int64_t jj = 0; jj < runs; jj++) {
+            const int64_t idx = runs == c ? jj : (int64_t)((qa * (uint64_t)jj + qb) % (uint64_t)c);
+            int32_t a, b;
+            const int centre = q_decode(row_ptr, col, v, idx, -1, &a, &b);
+            if (b == v || a < v || b < v) continue;   /* keyed at its smallest vertex */
+            const int closed = adjacent(row_ptr, col, a, b);
+            int shapes[2], ns = 0;
+            if (centre) {
+                if (mode == 1) shapes[ns++] = closed ? 7 : 3;
+                else { shapes[ns++] = 3; if (closed) shapes[ns++] = 7; }
+            } else {
+                if (mode == 1 && adjacent(row_ptr, col, v, b)) continue;
+                shapes[ns++] = 5;
+            }
+            for (int si = 0; si < ns; si++) {
+                const int sh = shapes[si];
+                int32_t ids[3] = {v, a, b};
+                uint32_t rows[3] = {0, 0, 0};
+                if (sh & 1) { rows[0] |= 2; rows[1] |= 1; }
+                if (sh & 2) { rows[0] |= 4; rows[2] |= 1; }
+                if (sh & 4) { rows[1] |= 4; rows[2] |= 2; }
+                /* ascending ids: v is the smallest; order a, b */
+                if (ids[1] > ids[2]) {
+                    int32_t ti = ids[1]; ids[1] = ids[2]; ids[2] = ti;
+                    uint32_t r0 = rows[0], r1 = rows[1], r2 = rows[2];
+                    uint32_t sw[3];
+                    sw[0] = (r0 & 1u) | ((r0 >> 1) & 2u) | ((r0 << 1) & 4u);
+                    sw[1] = (r2 & 1u) | ((r2 >> 1) & 2u) | ((r2 << 1) & 4u);
+                    sw[2] = (r1 & 1u) | ((r1 >> 1) & 2u) | ((r1 << 1) & 4u);
+                    rows[0] = sw[0]; rows[1] = sw[1]; rows[2] = sw[2];
+                }
+                const int32_t pat = q_record(&o3, ids, rows);
+                es_push(&all3, ids, rows, pat);
+            }
+        }
+    }
+    estore_t cur = {3, 0, 0, NULL, NULL, NULL};
+    oracle_t last;
+    int have_last = 0;
+    if (k == 3) {
+        last = o3; have_last = 1;
+    } else {
+        if (k & 1) {
+            q_keep_frequent(&o3, &all3, t, &cur);
+        } else {
+            /* size 2: every edge, exactly */
+            oracle_t o2;
+            q_ctx_init(&o2, 2, row_ptr, col, labels, n, mode);
+            estore_t all2 = {2, 0, 0, NULL, NULL, NULL};
+            for (int32_t x = 0; x < n; x++)
+                for (int32_t q = row_ptr[x]; q < row_ptr[x + 1]; q++) {
+                    if (col[q] <= x) continue;
+                    int32_t ids[2] = {x, col[q]};
+                    uint32_t rows[2] = {2u, 1u};
+                    es_push(&all2, ids, rows, q_record(&o2, ids, rows));
+                }
+            cur.l = 2;
+            q_keep_frequent(&o2, &all2, t, &cur);
+            es_free(&all2);
+            q_ctx_free(&o2);
+        }
+        while (cur.l + 2 <= k) {
+            oracle_t on;
+            q_ctx_init(&on, cur.l + 2, row_ptr, col, labels, n, mode);
+            estore_t alln = {cur.l + 2, 0, 0, NULL, NULL, NULL};
+            q_join(&on, &o3, t, &cur, seed, join_quota, &alln);
+            es_free(&cur);
+            memset(&cur, 0, sizeof(cur));
+            if (alln.l == k) {
+                last = on; have_last = 1;
+                es_free(&alln);
+                break;
+            }
+            q_keep_frequent(&on, &alln, t, &cur);
+            es_free(&alln);
+            q_ctx_free(&on);
+        }
+    }
+    es_free(&all3);
+    es_free(&cur);
+    oracle_result_t *r = have_last ? q_result(&last, k, t) : NULL;
+    if (have_last && k != 3) q_ctx_free(&last);
+    q_ctx_free(&o3);
+    return r;
+}
+
+/* test hook: the draw's (a, b) for hash h and modulus c >= 2 */
+void oracle_quota_draw(uint64_t h, uint64_t c, uint64_t *a, uint64_t *b) { q_draw(h, c, a, b); }

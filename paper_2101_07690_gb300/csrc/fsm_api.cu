@@ -150,6 +150,8 @@ struct fsm_graph {
     int64_t qp_initial = 0;               // option "qp_capacity": first quick-pattern table size (0 = 2^20)
     int explore = 0;                      // option "explore": 0 two-vertex (the method), 1 single-vertex
     int quick_pattern = 0;                // option "quick_pattern": 0 index-based, 1 edge list
+    int64_t join_quota = 0;               // option "join_quota": ST x of Section 5 (0 = off)
+    int64_t match_quota = 0;              // option "match_quota": M.ST of Section 5 (0 = off)
     int autotune = 0;
     int group = 2;   // persistent launch: frontier grouped by pattern id first (1), never (0), from l = 3 (2)
     int fused = 0;
@@ -329,7 +331,7 @@ struct Miner {
             CapturedGraph cg(st);
             cg.begin();
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, V, base, st), "unit counts");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, V, A.quota, A.edge_quota, A.qseed, base, st), "unit counts");
                 ck(launch_scan_i64(base, base, r.ne * L, tmp, st), "unit scan");
                 bytes(r);
                 ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
@@ -347,7 +349,7 @@ struct Miner {
             if (prof) ck(cudaEventRecord(prof_ev[ei].b, st), "event record");
         } else {
             for (const Range &r : ranges) {
-                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, V, base, st), "unit counts");
+                ck(launch_unit_counts(A.g, in.fv, in.N, r.e0, r.ne, L, V, A.quota, A.edge_quota, A.qseed, base, st), "unit counts");
                 ck(launch_scan_i64(base, base, r.ne * L, tmp, st), "unit scan");
                 const int64_t total = d2h(base + r.ne * L, st);
                 if (total == 0) continue;
@@ -415,7 +417,7 @@ struct Miner {
         int64_t *base = mem.get<int64_t>(nu + 1);
         void *tmp = mem.get<char>((int64_t)scan_temp_bytes(nu) + 16);
         unsigned long long *ctr = mem.get<unsigned long long>(1);
-        ck(launch_unit_counts(A.g, in.fv, in.N, 0, ne, L, V, cnt, st), "unit counts");
+        ck(launch_unit_counts(A.g, in.fv, in.N, 0, ne, L, V, A.quota, A.edge_quota, A.qseed, cnt, st), "unit counts");
         ck(launch_scan_i64(cnt, base, nu, tmp, st), "unit scan");
         const int64_t total = d2h(base + nu, st);
         const int grid = grid_for(L, pass);
@@ -474,6 +476,14 @@ struct Miner {
         A.piece_sel = piece_sel;
         A.err = G->err;
         A.sampled = sampled ? 1 : 0;
+        if (V == FSM_EXPLORE_TV_QUOTA) {
+            // Section 5: size-3 matching (l = 1) draws match_quota candidates per vertex; every
+            // join draws join_quota^2 pieces per key group and, joining edges, join_quota edges
+            // per key vertex
+            A.quota = L == 1 ? G->match_quota : G->join_quota * G->join_quota;
+            A.edge_quota = L == 2 ? G->join_quota : 0;
+            A.qseed = G->seed;
+        }
         if (sampled) {
             // pieces come from the kept directed edges only (rate sqrt(p) each)
             const uint64_t thr = (uint64_t)(std::sqrt(p) * 18446744073709551616.0);
@@ -1134,6 +1144,12 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
         } else if (k == "chunk") {
             if (value != 0 && (value < 32 || value > 65536 || (value & (value - 1)))) fail(FSM_EINVAL, "chunk must be 0 or a power of two in [32, 65536]");
             g->chunk = (int32_t)value;
+        } else if (k == "join_quota") {
+            if (value < 0 || value > 65536) fail(FSM_EINVAL, "join_quota must be in [0, 65536]");
+            g->join_quota = value;
+        } else if (k == "match_quota") {
+            if (value < 0 || value > ((int64_t)1 << 32)) fail(FSM_EINVAL, "match_quota must be in [0, 2^32]");
+            g->match_quota = value;
         } else if (k == "explore") {
             if (value != 0 && value != 1) fail(FSM_EINVAL, "explore must be 0 (two-vertex) or 1 (single-vertex)");
             g->explore = (int)value;
@@ -1166,12 +1182,16 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         if (min_support < 1) fail(FSM_EINVAL, "min_support must be >= 1");
         if (!(sample_rate > 0.0 && sample_rate <= 1.0)) fail(FSM_EINVAL, "sample_rate must be in (0, 1]");
         const bool sampled = sample_rate < 1.0 && k >= 3;   // levels 1 and 2 join no pieces
-        const int V = g->explore == 1 ? FSM_EXPLORE_SV : g->quick_pattern == 1 ? FSM_EXPLORE_TV_EDGELIST : FSM_EXPLORE_TV;
-        if (g->explore == 1 && g->quick_pattern == 1)
-            fail(FSM_EUNSUPPORTED, "edge-list quick patterns are built for two-vertex exploration only");
+        const bool quota = g->join_quota > 0 || g->match_quota > 0;
+        const int V = g->explore == 1 ? FSM_EXPLORE_SV : g->quick_pattern == 1 ? FSM_EXPLORE_TV_EDGELIST
+                    : quota ? FSM_EXPLORE_TV_QUOTA : FSM_EXPLORE_TV;
+        if (g->explore + g->quick_pattern + (quota ? 1 : 0) > 1)
+            fail(FSM_EUNSUPPORTED, "single-vertex exploration, edge-list quick patterns and sampling quotas exclude each other");
         if (V != FSM_EXPLORE_TV && sampled)
-            fail(FSM_EUNSUPPORTED, "sampled mining runs with two-vertex exploration and index-based quick patterns only");
-        if (V != FSM_EXPLORE_TV && k > 7) fail(FSM_EUNSUPPORTED, "the exploration ablations support k <= 7");
+            fail(FSM_EUNSUPPORTED, "rate-sampled mining runs with two-vertex exploration and index-based quick patterns, "
+                                   "without sampling quotas, only");
+        if ((V == FSM_EXPLORE_SV || V == FSM_EXPLORE_TV_EDGELIST) && k > 7)
+            fail(FSM_EUNSUPPORTED, "the exploration ablations support k <= 7");
         ck(cudaSetDevice(g->device), "cudaSetDevice");
         cudaStream_t st = g->stream;
         cudaEvent_t ev0, ev1, evf;
@@ -1240,6 +1260,9 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
             if (res.P >= 0) {
                 ck(cudaEventRecord(ev1, st), "event record");
                 fill_result(r, res, k, st);
+                // sampling quotas: supports and counts are those of the drawn embeddings (lower
+                // bounds of the exact ones)
+                if (V == FSM_EXPLORE_TV_QUOTA) r->exact.assign(r->exact.size(), 0);
             }
             if (g->profile) {
                 unsigned long long pb[(FSM_MAXL + 1) * 4];

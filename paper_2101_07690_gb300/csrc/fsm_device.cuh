@@ -22,6 +22,7 @@
 #define FSM_EXPLORE_TV 0           // two-vertex exploration, index-based quick patterns (the method)
 #define FSM_EXPLORE_SV 1           // single-vertex exploration (l -> l+1), index-based quick patterns
 #define FSM_EXPLORE_TV_EDGELIST 2  // two-vertex exploration, edge-list quick patterns
+#define FSM_EXPLORE_TV_QUOTA 3     // two-vertex exploration with per-key-group sampling quotas
 #define FSM_EMPTY_KEY 0xFFFFFFFFFFFFFFFFull
 #define FSM_HD __host__ __device__ __forceinline__
 
@@ -168,6 +169,60 @@ FSM_HD bool keep_edge(uint64_t seed, uint64_t thr, int32_t x, int32_t y) {
     h = splitmix_step(h ^ (uint64_t)(uint32_t)x);
     h = splitmix_step(h ^ (uint64_t)(uint32_t)y);
     return h < thr;
+}
+
+// ---------------------------------------------------------------------------- sampling quotas
+//
+// Section 5's sampling with fixed iteration counts: a loop over the candidates of one key group
+// runs all of them when there are at most Q, otherwise Q drawn uniformly.  Here a key group is
+// one unit (stored embedding s, key vertex v = s[i]) and its loop runs over the unit's candidate
+// pieces, numbered as the extension kernel enumerates them (centre pairs of v's list, then end
+// pieces along v's list).  A unit with c > Q candidates runs candidates (a * j + b) mod c for
+// j = 0 .. Q-1: a uniformly placed, randomly strided arithmetic progression, Q distinct pieces
+// since gcd(a, c) = 1.  a and b come from the unit hash
+//     h = H(... H(H(seed) ^ x_0) ... ^ x_{l-1}) then h = H(h ^ (2^32 + v))
+// over the ids x_0 < ... < x_{l-1} of s (so the draw does not depend on the order in which s
+// is stored), H one splitmix64 step: a = the first integer coprime to c at or after
+// 1 + (h mod (c - 1)), wrapping from c - 1 to 1, and b = H(h) mod c.
+// When an edge list is joined (l = 2), the edges of each key vertex v are sampled too: with
+// d(v) > X, the unit of edge {v, w} runs only if (a_v * pos + b_v) mod d(v) < X, pos = w's
+// position in v's list and (a_v, b_v) drawn as above from g_v = H(H(seed) ^ (2^33 + v)) and
+// modulus d(v): X of v's edges, uniformly.
+
+FSM_HD uint64_t gcd_u64(uint64_t x, uint64_t y) {
+    while (y) {
+        const uint64_t t = x % y;
+        x = y;
+        y = t;
+    }
+    return x;
+}
+
+// a, b of the affine draw for modulus c >= 2 from hash h
+FSM_HD void quota_affine(uint64_t h, uint64_t c, uint64_t &a, uint64_t &b) {
+    a = 1 + h % (c - 1);
+    while (gcd_u64(a, c) != 1) a = a + 1 == c ? 1 : a + 1;
+    b = splitmix_step(h) % c;
+}
+
+// unit hash of embedding s (ids in any order, L <= FSM_MAXL) joined at v
+FSM_HD uint64_t quota_unit_hash(uint64_t seed, const int32_t *ids, int L, int32_t v) {
+    int32_t s[FSM_MAXL];
+    for (int h = 0; h < L; ++h) s[h] = ids[h];
+    for (int a = 1; a < L; ++a)
+        for (int b = a; b > 0 && s[b - 1] > s[b]; --b) { const int32_t t = s[b]; s[b] = s[b - 1]; s[b - 1] = t; }
+    uint64_t h = splitmix_step(seed);
+    for (int a = 0; a < L; ++a) h = splitmix_step(h ^ (uint64_t)(uint32_t)s[a]);
+    return splitmix_step(h ^ ((1ull << 32) + (uint64_t)(uint32_t)v));
+}
+
+// Does the unit of edge {v, w} (w at position pos of v's list of length d) run under an edge
+// quota X?
+FSM_HD bool quota_edge_kept(uint64_t seed, int32_t v, int64_t pos, int64_t d, int64_t X) {
+    if (d <= X) return true;
+    uint64_t a, b;
+    quota_affine(splitmix_step(splitmix_step(seed) ^ ((1ull << 33) + (uint64_t)(uint32_t)v)), (uint64_t)d, a, b);
+    return (a * (uint64_t)pos + b) % (uint64_t)d < (uint64_t)X;
 }
 
 // ---------------------------------------------------------------------------- dissection

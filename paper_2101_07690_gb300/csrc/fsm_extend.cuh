@@ -82,6 +82,11 @@ struct ExtArgs {
     const int32_t *cls_size;
     // sampled last level (pieces come from the kept edges in g.prow / g.pcol)
     int sampled;
+    // sampling quotas (variant FSM_EXPLORE_TV_QUOTA): candidate pieces per unit (0 = all) and,
+    // when an edge list is joined, edges per key vertex (0 = all); draws seeded by qseed
+    int64_t quota;
+    int64_t edge_quota;
+    uint64_t qseed;
     int *err;
 };
 
@@ -557,7 +562,9 @@ template <int L, int PASS, int V>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                          const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
                                          CountCache *cc, DomCache &dc, const uint32_t *mk, const int32_t (&RK)[L],
-                                         int32_t cpos, int32_t &ecur) {
+                                         int32_t cpos, int32_t &ecur, const ulonglong2 qab, uint64_t qc) {
+    // quota draw: the j-th candidate run by this unit is candidate (a * j + b) mod c
+    if (V == FSM_EXPLORE_TV_QUOTA && qc) lq = (int64_t)((qab.x * (uint64_t)lq + qab.y) % qc);
     const DevGraph &g = A.g;
     const int32_t v = S[i];
     const int32_t rp = __ldg(g.prow + v);               // the lists pieces are drawn from
@@ -834,6 +841,8 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
             }
         }
         int64_t cur = -1, ub = 0;
+        ulonglong2 qab = make_ulonglong2(0ull, 0ull);   // quota draw of the current unit
+        uint64_t qc = 0;                                // its candidate count, 0 = no draw
         int32_t cpos = 0;   // l = 2: entries of the key vertex's list below the other vertex of s
         int32_t ecur = 0;   // end list of this lane's last end piece in the unit
         int32_t S[L];
@@ -864,13 +873,27 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
                     const int32_t rb = __ldg(A.g.prow + S[i]);
                     cpos = count_below(A.g.pcol + rb, __ldg(A.g.prow + S[i] + 1) - rb, S[1 - i]);
                 }
+                if constexpr (V == FSM_EXPLORE_TV_QUOTA) {
+                    // the unit's candidates before the quota cut (as the prefix kernel counted)
+                    const int32_t v = S[i];
+                    const int64_t d = __ldg(A.g.prow + v + 1) - __ldg(A.g.prow + v);
+                    const int64_t pairs = d * (d - 1) / 2;
+                    const int64_t c = (L == 2 ? centre_pairs(d, cpos) : pairs) + (__ldg(A.g.ppc + v) - pairs);
+                    qc = 0;
+                    if (A.quota > 0 && c > A.quota) {
+                        uint64_t qa, qb;
+                        quota_affine(quota_unit_hash(A.qseed, S, L, v), (uint64_t)c, qa, qb);
+                        qab = make_ulonglong2(qa, qb);
+                        qc = (uint64_t)c;
+                    }
+                }
 #pragma unroll
                 for (int p = 0; p < L; ++p) dc.soff[p] = -1;
             }
             if constexpr (V == FSM_EXPLORE_SV)
                 do_edge<L, PASS>(A, S, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK);
             else
-                do_piece<L, PASS, V>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos, ecur);
+                do_piece<L, PASS, V>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos, ecur, qab, qc);
         }
         if (counts) flush_warp_counts<PASS == PASS_FUSED>(A, cc);
     }
@@ -903,5 +926,7 @@ cudaError_t launch_extend_sv(int pass, int L, const ExtArgs &A, int grid, cudaSt
 cudaError_t occupancy_extend_sv(int pass, int L, int *blocks_per_sm);
 cudaError_t launch_extend_edgelist(int pass, int L, const ExtArgs &A, int grid, cudaStream_t st);
 cudaError_t occupancy_extend_edgelist(int pass, int L, int *blocks_per_sm);
+cudaError_t launch_extend_quota(int pass, int L, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t occupancy_extend_quota(int pass, int L, int *blocks_per_sm);
 
 } // namespace fsm

@@ -217,7 +217,7 @@ cudaError_t launch_prepare(const DevGraph &g, int64_t *piece_cnt, int32_t *end_o
 
 namespace {
 __global__ void unit_counts_kernel(const DevGraph g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
-                                   int V, int64_t *cnt) {
+                                   int V, int64_t quota, int64_t edge_quota, uint64_t qseed, int64_t *cnt) {
     const int64_t nu = ne * L;
     for (int64_t u = gtid(); u < nu; u += gstride()) {
         const int64_t e = e0 + u / L;
@@ -232,8 +232,11 @@ __global__ void unit_counts_kernel(const DevGraph g, const int32_t *fv, int64_t 
             // centre pairs restricted to those with an end below the other vertex of s
             const int32_t w = fv[(int64_t)(1 - p) * fN + e];
             const int32_t rb = g.prow[v], d = g.prow[v + 1] - rb;
-            c += centre_pairs(d, count_below(g.pcol + rb, d, w)) - (int64_t)d * (d - 1) / 2;
+            const int32_t pos = count_below(g.pcol + rb, d, w);   // w's position in v's list
+            c += centre_pairs(d, pos) - (int64_t)d * (d - 1) / 2;
+            if (V == FSM_EXPLORE_TV_QUOTA && edge_quota > 0 && !quota_edge_kept(qseed, v, pos, d, edge_quota)) c = 0;
         }
+        if (V == FSM_EXPLORE_TV_QUOTA && quota > 0 && c > quota) c = quota;
         cnt[u] = c;
     }
 }
@@ -267,9 +270,11 @@ cudaError_t launch_tri_bits(const DevGraph &g, int32_t dmin, const int64_t *off,
 }
 
 cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L,
-                               int V, int64_t *cnt, cudaStream_t st) {
+                               int V, int64_t quota, int64_t edge_quota, uint64_t qseed, int64_t *cnt,
+                               cudaStream_t st) {
     LAUNCHED(1);
-    unit_counts_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(g, fv, fN, e0, ne, L, V, cnt);
+    unit_counts_kernel<<<blocks_for(ne * L), kThreads, 0, st>>>(g, fv, fN, e0, ne, L, V, quota, edge_quota, qseed,
+                                                                cnt);
     return cudaGetLastError();
 }
 

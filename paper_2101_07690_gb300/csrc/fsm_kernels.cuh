@@ -36,9 +36,11 @@ cudaError_t launch_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *te
 
 // ---- per-batch unit piece counts: cnt[u] = g.ppc[v] for the key vertex v = fv[(u % L) * fN + e0 + u / L],
 //      with the centre pairs cut to centre_pairs(d, c) when L == 2 (see fsm_device.cuh); with
-//      V = FSM_EXPLORE_SV (single-vertex exploration) cnt[u] = d(v)
+//      V = FSM_EXPLORE_SV (single-vertex exploration) cnt[u] = d(v); with V = FSM_EXPLORE_TV_QUOTA
+//      the count is cut to min(c, quota), and at L == 2 to 0 for edges outside their key vertex's
+//      edge quota (see fsm_device.cuh)
 cudaError_t launch_unit_counts(const DevGraph &g, const int32_t *fv, int64_t fN, int64_t e0, int64_t ne, int L, int V,
-                               int64_t *cnt, cudaStream_t st);
+                               int64_t quota, int64_t edge_quota, uint64_t qseed, int64_t *cnt, cudaStream_t st);
 
 // algorithmic bytes of one batch of units, added to *sum: per unit 4 * (d(v) + end pieces of v)
 // (the key list and every end list read once; single-vertex exploration: 4 * d(v)) plus
