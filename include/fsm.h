@@ -114,12 +114,16 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                64..2^30; 0 = at least 2^20, sized from the previous call).  A table that fills
  *                past half is grown x4 and its pass repeated (stat "qp_grows"); results are
  *                identical.
- *   "fused"      1 = the last level counts quick patterns and fills MNI domains in one pass,
- *                into per-key bitmaps merged per pattern afterwards; 0 = a count pass then a
- *                domain pass (default: measured faster, as per-key bitmaps multiply the bit
- *                atomics).  Both give identical results; a pool shortfall falls back to the two
- *                passes.
- *   "fused_pool" size in 32-bit words of the per-key bitmap pool (0 = sized automatically).
+ *   "fused"      1 = the last level of exact mining (k <= 7) is enumerated once: each accepted
+ *                join is counted under its quick pattern and sets its MNI domain bits at once;
+ *                the first lane to meet a quick pattern canonicalises it and claims its
+ *                pattern's orbit bitmaps (every pattern gets bitmaps, frequent or not); 0 = a
+ *                count pass, canonicalisation, then a domain pass for the patterns that can
+ *                still reach t (default).  Identical results; when the bitmap pool or the pattern
+ *                table runs out, the level is counted again and finished in two passes (stat
+ *                "fused_fallbacks").
+ *   "fused_pool" size in 32-bit words of the one-pass level's bitmap pool (0 = twice what the
+ *                previous call used, else 40% of the free device memory, at most 2^32 words).
  *   "seed"       64-bit seed of the piece sampling of fsm_mine with sample_rate < 1 (default 0).
  *   "candidates" 1 = sampled mining returns every candidate pattern of the sampled level with
  *                its estimated support (smallest orbit popcount / p) and its 32 features

@@ -222,6 +222,7 @@ struct RunStats {
     // profiling (option "profile"): per extension pass, device time, launches, algorithmic bytes
     int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0, sampled_edges = 0;
     int64_t qp_grows = 0;                  // quick-pattern table overflows (table grown x4, pass repeated)
+    int64_t fused_fallbacks = 0;           // one-pass last levels redone as two passes (pool or table full)
     int64_t pieces_l[FSM_MAXL + 1] = {};   // pieces enumerated by the count pass, per extended level size
     double pass_ns[FSM_MAXL + 1][4] = {};
     int64_t pass_launches[FSM_MAXL + 1][4] = {}, pass_bytes[FSM_MAXL + 1][4] = {};
@@ -406,8 +407,8 @@ struct Miner {
     }
 
     // Autotuner: time a pass on a sample of the frontier for each candidate chunk size and keep
-    // the fastest for this level: the domain pass (idempotent: it only ORs domain bits), or the
-    // fused pass, whose tables the caller wipes afterwards.
+    // the fastest for this level: the domain pass (idempotent: it only ORs domain bits), or, before
+    // a one-pass last level, the count pass, whose table the caller wipes afterwards.
     void tune_chunk(const LevelSet &in, ExtArgs A, int pass = PASS_DOMAIN) {
         const int L = in.L;
         if (!G->autotune || G->chunk > 0 || G->tuned_chunk[L] > 0 || in.N == 0) return;
@@ -440,7 +441,7 @@ struct Miner {
             A.nchunks = (total + chunk - 1) / chunk;
             ck(cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), st), "memset");
             ck(cudaEventRecord(a, st), "event record");
-            ck(pass == PASS_FUSED ? launch_extend_fused(L, A, grid, st) : launch_extend_domain(L, V, A, grid, st),
+            ck(pass == PASS_COUNT ? launch_extend_count(L, V, A, grid, st) : launch_extend_domain(L, V, A, grid, st),
                "extension kernel");
             ck(cudaEventRecord(b, st), "event record");
             ck(cudaEventSynchronize(b), "event sync");
@@ -507,20 +508,22 @@ struct Miner {
             rs.sampled_edges = kept;
         }
         const int64_t t_live = sampled ? 1 : t;   // sampled counts say nothing about reaching t
-        // ---- pass 1: quick patterns and their embedding counts (last level: fused with the
-        // domains, into per-key bitmaps from a pool, when the pool can be had)
+        // ---- pass 1: quick patterns and their embedding counts; at the last level (k <= 7, exact
+        // mining) also the MNI domains, in the same enumeration, when option "fused" is set
         int64_t cap = G->qp_initial > 0 ? G->qp_initial : (int64_t)1 << 20;
         if (G->qp_initial == 0)
             while (cap < 4 * G->qp_hint[L] && cap < ((int64_t)1 << 30)) cap <<= 1;
-        unsigned long long *keys = nullptr, *qcount = nullptr, *used = nullptr, *qdom = nullptr, *ptop = nullptr;
+        unsigned long long *keys = nullptr, *qcount = nullptr, *used = nullptr, *ptop = nullptr, *ckeys = nullptr,
+                           *coff = nullptr;
+        long long *soff = nullptr;
         uint32_t *pool = nullptr;
         unsigned long long pool_words = 0;
-        bool fused = final && G->fused && V == FSM_EXPLORE_TV;
+        bool fused = final && G->fused && V == FSM_EXPLORE_TV && !sampled && K <= 7;
         if (fused) {
             size_t fr = 0, tot = 0;
             ck(cudaMemGetInfo(&fr, &tot), "memory info");
-            // the size the last call needed (twice, for safety), else 40% of the free memory
-            const unsigned long long cap_words = (unsigned long long)std::min<size_t>(fr / 4 * 2 / 5, (size_t)12 << 30);
+            // twice what the last call needed, else 40% of the free memory, at most 2^32 words
+            const unsigned long long cap_words = (unsigned long long)std::min<size_t>(fr / 4 * 2 / 5, (size_t)1 << 32);
             pool_words = G->pool_hint[L] ? std::min(cap_words, 2 * G->pool_hint[L] + (1ull << 22)) : cap_words;
             pool_words = std::max<unsigned long long>(pool_words, 1ull << 20);
             if (G->pool_force) pool_words = G->pool_force;
@@ -534,25 +537,47 @@ struct Miner {
                 ptop = mem.get<unsigned long long>(1);
             }
         }
-        for (;;) {
-            keys = mem.get<unsigned long long>(cap);
-            qcount = mem.get<unsigned long long>(cap);
-            used = mem.get<unsigned long long>(1);
+        auto release_pass1 = [&]() {
+            for (void *q : {(void *)keys, (void *)qcount, (void *)used, (void *)ckeys, (void *)coff, (void *)soff})
+                if (q) mem.release(q);
+            keys = qcount = used = ckeys = coff = nullptr;
+            soff = nullptr;
+        };
+        auto clear_pass1 = [&]() {
             ck(launch_fill_u64(keys, FSM_EMPTY_KEY, cap, st), "fill");
             ck(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long) * cap, st), "memset");
             ck(cudaMemsetAsync(used, 0, sizeof(unsigned long long), st), "memset");
             ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
             ck(cudaMemsetAsync(G->stats, 0, 3 * sizeof(unsigned long long), st), "memset");
             if (fused) {
-                qdom = mem.get<unsigned long long>(cap * 8);
-                ck(cudaMemsetAsync(qdom, 0, sizeof(unsigned long long) * cap * 8, st), "memset");
+                ck(launch_fill_u64(ckeys, FSM_EMPTY_KEY, cap, st), "fill");
+                ck(cudaMemsetAsync(coff, 0, sizeof(unsigned long long) * cap, st), "memset");
+                ck(cudaMemsetAsync(soff, 0xff, sizeof(long long) * cap * 8, st), "memset");
                 ck(cudaMemsetAsync(pool, 0, pool_words * 4, st), "memset");
                 ck(cudaMemsetAsync(ptop, 0, sizeof(unsigned long long), st), "memset");
-                A.qp_dom = qdom;
+            }
+        };
+        for (;;) {
+            keys = mem.get<unsigned long long>(cap);
+            qcount = mem.get<unsigned long long>(cap);
+            used = mem.get<unsigned long long>(1);
+            if (fused) {
+                // the pattern (code) table has as many slots as the quick-pattern table, so it is
+                // at most half full whenever that one is
+                ckeys = mem.get<unsigned long long>(cap);
+                coff = mem.get<unsigned long long>(cap);
+                soff = mem.get<long long>(cap * 8);
+                A.pat_lab = in.lab8;
+                A.code_keys = ckeys;
+                A.code_off = coff;
+                A.code_mask = (uint64_t)cap - 1;
+                A.slot_off = soff;
                 A.pool = pool;
                 A.pool_top = ptop;
                 A.pool_words = pool_words;
                 A.cls_size = G->cls_size;
+                A.explore = V;
+                A.level = L;
             }
             A.qp.keys = keys;
             A.qp.count = qcount;
@@ -560,38 +585,33 @@ struct Miner {
             A.qp.used = used;
             A.qp.max_used = (unsigned long long)(cap / 2);
             A.stats = G->stats;
+            clear_pass1();
             if (fused && G->autotune && G->chunk <= 0 && G->tuned_chunk[L] <= 0) {
-                // trial fused passes on a sample; their counts and bits are then wiped
-                tune_chunk(in, A, PASS_FUSED);
-                ck(launch_fill_u64(keys, FSM_EMPTY_KEY, cap, st), "fill");
-                ck(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long) * cap, st), "memset");
-                ck(cudaMemsetAsync(used, 0, sizeof(unsigned long long), st), "memset");
-                ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
-                ck(cudaMemsetAsync(G->stats, 0, 3 * sizeof(unsigned long long), st), "memset");
-                ck(cudaMemsetAsync(qdom, 0, sizeof(unsigned long long) * cap * 8, st), "memset");
-                ck(cudaMemsetAsync(pool, 0, pool_words * 4, st), "memset");
-                ck(cudaMemsetAsync(ptop, 0, sizeof(unsigned long long), st), "memset");
+                // chunk size from trial count passes on a sample; their counts are then wiped
+                tune_chunk(in, A, PASS_COUNT);
+                clear_pass1();
             }
             run_pass(fused ? PASS_FUSED : PASS_COUNT, in, A, pat_off);
             const int ew = err_word();
             if (ew & FSM_ERR_QP_OVERFLOW) {
-                mem.release(keys);
-                mem.release(qcount);
-                mem.release(used);
-                if (qdom) mem.release(qdom);
+                release_pass1();
                 if (cap >= ((int64_t)1 << 31)) fail(FSM_EUNSUPPORTED, "more than 2^30 distinct quick patterns in one level");
                 cap <<= 2;
                 rs.qp_grows += 1;
                 continue;
             }
-            if (ew & ~FSM_ERR_POOL) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
-            if (ew & FSM_ERR_POOL) {
-                fused = false;   // pool too small: the separate domain pass decides
+            if (ew & ~(FSM_ERR_POOL | FSM_ERR_CODE_FULL))
+                fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+            if (ew) {
+                // pool or pattern table too small: the one-pass level stopped early; count again
+                // in a clean count pass and fill the domains in a domain pass
+                fused = false;
                 G->pool_hint[L] = 0;
-                ck(cudaMemsetAsync(G->err, 0, sizeof(int), st), "memset");
-            } else if (fused) {
-                G->pool_hint[L] = d2h(ptop, st);
+                rs.fused_fallbacks += 1;
+                release_pass1();
+                continue;
             }
+            if (fused) G->pool_hint[L] = d2h(ptop, st);
             break;
         }
         unsigned long long st2[3];
@@ -637,36 +657,43 @@ struct Miner {
         int64_t *woff = mem.get<int64_t>(np * 8 + 1);
         int64_t *doff = mem.get<int64_t>(np * 8);
         void *stmp2 = mem.get<char>((int64_t)scan_temp_bytes(np * 8) + 16);
-        ck(launch_domain_sizes(K, plab, orbit, minorb, pcount, np, t_live, G->cls_size, live, words, st), "domain sizes");
-        ck(launch_scan_i64(words, woff, np * 8, stmp2, st), "domain scan");
-        ck(launch_domain_offsets(words, woff, np * 8, doff, st), "domain offsets");
-        const int64_t nwords = d2h(woff + np * 8, st);
-        uint32_t *dom = mem.get<uint32_t>(nwords);
-        ck(cudaMemsetAsync(dom, 0, sizeof(uint32_t) * std::max<int64_t>(nwords, 1), st), "memset");
+        unsigned long long *sigma = mem.get<unsigned long long>(np);
+        ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
+        uint32_t *dom = nullptr;
+        int64_t *sbase = nullptr;
         rs.patterns = np;
-        // live pattern count (for statistics)
-        std::vector<uint8_t> hl((size_t)np);
-        if (np) {
-            ck(cudaMemcpyAsync(hl.data(), live, (size_t)np, cudaMemcpyDeviceToHost, st), "copy");
-            ck(cudaStreamSynchronize(st), "sync");
-        }
-        rs.live = std::count(hl.begin(), hl.end(), (uint8_t)1);
-        // ---- pass 2: MNI domains (Definition 2)
-        A.qp.pattern = qpat;
-        A.qp.perm = qperm;
-        A.live = live;
-        A.orbit = orbit;
-        A.dom_off = doff;
-        A.dom = dom;
-        int64_t *sbase = mem.get<int64_t>(cap * 8);
-        ck(launch_slot_bases(K, slots, nq, qpat, qperm, live, orbit, doff, sbase, st), "slot bases");
-        A.slot_base = sbase;
-        A.stats = nullptr;
-        if (rs.live > 0) {
-            if (fused) {
-                ck(launch_merge_domains(K, slots, nq, qpat, qperm, qdom, pool, live, orbit, doff, words, dom, st),
-                   "merge domains");
-            } else {
+        if (fused) {
+            // every pattern has its orbit bitmaps in the pool already: MNI from there
+            rs.live = np;
+            ck(launch_fused_support(K, plab, padj, orbit, np, ckeys, coff, (uint64_t)cap - 1, G->cls_size, pool, sigma,
+                                    st), "fused support");
+            if (G->profile) rs.pass_bytes[L][PASS_FUSED] += rs.final_accepted * 4 * K;   // one bitmap word per position
+        } else {
+            ck(launch_domain_sizes(K, plab, orbit, minorb, pcount, np, t_live, G->cls_size, live, words, st), "domain sizes");
+            ck(launch_scan_i64(words, woff, np * 8, stmp2, st), "domain scan");
+            ck(launch_domain_offsets(words, woff, np * 8, doff, st), "domain offsets");
+            const int64_t nwords = d2h(woff + np * 8, st);
+            dom = mem.get<uint32_t>(nwords);
+            ck(cudaMemsetAsync(dom, 0, sizeof(uint32_t) * std::max<int64_t>(nwords, 1), st), "memset");
+            // live pattern count (for statistics)
+            std::vector<uint8_t> hl((size_t)np);
+            if (np) {
+                ck(cudaMemcpyAsync(hl.data(), live, (size_t)np, cudaMemcpyDeviceToHost, st), "copy");
+                ck(cudaStreamSynchronize(st), "sync");
+            }
+            rs.live = std::count(hl.begin(), hl.end(), (uint8_t)1);
+            // ---- pass 2: MNI domains (Definition 2)
+            A.qp.pattern = qpat;
+            A.qp.perm = qperm;
+            A.live = live;
+            A.orbit = orbit;
+            A.dom_off = doff;
+            A.dom = dom;
+            sbase = mem.get<int64_t>(cap * 8);
+            ck(launch_slot_bases(K, slots, nq, qpat, qperm, live, orbit, doff, sbase, st), "slot bases");
+            A.slot_base = sbase;
+            A.stats = nullptr;
+            if (rs.live > 0) {
                 tune_chunk(in, A);
                 run_pass(PASS_DOMAIN, in, A, pat_off);
                 if (G->profile) {
@@ -682,14 +709,12 @@ struct Miner {
                     rs.pass_bytes[L][PASS_DOMAIN] += joins * 4 * K;
                 }
             }
+            ck(launch_support(K, orbit, live, doff, words, dom, np, sigma, st), "support");
         }
         if (pool) {
             mem.release(pool);
             pool = nullptr;
         }
-        unsigned long long *sigma = mem.get<unsigned long long>(np);
-        ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
-        ck(launch_support(K, orbit, live, doff, words, dom, np, sigma, st), "support");
         float *feat = nullptr;
         if (sampled && np > 0) {
             int64_t *aut = mem.get<int64_t>(np);
@@ -706,7 +731,7 @@ struct Miner {
         ck(launch_scan_i64(fflag, fscan, np, stmp2, st), "frequent scan");
         ck(launch_new_ids(fflag, fscan, np, newid, st), "new ids");
         const int64_t nf = d2h(fscan + np, st);
-                mem.release(dom);
+        if (dom) mem.release(dom);
         // ---- frequent patterns of size K
         out.P = nf;
         out.lab8 = mem.get<uint64_t>(nf);
@@ -748,9 +773,9 @@ struct Miner {
         }
         const int ew = err_word();
         if (ew) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
-        if (qdom) mem.release(qdom);
-        mem.release(sbase);
-        for (void *p : std::initializer_list<void *>{keys, qcount, used, slots, nq_d, qpat, qperm, flag, ids, stmp, plab,
+        if (sbase) mem.release(sbase);
+        release_pass1();
+        for (void *p : std::initializer_list<void *>{slots, nq_d, qpat, qperm, flag, ids, stmp, plab,
                                                      padj, orbit, minorb, pcount, live, words, woff, doff, stmp2, sigma,
                                                      fflag, fscan, newid})
             mem.release(p);
@@ -1306,6 +1331,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["recount_frontier"] = rs.recount_frontier;
         r->stats["sampled_edges"] = rs.sampled_edges;
         r->stats["qp_grows"] = rs.qp_grows;
+        r->stats["fused_fallbacks"] = rs.fused_fallbacks;
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["chunk_l" + std::to_string(L)] = g->tuned_chunk[L];
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["pieces_l" + std::to_string(L)] = rs.pieces_l[L];
         const char *pn[4] = {"count", "domain", "emit", "fused"};

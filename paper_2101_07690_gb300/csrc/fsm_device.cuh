@@ -31,7 +31,8 @@
 #define FSM_ERR_QP_MISSING   2   // a key seen in a later pass was not in the table
 #define FSM_ERR_BOUNDS       4   // an index check failed
 #define FSM_ERR_CSR          8   // malformed CSR found by validation
-#define FSM_ERR_POOL        16   // the fused pass ran out of per-key bitmap pool: domain pass instead
+#define FSM_ERR_POOL        16   // the one-pass last level ran out of bitmap pool: two passes instead
+#define FSM_ERR_CODE_FULL   32   // the one-pass last level's pattern table is full: two passes instead
 
 namespace fsm {
 

@@ -17,16 +17,17 @@
 //   PASS_COUNT   insert the key into the quick-pattern table and count it;
 //   PASS_DOMAIN  set the MNI domain bits of its pattern's orbits (Definition 2);
 //   PASS_EMIT    write it, permuted into canonical order, to the next frontier;
-//   PASS_FUSED   (last level) count it and set the bits of its vertices in bitmaps kept per
-//                (quick-pattern key, local position), allocated on first use from a pool;
-//                after canonicalisation they are merged into the patterns' orbit bitmaps, so
-//                the last level is enumerated once instead of twice.
+//   PASS_FUSED   (last level, k <= 7) count it and set the MNI domain bits of its pattern's
+//                orbits in the same enumeration: the lane that first meets a quick pattern
+//                canonicalises it, claims its pattern's orbit bitmaps (one CAS on the pattern's
+//                entry in a table of canonical codes) and publishes the bitmap word offset of
+//                every local position; nothing waits on another lane.
 //
 // Scheduling: the pieces of a batch of units form one index space [0, total) (exclusive prefix
 // `unit_base`); warps take fixed-size chunks of it from an atomic counter, so hub vertices
 // with millions of pieces are split across many warps and light units share a warp.
 #pragma once
-#include "fsm_device.cuh"
+#include "fsm_canon.cuh"
 
 namespace fsm {
 
@@ -74,12 +75,20 @@ struct ExtArgs {
     int64_t out_N;
     unsigned long long *out_cursor;
     unsigned long long *stats;     // [0] joins tested, [1] joins accepted, [2] pieces enumerated
-    // fused pass: per-key bitmaps (offset + 1 into pool, 0 = none) and their pool
-    unsigned long long *qp_dom;    // [cap * 8]
+    // one-pass last level (PASS_FUSED): a table of canonical codes (packed by pack_code) with the
+    // pool word offset + 1 of each pattern's orbit bitmaps (0 = not yet claimed), and the bitmap
+    // word offset of every (key slot, local position), -1 until published
+    const uint64_t *pat_lab;       // [P] 8 label bytes of the size-l patterns
+    unsigned long long *code_keys; // [code_mask + 1], FSM_EMPTY_KEY when free
+    unsigned long long *code_off;  // [code_mask + 1]
+    uint64_t code_mask;
+    long long *slot_off;           // [cap * 8]
     uint32_t *pool;
     unsigned long long *pool_top;
     unsigned long long pool_words;
     const int32_t *cls_size;
+    int explore;                   // exploration variant (quick-pattern key layout)
+    int level;                     // L, the size of the embeddings extended
     // sampled last level (pieces come from the kept edges in g.prow / g.pcol)
     int sampled;
     // sampling quotas (variant FSM_EXPLORE_TV_QUOTA): candidate pieces per unit (0 = all) and,
@@ -258,6 +267,79 @@ __device__ __forceinline__ void flush_warp_counts(const ExtArgs &A, CountCache *
     __syncwarp();
 }
 
+// ---- one-pass last level: publication of per-slot bitmap offsets (gpu-scope release/acquire)
+__device__ __forceinline__ long long ld_acquire_s64(const long long *p) {
+    long long v;
+    asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ long long ld_relaxed_s64(const long long *p) {
+    long long v;
+    asm volatile("ld.relaxed.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_s64(long long *p, long long v) {
+    asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_relaxed_s64(long long *p, long long v) {
+    asm volatile("st.relaxed.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// First sight of a quick pattern in the one-pass last level: canonicalise the graph its key
+// denotes, find or claim its pattern's entry in the code table, claim the pattern's orbit
+// bitmaps from the pool unless another lane already did (one CAS decides; a loser's pool words
+// stay unused), and publish the bitmap word offset of each local position -- position 0 last,
+// with release semantics, so a reader that sees it set sees the others.  Lanes racing on one key
+// compute and write the same values.  On a full table or pool the error word says so and nothing
+// is published; the host then runs the last level as two passes.
+struct ResolveArgs {
+    const uint64_t *pat_lab, *pat_adj;
+    const int32_t *cls_size;
+    unsigned long long *code_keys, *code_off, *pool_top;
+    uint64_t code_mask;
+    unsigned long long pool_words;
+    long long *slot_off;
+    int *err;
+    int explore, level;
+};
+
+static __device__ __noinline__ void resolve_slot(const ResolveArgs A, int64_t slot, uint64_t key) {
+    int K, lab[FSM_MAXK], rep[FSM_MAXK];
+    uint32_t adj[FSM_MAXK];
+    key_graph(A.explore, A.level, key, A.pat_lab, A.pat_adj, K, lab, adj);
+    unsigned long long clab;
+    uint32_t cadj, inv;
+    canonicalise(K, lab, adj, clab, cadj, inv);
+    orbit_reps(K, clab, cadj, rep);
+    int64_t pre[FSM_MAXK], words = 0;
+    for (int c = 0; c < K; ++c) {
+        pre[c] = words;
+        if (rep[c] == c) words += ((int64_t)__ldg(A.cls_size + ((clab >> (8 * (7 - c))) & 0xff)) + 31) / 32;
+    }
+    const uint64_t pk = pack_code(K, clab, cadj);
+    uint64_t h = mix64(pk) & A.code_mask;
+    int64_t ci = -1;
+    for (int probe = 0; probe < FSM_MAX_PROBES; ++probe) {
+        unsigned long long cur = __ldcg(A.code_keys + h);
+        if (cur == FSM_EMPTY_KEY) cur = atomicCAS(A.code_keys + h, FSM_EMPTY_KEY, pk);
+        if (cur == FSM_EMPTY_KEY || cur == pk) { ci = (int64_t)h; break; }
+        h = (h + 1) & A.code_mask;
+    }
+    if (ci < 0) { atomicOr(A.err, FSM_ERR_CODE_FULL); return; }
+    unsigned long long off = __ldcg(A.code_off + ci);
+    if (off == 0ull) {
+        const unsigned long long res = atomicAdd(A.pool_top, (unsigned long long)words);
+        if (res + (unsigned long long)words > A.pool_words) { atomicOr(A.err, FSM_ERR_POOL); return; }
+        const unsigned long long old = atomicCAS(A.code_off + ci, 0ull, res + 1ull);
+        off = old ? old : res + 1ull;
+    }
+    long long *so = A.slot_off + slot * 8;
+    for (int hh = K - 1; hh >= 0; --hh) {
+        const long long v = (long long)(off - 1ull) + pre[rep[(inv >> (3 * hh)) & 7]];
+        if (hh) st_relaxed_s64(so + hh, v); else st_release_s64(so, v);
+    }
+}
+
 // One accepted join: act according to PASS.
 // Per-lane memory of bitmap words already set (PASS_DOMAIN, PASS_FUSED): the last word of a piece
 // vertex with its bits, and per position of s the last bitmap offset set for it (valid within
@@ -279,31 +361,43 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
         return;
     }
     if (PASS == PASS_FUSED) {
+        // count the key (warp-aggregated), then set its orbits' bits as the domain pass does
         const unsigned act = __activemask();
         const unsigned grp = __match_any_sync(act, key);
         const int lane = threadIdx.x & 31;
         const int leader = __ffs(grp) - 1;
         long long slot = -1;
-        if (lane == leader) slot = count_key_slot(A, cc, key, __popc(grp));
-        slot = __shfl_sync(grp, slot, leader);
-        if (slot < 0) return;   // table overflow: the pass is repeated with a larger table
-#pragma unroll
-        for (int h = 0; h < K; ++h) {
-            unsigned long long *pp = A.qp_dom + slot * 8 + h;
-            unsigned long long off = *(volatile unsigned long long *)pp;
-            if (off == 0ull) {
-                const int lab = __ldg(A.g.labels + gid[h]);
-                const unsigned long long words = ((unsigned long long)__ldg(A.cls_size + lab) + 31ull) / 32ull;
-                const unsigned long long res = atomicAdd(A.pool_top, words);
-                if (res + words > A.pool_words) { atomicOr(A.err, FSM_ERR_POOL); return; }
-                const unsigned long long old = atomicCAS(pp, 0ull, res + 1ull);
-                off = old ? old : res + 1ull;
+        if (lane == leader) {
+            slot = count_key_slot(A, cc, key, __popc(grp));
+            if (slot >= 0 && ld_acquire_s64(A.slot_off + slot * 8) < 0) {
+                const ResolveArgs R{A.pat_lab, A.pat_adj, A.cls_size, A.code_keys, A.code_off, A.pool_top,
+                                    A.code_mask, A.pool_words, A.slot_off, A.err, A.explore, A.level};
+                resolve_slot(R, slot, key);
             }
+        }
+        slot = __shfl_sync(grp, slot, leader);
+        __syncwarp(grp);
+        if (slot < 0) return;   // table overflow: the pass is repeated with a larger table
+        const long long *so = A.slot_off + slot * 8;
+        const long long o0 = ld_acquire_s64(so);
+        if (o0 < 0) return;     // pool or code table full (flagged): the level is redone in two passes
+#pragma unroll
+        for (int h = 0; h < L; ++h) {
+            const long long off = h ? ld_relaxed_s64(so + h) : o0;
+            if (off == dc.soff[h]) continue;
+            dc.soff[h] = off;
+            uint32_t *w = A.pool + off + (rk[h] >> 5);
+            const uint32_t bit = 1u << (rk[h] & 31);
+            if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+        }
+#pragma unroll
+        for (int h = L; h < K; ++h) {
+            const long long off = ld_relaxed_s64(so + h);
             const int32_t r = __ldg(A.g.rank + gid[h]);
-            uint32_t *w = A.pool + (off - 1ull) + (r >> 5);
+            uint32_t *w = A.pool + off + (r >> 5);
             const uint32_t bit = 1u << (r & 31);
             if (w == dc.w && (dc.bits & bit)) continue;
-            if (!(__ldcg(w) & bit)) atomicOr(w, bit);
+            atomicOr(w, bit);
             if (w != dc.w) { dc.w = w; dc.bits = 0; }
             dc.bits |= bit;
         }
@@ -792,7 +886,9 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
         unsigned long long c = 0;
         if (lane == 0) {
             // an overflowing count pass is repeated with a larger table: stop early
-            if ((PASS == PASS_COUNT || PASS == PASS_FUSED) && (*(volatile int *)A.err & FSM_ERR_QP_OVERFLOW)) c = ~0ull;
+            if ((PASS == PASS_COUNT && (*(volatile int *)A.err & FSM_ERR_QP_OVERFLOW)) ||
+                (PASS == PASS_FUSED && *(volatile int *)A.err))
+                c = ~0ull;
             else c = atomicAdd(A.chunk_ctr, 1ull);
         }
         c = __shfl_sync(0xffffffffu, c, 0);
@@ -863,7 +959,7 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
                     S[p] = __ldg(A.fv + (int64_t)p * A.fN + e);
                     SL[p] = __ldg(A.g.labels + S[p]);
                     SR[p] = make_int2(__ldg(A.g.row_ptr + S[p]), __ldg(A.g.row_ptr + S[p] + 1));
-                    RK[p] = PASS == PASS_DOMAIN ? __ldg(A.g.rank + S[p]) : 0;
+                    RK[p] = (PASS == PASS_DOMAIN || PASS == PASS_FUSED) ? __ldg(A.g.rank + S[p]) : 0;
                 }
                 pid = __ldg(A.fpid + e);
                 srows = L >= 2 ? __ldg(A.pat_adj + pid) : 0ull;

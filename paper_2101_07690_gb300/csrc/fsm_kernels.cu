@@ -1,6 +1,7 @@
 // fsm_kernels.cu -- graph preparation, scans, quick-pattern bookkeeping, canonicalisation,
 // orbits, MNI domains and supports, and the size-1 / size-2 base levels.
 #include "fsm_kernels.cuh"
+#include "fsm_canon.cuh"
 
 #include <climits>
 
@@ -352,119 +353,6 @@ cudaError_t launch_qp_compact(const unsigned long long *keys, int64_t cap, int64
 
 namespace {
 
-__device__ __forceinline__ bool next_perm(int *a, int n) {
-    int i = n - 2;
-    while (i >= 0 && a[i] >= a[i + 1]) --i;
-    if (i < 0) {
-        for (int l = 0, r = n - 1; l < r; ++l, --r) { int t = a[l]; a[l] = a[r]; a[r] = t; }
-        return false;
-    }
-    int j = n - 1;
-    while (a[j] <= a[i]) --j;
-    int t = a[i]; a[i] = a[j]; a[j] = t;
-    for (int l = i + 1, r = n - 1; l < r; ++l, --r) { t = a[l]; a[l] = a[r]; a[r] = t; }
-    return true;
-}
-
-// Advance perm to the next permutation that keeps every position's label (positions with equal
-// labels form contiguous segments seg_start[c]..); false after the last one.
-__device__ __forceinline__ bool next_label_perm(int K, const int *seg_start, int *perm) {
-    int c = K - 1;
-    while (c >= 0) {
-        const int s = seg_start[c];
-        if (c - s + 1 >= 2 && next_perm(perm + s, c - s + 1)) return true;
-        c = s - 1;
-    }
-    return false;
-}
-
-__device__ __forceinline__ uint32_t adj_code(int K, const uint32_t *adj, const int *perm) {
-    uint32_t code = 0;
-    for (int c1 = 0; c1 < K; ++c1) {
-        const uint32_t row = adj[perm[c1]];
-        for (int c2 = c1 + 1; c2 < K; ++c2) code = (code << 1) | ((row >> perm[c2]) & 1u);
-    }
-    return code;
-}
-
-// Canonical code of a labeled K-vertex graph: the smallest (label sequence, adjacency
-// sequence) over all vertex orders.  The smallest label sequence is the sorted one, so only
-// label-preserving orders of the sorted positions are enumerated.  inv[h] = canonical
-// position of vertex h in the first optimal order.
-__device__ void canonicalise(int K, const int *lab, const uint32_t *adj, unsigned long long &clab,
-                             uint32_t &cadj, uint32_t &inv) {
-    int perm[FSM_MAXK], seg[FSM_MAXK], best[FSM_MAXK];
-    for (int h = 0; h < K; ++h) perm[h] = h;
-    for (int a = 1; a < K; ++a)          // insertion sort by label (stable)
-        for (int b = a; b > 0 && lab[perm[b - 1]] > lab[perm[b]]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
-    for (int c = 0; c < K; ++c) seg[c] = (c > 0 && lab[perm[c]] == lab[perm[c - 1]]) ? seg[c - 1] : c;
-    // within each segment start from ascending vertex index (next_perm enumerates from there)
-    for (int c = 0; c < K; ++c)
-        for (int b = c; b > seg[c] && perm[b - 1] > perm[b]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
-    uint32_t bc = 0xffffffffu;
-    do {
-        const uint32_t code = adj_code(K, adj, perm);
-        if (code < bc) {
-            bc = code;
-            for (int c = 0; c < K; ++c) best[c] = perm[c];
-        }
-    } while (next_label_perm(K, seg, perm));
-    unsigned long long l = 0;
-    for (int c = 0; c < K; ++c) l |= (unsigned long long)(lab[best[c]] & 0xff) << (8 * (7 - c));
-    uint32_t iv = 0;
-    for (int c = 0; c < K; ++c) iv |= (uint32_t)c << (3 * best[c]);
-    clab = l;
-    cadj = bc;
-    inv = iv;
-}
-
-// The labeled graph a quick-pattern key denotes, in the key's local vertex order (the order the
-// extension kernel's accept step uses for that key's positions).
-__device__ void key_graph(int V, int L, uint64_t key, const uint64_t *pat_lab8, const uint64_t *pat_adj8, int &K,
-                          int *labH, uint32_t *adjH) {
-    if (V == FSM_EXPLORE_TV_EDGELIST) {
-        // labels and edges listed over the vertices in ascending id order
-        K = L + 2;
-        int bit = 42;
-        for (int a = 0; a < K; ++a) adjH[a] = 0;
-        for (int a = 0; a < K; ++a) {
-            labH[a] = (int)(key >> (6 * a)) & 63;
-            for (int b = a + 1; b < K; ++b, ++bit)
-                if ((key >> bit) & 1ull) { adjH[a] |= 1u << b; adjH[b] |= 1u << a; }
-        }
-        return;
-    }
-    uint32_t pid, pidx, cross;
-    int i, jpos;
-    split_key(key, pid, pidx, i, jpos, cross);
-    const uint64_t lab8 = pat_lab8[pid], srows = pat_adj8[pid];
-    for (int h = 0; h < L; ++h) labH[h] = (int)(lab8 >> (8 * h)) & 0xff;
-    if (V == FSM_EXPLORE_SV) {
-        // <pid(s), label(a), i, cross bits>: a joined to s[i] and to the cross positions
-        K = L + 1;
-        for (int h = 0; h < L; ++h) adjH[h] = (uint32_t)(srows >> (8 * h)) & 0xffu;
-        labH[L] = (int)(pidx & 63);
-        adjH[L] = 1u << i;
-        adjH[i] |= 1u << L;
-        for (int p = 0; p < L; ++p) {
-            if (p == i || !((cross >> (p < i ? p : p - 1)) & 1u)) continue;
-            adjH[p] |= 1u << L;
-            adjH[L] |= 1u << p;
-        }
-        return;
-    }
-    K = L + 2;
-    const int shape = (int)(pidx >> 18);
-    const int pl[3] = {(int)(pidx >> 12) & 63, (int)(pidx >> 6) & 63, (int)pidx & 63};
-    const int q0 = jpos == 0 ? 1 : 0;
-    const int q1 = jpos == 2 ? 1 : 2;
-    labH[L] = pl[q0];
-    labH[L + 1] = pl[q1];
-    uint32_t tj0, tj1, txx;
-    piece_join_edges(shape, jpos, tj0, tj1, txx);
-    join_graph(L, srows, i, tj0, tj1, txx, cross, adjH);
-}
-
 __global__ void qp_canon_kernel(int L, int V, const unsigned long long *keys, const int64_t *slots, int64_t nq,
                                 const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
                                 uint32_t *perm_out) {
@@ -518,15 +406,6 @@ __global__ void assign_kernel(const CodeRec *r, int64_t n, const int64_t *slots,
         qp_pattern[slots[r[t].idx]] = (int32_t)pid;
         if (flag[t]) { pat_lab[pid] = r[t].lab; pat_adj[pid] = r[t].adj; }
     }
-}
-
-__device__ __forceinline__ void decode_code(int K, unsigned long long clab, uint32_t cadj, int *lab, uint32_t *adj) {
-    const int np = K * (K - 1) / 2;
-    for (int c = 0; c < K; ++c) { lab[c] = (int)(clab >> (8 * (7 - c))) & 0xff; adj[c] = 0; }
-    int q = 0;
-    for (int c1 = 0; c1 < K; ++c1)
-        for (int c2 = c1 + 1; c2 < K; ++c2, ++q)
-            if ((cadj >> (np - 1 - q)) & 1u) { adj[c1] |= 1u << c2; adj[c2] |= 1u << c1; }
 }
 
 __global__ void orbits_kernel(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
@@ -1352,40 +1231,56 @@ cudaError_t launch_decide(const float *pred, int64_t np, float logt, float delta
 }
 
 namespace {
-__global__ void merge_domains_kernel(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
-                                     const uint32_t *qp_perm, const unsigned long long *qp_dom, const uint32_t *pool,
-                                     const uint8_t *live, const uint64_t *orbit, const int64_t *dom_off,
-                                     const int64_t *words, uint32_t *dom) {
+// MNI support of each pattern from the one-pass last level's orbit bitmaps: the pattern's entry
+// in the code table gives its bitmap block; orbit representatives (ascending canonical
+// position) hold ceil(|V_label| / 32) words each, in that order.  One warp per pattern.
+__global__ void fused_support_kernel(int K, const unsigned long long *plab, const uint32_t *padj, const uint64_t *orbit,
+                                     int64_t np, const unsigned long long *ckeys, const unsigned long long *coff,
+                                     uint64_t cmask, const int32_t *cls_size, const uint32_t *pool,
+                                     unsigned long long *sigma) {
     const int lane = threadIdx.x & 31;
-    const int64_t nw = nq * K;
-    for (int64_t w = gtid() >> 5; w < nw; w += gstride() >> 5) {
-        const int64_t slot = slots[w / K];
-        const int h = (int)(w % K);
-        const int32_t P = qp_pattern[slot];
-        if (!live[P]) continue;
-        const unsigned long long off = qp_dom[slot * 8 + h];
-        if (off == 0ull) continue;
-        const int c = (int)((qp_perm[slot] >> (3 * h)) & 7u);
-        const int o = (int)((orbit[P] >> (8 * c)) & 0xff);
-        uint32_t *dst = dom + dom_off[(int64_t)P * 8 + o];
-        const uint32_t *src = pool + (off - 1ull);
-        const int64_t n = words[(int64_t)P * 8 + o];
-        for (int64_t x = lane; x < n; x += 32) {
-            const uint32_t v = src[x];
-            if (v) atomicOr(dst + x, v);
+    for (int64_t P = gtid() >> 5; P < np; P += gstride() >> 5) {
+        const uint64_t pk = pack_code(K, plab[P], padj[P]);
+        uint64_t h = mix64(pk) & cmask;
+        int64_t ci = -1;
+        for (uint64_t probe = 0; probe <= cmask; ++probe) {
+            const unsigned long long cur = ckeys[h];
+            if (cur == pk) { ci = (int64_t)h; break; }
+            if (cur == FSM_EMPTY_KEY) break;
+            h = (h + 1) & cmask;
         }
+        if (ci < 0 || coff[ci] == 0ull) {   // cannot happen: every key was resolved before use
+            if (lane == 0) sigma[P] = 0;
+            continue;
+        }
+        const uint64_t off = coff[ci] - 1ull;
+        uint64_t pre = 0;
+        unsigned long long mn = ~0ull;
+        for (int c = 0; c < K; ++c) {
+            if ((int)((orbit[P] >> (8 * c)) & 0xff) != c) continue;
+            const int lab = (int)((plab[P] >> (8 * (7 - c))) & 0xff);
+            const uint64_t nw = ((uint64_t)cls_size[lab] + 31) / 32;
+            unsigned long long cnt = 0;
+            for (uint64_t x = lane; x < nw; x += 32) cnt += __popc(pool[off + pre + x]);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            if (cnt < mn) mn = cnt;
+            pre += nw;
+        }
+        if (lane == 0) sigma[P] = mn;
     }
 }
+
 } // namespace
 
-cudaError_t launch_merge_domains(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
-                                 const uint32_t *qp_perm, const unsigned long long *qp_dom, const uint32_t *pool,
-                                 const uint8_t *live, const uint64_t *orbit, const int64_t *dom_off,
-                                 const int64_t *words, uint32_t *dom, cudaStream_t st) {
-    if (nq <= 0) return cudaSuccess;
+cudaError_t launch_fused_support(int K, const unsigned long long *plab, const uint32_t *padj, const uint64_t *orbit,
+                                 int64_t np, const unsigned long long *ckeys, const unsigned long long *coff,
+                                 uint64_t cmask, const int32_t *cls_size, const uint32_t *pool, unsigned long long *sigma,
+                                 cudaStream_t st) {
+    if (np <= 0) return cudaSuccess;
     LAUNCHED(1);
-    merge_domains_kernel<<<blocks_for(nq * K * 32), kThreads, 0, st>>>(K, slots, nq, qp_pattern, qp_perm, qp_dom, pool,
-                                                                       live, orbit, dom_off, words, dom);
+    fused_support_kernel<<<blocks_for(np * 32), kThreads, 0, st>>>(K, plab, padj, orbit, np, ckeys, coff, cmask, cls_size,
+                                                                   pool, sigma);
     return cudaGetLastError();
 }
 

@@ -185,12 +185,12 @@ cudaError_t launch_keep_counts(const unsigned long long *count, const uint8_t *k
 cudaError_t launch_decide(const float *pred, int64_t np, float logt, float delta, uint8_t *keep, uint8_t *uncertain,
                           cudaStream_t st);
 
-// Fused last level: OR each live pattern's per-key bitmaps (qp_dom: offset + 1 into pool per
-// (slot, local position)) into the pattern's orbit bitmaps; one warp per (key, position).
-cudaError_t launch_merge_domains(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
-                                 const uint32_t *qp_perm, const unsigned long long *qp_dom, const uint32_t *pool,
-                                 const uint8_t *live, const uint64_t *orbit, const int64_t *dom_off,
-                                 const int64_t *words, uint32_t *dom, cudaStream_t st);
+// MNI supports from the one-pass last level: sigma[P] = the smallest orbit popcount of pattern
+// P's bitmap block, found through its entry in the code table (ckeys / coff, cmask + 1 slots)
+cudaError_t launch_fused_support(int K, const unsigned long long *plab, const uint32_t *padj, const uint64_t *orbit,
+                                 int64_t np, const unsigned long long *ckeys, const unsigned long long *coff,
+                                 uint64_t cmask, const int32_t *cls_size, const uint32_t *pool, unsigned long long *sigma,
+                                 cudaStream_t st);
 
 // Domain pass helper: for every distinct key (slot) and local position h, the word offset of
 // the bitmap its vertex goes to (the orbit of canonical position perm[h] of its pattern), or -1

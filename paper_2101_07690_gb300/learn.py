@@ -58,12 +58,32 @@ def compare(exact: dict, got: dict) -> dict:
             "exact_patterns": len(exact), "returned": len(got)}
 
 
+def quota_rows(G, k: int, t: int, exact: dict, quotas, seed: int = 1) -> list:
+    """Section 5's own sampling (ST x: x^2 candidate pieces per key group, x edges per key vertex
+    when edges are joined) on an open graph handle, for each x: time, and precision, recall and
+    median support error against the exact frequent set.  The drawn supports are lower bounds,
+    so precision is 1 by construction."""
+    import time
+    rows = []
+    G.set_option("model", 0)
+    G.set_option("seed", seed)
+    for x in quotas:
+        G.set_option("join_quota", int(x))
+        t0 = time.perf_counter()
+        r = G.mine(k, t)
+        row = {"join_quota": int(x), "seconds": time.perf_counter() - t0}
+        row.update(compare(exact, frequent_set(r, k)))
+        rows.append(row)
+    G.set_option("join_quota", 0)
+    return rows
+
+
 def study(workload: str, k: int, t: int, p: float, train_scale: float, train_seeds, cap, test_scale: float = 1.0,
-          test_cap=None, deltas=(0.0, 0.1, 0.25, 0.5), epochs: int = 200, seed: int = 1) -> dict:
+          test_cap=None, deltas=(0.0, 0.1, 0.25, 0.5), epochs: int = 200, seed: int = 1, quotas=()) -> dict:
     """Train on copies of a workload (other seeds), then mine the test graph exactly, with the
-    plain sampled estimator, and with the learned decision plus exact recount for each recount
-    band delta; report time and accuracy of each against the exact result, and the network's
-    error on held-out training pairs."""
+    plain sampled estimator, with the learned decision plus exact recount for each recount band
+    delta, and with Section 5's quotas ST x for each x in quotas; report time and accuracy of
+    each against the exact result, and the network's error on held-out training pairs."""
     import time
 
     import graphgen as gg
@@ -107,6 +127,9 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
                    "recounted": int(r["stats"]["recount_patterns"]), "exactly_counted": int(r["exact"].sum())}
             row.update(compare(exact, frequent_set(r, k)))
             out["learned"].append(row)
+        G.set_option("delta_milli", 500)
+        if quotas:
+            out["quota"] = quota_rows(G, k, t, exact, quotas, seed=seed)
         G.close()
         return out
     finally:
@@ -128,7 +151,10 @@ if __name__ == "__main__":
     ap.add_argument("--test-cap", type=float, default=300)
     ap.add_argument("--deltas", default="0,0.05,0.1,0.25,0.5")
     ap.add_argument("--epochs", type=int, default=200)
+    ap.add_argument("--quotas", default="", help="Section 5 ST x values to compare, e.g. 2,4,8")
+    ap.add_argument("--test-scale", type=float, default=1.0)
     a = ap.parse_args()
     lo, hi = (int(x) for x in a.train_seeds.split("-"))
     print(json.dumps(study(a.workload, a.k, a.t, a.p, a.train_scale, range(lo, hi + 1), a.cap,
-                           test_cap=a.test_cap, deltas=[float(x) for x in a.deltas.split(",")], epochs=a.epochs)))
+                           test_scale=a.test_scale, test_cap=a.test_cap, deltas=[float(x) for x in a.deltas.split(",")],
+                           epochs=a.epochs, quotas=[int(x) for x in a.quotas.split(",") if x])))

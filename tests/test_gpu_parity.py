@@ -313,3 +313,21 @@ def test_ablation_counters(fsm):
             assert np.array_equal(r[key], ref[key])
     assert el["stats"]["quick_patterns"] > ref["stats"]["quick_patterns"]
     assert ref["stats"]["levels"] == 2 and sv["stats"]["levels"] == 3
+
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+def test_one_pass_last_level(fsm, mode):
+    """Option fused = 1: the last level counted and its domains filled in one enumeration, with
+    quick patterns canonicalised on first sight in the kernel -- the oracle's result, also when
+    a small bitmap pool forces the count-and-domain fallback."""
+    for g, k, t in [(_hub_graph(), 5, 40), (gg.workload("er1000"), 5, 10), (gg.workload("er1000"), 3, 30),
+                    (gg.erdos_renyi(40, 2.5, seed=7, num_labels=2), 7, 2), (gg.workload("cl100k", scale=0.005, cap=30), 4, 6)]:
+        for launch in (0, 1, 2):
+            check(fsm, g, k, t, mode, {"fused": 1, "launch": launch})
+    G = fsm.Graph.from_graphgen(_hub_graph(), mode)
+    G.set_option("fused", 1)
+    G.set_option("fused_pool", 64)
+    got = G.mine(5, 40, stats=True)
+    G.close()
+    assert got["stats"]["fused_fallbacks"] >= 1
+    _same(got, oracle_at(_hub_graph(), 5, 40, mode), "fused fallback")
