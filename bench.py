@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--launch", type=int, default=1, choices=[0, 1, 2],
                    help="0 batched, 1 persistent work-stealing (CUDA graph), 2 one launch per pattern")
     p.add_argument("--autotune", type=int, default=1, choices=[0, 1])
+    p.add_argument("--fused", type=int, default=1, choices=[0, 1],
+                   help="1: the last level counted and its domains filled in one enumeration; 0: two passes")
     return p.parse_args()
 
 
@@ -270,6 +272,7 @@ def time_to_solution(args, fsm):
     o = oracle.mine(g, args.k, t, args.mode)
     o_s = time.perf_counter() - t0
     G = fsm.Graph.from_graphgen(g, args.mode)
+    G.set_option("fused", args.fused)
     G.mine(args.k, t)   # first call: lazy set-up
     t0 = time.perf_counter()
     r = G.mine(args.k, t)
@@ -296,6 +299,7 @@ def run_ours(args, rank, world, local_rank):
     G.set_option("stream", stream.cuda_stream)
     G.set_option("launch", args.launch)
     G.set_option("autotune", args.autotune)
+    G.set_option("fused", args.fused)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
     last = {}
 
@@ -372,6 +376,7 @@ def run_ours(args, rank, world, local_rank):
             h = fsm.fsm_load_graph(rp.data_ptr(), cl.data_ptr(), lb.data_ptr(), g.n, g.num_labels)
             fsm.fsm_set_option(h, "mode", 0 if args.mode == "edge" else 1)
             fsm.fsm_set_option(h, "launch", args.launch)
+            fsm.fsm_set_option(h, "fused", args.fused)
             for t in ths:
                 r = fsm.fsm_mine(h, args.k, t)
                 out = fsm.fsm_result_copy(r, args.k)
@@ -419,7 +424,8 @@ def run_ours(args, rank, world, local_rank):
                 "data": "synthetic (seeded Chung-Lu graph of the named shape)",
                 "config": dict(workload_config(args, g), parallelism=f"replicas{world}",
                                launch={0: "batched", 1: "persistent", 2: "per-pattern"}[args.launch],
-                               autotune=bool(args.autotune)),
+                               autotune=bool(args.autotune),
+                               last_level="one pass (count + domains)" if args.fused else "count pass + domain pass"),
                 "e2e": e2e, "gpu_launches": int(agg["kernel_launches"]),
                 "embeddings_per_step": int(agg["embeddings"] // args.steps),
                 "patterns_per_step": int(agg["patterns_out"] // args.steps),

@@ -123,7 +123,7 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *                table runs out, the level is counted again and finished in two passes (stat
  *                "fused_fallbacks").
  *   "fused_pool" size in 32-bit words of the one-pass level's bitmap pool (0 = twice what the
- *                previous call used, else 40% of the free device memory, at most 2^32 words).
+ *                previous call used, else 40% of the free device memory).
  *   "seed"       64-bit seed of the piece sampling of fsm_mine with sample_rate < 1 (default 0).
  *   "candidates" 1 = sampled mining returns every candidate pattern of the sampled level with
  *                its estimated support (smallest orbit popcount / p) and its 32 features
@@ -134,6 +134,14 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *   "delta_milli" recount band of sampled mining with a model, in thousandths of a natural log
  *                unit (default 500): patterns with |log prediction - log t| <= delta are
  *                recounted exactly.
+ *   "debug"      1 = the extension kernels check every decoded list index against its list
+ *                before reading; a failed check sets the call's error word and skips the read (no
+ *                trap), and the call returns FSM_ECUDA; 0 = off (default).
+ *   "time_limit_ms" > 0: the extension kernels stop taking work once this much device time has
+ *                passed since the call started (checked at every work chunk) and the call returns
+ *                FSM_ETIMEOUT with no result; the handle stays usable; 0 = no limit (default).
+ *   "fail_alloc_after" test hook: > 0 makes the call's n-th device allocation report failure, so
+ *                the call returns FSM_ENOMEM (everything it allocated is released); 0 = off.
  *   "profile"    1 = time every extension-kernel launch with CUDA events and sum its algorithmic
  *                bytes (reported by fsm_result_stat); adds one synchronisation per launch.
  * Unknown keys or out-of-range values give FSM_EINVAL.
@@ -238,6 +246,9 @@ const char *fsm_last_error(void);
  *   fsm_mlp_set_params / fsm_mlp_get_params   copy the 6337 master weights in / out (set also
  *                        resets Adam's moments).
  *   fsm_mlp_set_norm     input means and standard deviations (32 each, deviations > 0).
+ *   fsm_mlp_fit_norm     the same, computed on the device from X[n][32]: column means and
+ *                        population standard deviations (accumulated in double), deviations
+ *                        floored at 1e-3.
  *   fsm_mlp_gradients    mean squared error over X[n][32], Y[n] and its gradient (6337 floats).
  *   fsm_mlp_train        epochs of shuffled minibatches (order from a splitmix64 stream of seed),
  *                        Adam (beta 0.9, 0.999, eps 1e-8) at rate lr; final_loss = last epoch's
@@ -249,6 +260,7 @@ int fsm_mlp_create(uint64_t seed, fsm_mlp **out);
 int fsm_mlp_set_params(fsm_mlp *m, const float *params);
 int fsm_mlp_get_params(const fsm_mlp *m, float *params);
 int fsm_mlp_set_norm(fsm_mlp *m, const float *mean, const float *stdev);
+int fsm_mlp_fit_norm(fsm_mlp *m, const float *X, int64_t n);
 int fsm_mlp_gradients(fsm_mlp *m, const float *X, const float *Y, int64_t n, float *grads, float *loss);
 int fsm_mlp_train(fsm_mlp *m, const float *X, const float *Y, int64_t n, int32_t epochs, int32_t batch,
                   float lr, uint64_t seed, float *final_loss);

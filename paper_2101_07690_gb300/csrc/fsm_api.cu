@@ -70,12 +70,15 @@ void keep_pool(int dev) {
 struct Arena {
     cudaStream_t st;
     std::vector<void *> ptrs;
+    int64_t made = 0, fail_at = 0;   // fail_at > 0: the fail_at-th allocation reports failure (test hook)
     explicit Arena(cudaStream_t s) : st(s) {}
     template <class T>
     T *get(int64_t n) {
         void *p = nullptr;
         size_t bytes = (size_t)std::max<int64_t>(n, 1) * sizeof(T);
         bytes = (bytes + 255) & ~(size_t)255;
+        if (fail_at > 0 && ++made == fail_at)
+            fail(FSM_ENOMEM, "device allocation: injected failure (option fail_alloc_after)");
         ck(cudaMallocAsync(&p, bytes, st), "device allocation");
         ptrs.push_back(p);
         return (T *)p;
@@ -150,6 +153,9 @@ struct fsm_graph {
     int64_t qp_initial = 0;               // option "qp_capacity": first quick-pattern table size (0 = 2^20)
     int explore = 0;                      // option "explore": 0 two-vertex (the method), 1 single-vertex
     int quick_pattern = 0;                // option "quick_pattern": 0 index-based, 1 edge list
+    int debug = 0;                        // option "debug": device bounds checks on decoded indices
+    int64_t time_limit_ms = 0;            // option "time_limit_ms": FSM_ETIMEOUT past it (0 = none)
+    int64_t fail_alloc_after = 0;         // option "fail_alloc_after": injected allocation failure
     int64_t join_quota = 0;               // option "join_quota": ST x of Section 5 (0 = off)
     int64_t match_quota = 0;              // option "match_quota": M.ST of Section 5 (0 = off)
     int autotune = 0;
@@ -458,6 +464,14 @@ struct Miner {
 
     int err_word() { return d2h(G->err, st); }
 
+    // Fail with the code a kernel's error word stands for (after the recoverable bits are handled)
+    [[noreturn]] void fail_word(int ew) {
+        if (ew & FSM_ERR_TIMEOUT)
+            fail(FSM_ETIMEOUT, "time limit of " + std::to_string(G->time_limit_ms) + " ms ran out (option time_limit_ms)");
+        if (ew & FSM_ERR_BOUNDS) fail(FSM_ECUDA, "a device bounds check failed (error word " + std::to_string(ew) + ")");
+        fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+    }
+
     // Extend `in` (size L) to size L+2.  piece_freq == nullptr at the size-3 level.
     // sampled: join only pieces kept by the splitmix64 rule at rate p; every candidate pattern
     // is returned with its sampled support and count and its 32 features.
@@ -477,6 +491,9 @@ struct Miner {
         A.piece_sel = piece_sel;
         A.err = G->err;
         A.sampled = sampled ? 1 : 0;
+        A.debug = G->debug;
+        A.time_limit_ns = (uint64_t)G->time_limit_ms * 1000000ull;
+        A.time_start = G->stats + 4;
         if (V == FSM_EXPLORE_TV_QUOTA) {
             // Section 5: size-3 matching (l = 1) draws match_quota candidates per vertex; every
             // join draws join_quota^2 pieces per key group and, joining edges, join_quota edges
@@ -522,8 +539,8 @@ struct Miner {
         if (fused) {
             size_t fr = 0, tot = 0;
             ck(cudaMemGetInfo(&fr, &tot), "memory info");
-            // twice what the last call needed, else 40% of the free memory, at most 2^32 words
-            const unsigned long long cap_words = (unsigned long long)std::min<size_t>(fr / 4 * 2 / 5, (size_t)1 << 32);
+            // twice what the last call needed, else 40% of the free memory
+            const unsigned long long cap_words = (unsigned long long)(fr / 4 * 2 / 5);
             pool_words = G->pool_hint[L] ? std::min(cap_words, 2 * G->pool_hint[L] + (1ull << 22)) : cap_words;
             pool_words = std::max<unsigned long long>(pool_words, 1ull << 20);
             if (G->pool_force) pool_words = G->pool_force;
@@ -593,6 +610,7 @@ struct Miner {
             }
             run_pass(fused ? PASS_FUSED : PASS_COUNT, in, A, pat_off);
             const int ew = err_word();
+            if (ew & (FSM_ERR_TIMEOUT | FSM_ERR_BOUNDS)) fail_word(ew);
             if (ew & FSM_ERR_QP_OVERFLOW) {
                 release_pass1();
                 if (cap >= ((int64_t)1 << 31)) fail(FSM_EUNSUPPORTED, "more than 2^30 distinct quick patterns in one level");
@@ -600,8 +618,7 @@ struct Miner {
                 rs.qp_grows += 1;
                 continue;
             }
-            if (ew & ~(FSM_ERR_POOL | FSM_ERR_CODE_FULL))
-                fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+            if (ew & ~(FSM_ERR_POOL | FSM_ERR_CODE_FULL)) fail_word(ew);
             if (ew) {
                 // pool or pattern table too small: the one-pass level stopped early; count again
                 // in a clean count pass and fill the domains in a domain pass
@@ -772,7 +789,7 @@ struct Miner {
             mem.release(cursor);
         }
         const int ew = err_word();
-        if (ew) fail(FSM_ECUDA, "extension kernel reported error word " + std::to_string(ew));
+        if (ew) fail_word(ew);
         if (sbase) mem.release(sbase);
         release_pass1();
         for (void *p : std::initializer_list<void *>{slots, nq_d, qpat, qperm, flag, ids, stmp, plab,
@@ -1169,6 +1186,15 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value) {
         } else if (k == "chunk") {
             if (value != 0 && (value < 32 || value > 65536 || (value & (value - 1)))) fail(FSM_EINVAL, "chunk must be 0 or a power of two in [32, 65536]");
             g->chunk = (int32_t)value;
+        } else if (k == "debug") {
+            if (value != 0 && value != 1) fail(FSM_EINVAL, "debug must be 0 or 1");
+            g->debug = (int)value;
+        } else if (k == "time_limit_ms") {
+            if (value < 0) fail(FSM_EINVAL, "time_limit_ms must be >= 0");
+            g->time_limit_ms = value;
+        } else if (k == "fail_alloc_after") {
+            if (value < 0) fail(FSM_EINVAL, "fail_alloc_after must be >= 0");
+            g->fail_alloc_after = value;
         } else if (k == "join_quota") {
             if (value < 0 || value > 65536) fail(FSM_EINVAL, "join_quota must be in [0, 65536]");
             g->join_quota = value;
@@ -1229,6 +1255,8 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r = new fsm_result();
         {
             Arena mem(st);
+            mem.fail_at = g->fail_alloc_after;
+            ck(launch_stamp_time(g->stats + 4, st), "time stamp");
             Miner m{g, st, mem, min_support, rs};
             m.V = V;
             if (g->profile) {

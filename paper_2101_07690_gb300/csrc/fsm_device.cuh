@@ -33,6 +33,7 @@
 #define FSM_ERR_CSR          8   // malformed CSR found by validation
 #define FSM_ERR_POOL        16   // the one-pass last level ran out of bitmap pool: two passes instead
 #define FSM_ERR_CODE_FULL   32   // the one-pass last level's pattern table is full: two passes instead
+#define FSM_ERR_TIMEOUT     64   // the call's time limit ran out (option "time_limit_ms")
 
 namespace fsm {
 

@@ -96,8 +96,17 @@ struct ExtArgs {
     int64_t quota;
     int64_t edge_quota;
     uint64_t qseed;
+    int debug;                     // option "debug": bounds-check decoded indices, flag and skip
+    uint64_t time_limit_ns;        // option "time_limit_ms" in ns (0 = none), from *time_start
+    const unsigned long long *time_start;   // the call's start on the device's global timer
     int *err;
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ int64_t last_le(const int64_t *base, int64_t lo, int64_t hi, int64_t x) {
     // largest u in [lo, hi] with base[u] <= x (base[lo] <= x assumed)
@@ -366,35 +375,46 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
         const unsigned grp = __match_any_sync(act, key);
         const int lane = threadIdx.x & 31;
         const int leader = __ffs(grp) - 1;
-        long long slot = -1;
+        // the leader counts the key, resolves it on first sight, and reads its offsets once; the
+        // lanes of the group receive them by shuffle
+        long long off[K];
+#pragma unroll
+        for (int h = 0; h < K; ++h) off[h] = -1;
         if (lane == leader) {
-            slot = count_key_slot(A, cc, key, __popc(grp));
-            if (slot >= 0 && ld_acquire_s64(A.slot_off + slot * 8) < 0) {
-                const ResolveArgs R{A.pat_lab, A.pat_adj, A.cls_size, A.code_keys, A.code_off, A.pool_top,
-                                    A.code_mask, A.pool_words, A.slot_off, A.err, A.explore, A.level};
-                resolve_slot(R, slot, key);
+            const long long slot = count_key_slot(A, cc, key, __popc(grp));
+            if (slot >= 0) {
+                const long long *so = A.slot_off + slot * 8;
+                long long o0 = ld_acquire_s64(so);
+                if (o0 < 0) {
+                    const ResolveArgs R{A.pat_lab, A.pat_adj, A.cls_size, A.code_keys, A.code_off, A.pool_top,
+                                        A.code_mask, A.pool_words, A.slot_off, A.err, A.explore, A.level};
+                    resolve_slot(R, slot, key);
+                    o0 = ld_acquire_s64(so);
+                }
+                if (o0 >= 0) {
+                    off[0] = o0;
+#pragma unroll
+                    for (int h = 1; h < K; ++h) off[h] = ld_relaxed_s64(so + h);
+                }
             }
         }
-        slot = __shfl_sync(grp, slot, leader);
-        __syncwarp(grp);
-        if (slot < 0) return;   // table overflow: the pass is repeated with a larger table
-        const long long *so = A.slot_off + slot * 8;
-        const long long o0 = ld_acquire_s64(so);
-        if (o0 < 0) return;     // pool or code table full (flagged): the level is redone in two passes
+#pragma unroll
+        for (int h = 0; h < K; ++h) off[h] = __shfl_sync(grp, off[h], leader);
+        // table overflow (the pass is repeated with a larger table), or pool or code table full
+        // (the level is redone in two passes): nothing to set
+        if (off[0] < 0) return;
 #pragma unroll
         for (int h = 0; h < L; ++h) {
-            const long long off = h ? ld_relaxed_s64(so + h) : o0;
-            if (off == dc.soff[h]) continue;
-            dc.soff[h] = off;
-            uint32_t *w = A.pool + off + (rk[h] >> 5);
+            if (off[h] == dc.soff[h]) continue;
+            dc.soff[h] = off[h];
+            uint32_t *w = A.pool + off[h] + (rk[h] >> 5);
             const uint32_t bit = 1u << (rk[h] & 31);
             if (!(__ldcg(w) & bit)) atomicOr(w, bit);
         }
 #pragma unroll
         for (int h = L; h < K; ++h) {
-            const long long off = ld_relaxed_s64(so + h);
             const int32_t r = __ldg(A.g.rank + gid[h]);
-            uint32_t *w = A.pool + off + (r >> 5);
+            uint32_t *w = A.pool + off[h] + (r >> 5);
             const uint32_t bit = 1u << (r & 31);
             if (w == dc.w && (dc.bits & bit)) continue;
             atomicOr(w, bit);
@@ -692,6 +712,7 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
             }
         }
         xb = y;
+        if (A.debug && (xa < 0 || xa >= y || y >= d)) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
         a = __ldg(g.pcol + rp + xa);
         b = __ldg(g.pcol + rp + y);
         if (L == 1 && a < v) return;                 // size-3 subgraphs keyed at their smallest vertex
@@ -716,7 +737,15 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
         ecur = lo;
         xa = lo;
         xb = -1;
+        if (A.debug && (lo < 0 || lo >= d)) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
         a = __ldg(g.pcol + rp + lo);
+        if (A.debug) {
+            const int64_t r = lq2 - __ldg(g.pend + rp + lo);
+            if (a < 0 || a >= g.n || r < 0 || r >= (int64_t)(__ldg(g.prow + a + 1) - __ldg(g.prow + a))) {
+                atomicOr(A.err, FSM_ERR_BOUNDS);
+                return;
+            }
+        }
         b = __ldg(g.pcol + __ldg(g.prow + a) + (int32_t)(lq2 - __ldg(g.pend + rp + lo)));
         if (b == v) return;
         if (L == 1 && (a < v || b < v)) return;
@@ -799,6 +828,7 @@ __device__ __forceinline__ void do_edge(const ExtArgs &A, const int32_t (&S)[L],
                                         const uint32_t *mk, const int32_t (&RK)[L]) {
     constexpr int K = L + 1;
     const int32_t v = S[i];
+    if (A.debug && (lq < 0 || lq >= __ldg(A.g.prow + v + 1) - __ldg(A.g.prow + v))) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
     const int32_t a = __ldg(A.g.pcol + __ldg(A.g.prow + v) + (int32_t)lq);
     if (in_s<L>(S, a)) return;
     uint32_t avail = 0;   // bit p' (p != i, p' = p minus one if p > i): a ~ s[p]
@@ -885,11 +915,16 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
     for (;;) {
         unsigned long long c = 0;
         if (lane == 0) {
-            // an overflowing count pass is repeated with a larger table: stop early
-            if ((PASS == PASS_COUNT && (*(volatile int *)A.err & FSM_ERR_QP_OVERFLOW)) ||
-                (PASS == PASS_FUSED && *(volatile int *)A.err))
-                c = ~0ull;
-            else c = atomicAdd(A.chunk_ctr, 1ull);
+            // stop early when the call ran out of time, when an overflowing count pass is to be
+            // repeated with a larger table, or when a one-pass level is to be redone in two passes
+            const int ew = *(volatile int *)A.err;
+            bool stop = (ew & FSM_ERR_TIMEOUT) || (PASS == PASS_COUNT && (ew & FSM_ERR_QP_OVERFLOW)) ||
+                        (PASS == PASS_FUSED && ew);
+            if (!stop && A.time_limit_ns && global_ns() - __ldcg(A.time_start) > A.time_limit_ns) {
+                atomicOr(A.err, FSM_ERR_TIMEOUT);
+                stop = true;
+            }
+            c = stop ? ~0ull : atomicAdd(A.chunk_ctr, 1ull);
         }
         c = __shfl_sync(0xffffffffu, c, 0);
         if (c >= (unsigned long long)nchunks) break;

@@ -928,12 +928,13 @@ __global__ void by_rank_kernel(const DevGraph g, const int64_t *cls_off, int32_t
 
 // one warp per (pattern, canonical position): popcount and mean log1p(degree) of the orbit's
 // sampled domain; lane 0 of the position-0 warp also writes the scalars
-__global__ void features_kernel(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj,
-                                const uint64_t *orbit, const int64_t *dom_off, const int64_t *words,
-                                const uint32_t *dom, const unsigned long long *pat_count,
-                                const int32_t *cls_size, const int64_t *cls_off, const int32_t *by_rank,
-                                const int32_t *row_ptr, int32_t n, float logp, float p, int64_t t,
-                                int64_t np, const int64_t *aut, float *feat) {
+// Features, per (pattern, canonical position) warp: the label frequency of the position and the
+// mean log1p(degree) over the sampled domain of its orbit; the orbit's popcount goes to pop[].
+__global__ void features_pos_kernel(int K, const unsigned long long *pat_lab, const uint64_t *orbit,
+                                    const int64_t *dom_off, const int64_t *words, const uint32_t *dom,
+                                    const int32_t *cls_size, const int64_t *cls_off, const int32_t *by_rank,
+                                    const int32_t *row_ptr, int32_t n, int64_t np, unsigned long long *pop,
+                                    float *feat) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = np * 8;
     for (int64_t w = gtid() >> 5; w < nw; w += gstride() >> 5) {
@@ -941,7 +942,7 @@ __global__ void features_kernel(int K, const unsigned long long *pat_lab, const 
         const int c = (int)(w & 7);
         float *f = feat + P * 32;
         if (c >= K) {
-            if (lane == 0) { f[8 + c] = 0.f; f[16 + c] = 0.f; }
+            if (lane == 0) { f[8 + c] = 0.f; f[16 + c] = 0.f; pop[w] = 0; }
             continue;
         }
         const int o = (int)((orbit[P] >> (8 * c)) & 0xff);
@@ -967,16 +968,23 @@ __global__ void features_kernel(int K, const unsigned long long *pat_lab, const 
         if (lane != 0) continue;
         f[8 + c] = logf((float)cls_size[lab] / (float)n);
         f[16 + c] = cnt ? sdeg / (float)cnt : 0.f;
-        if (c != 0) continue;
-        // orbit popcounts ascending (recount the representatives' bitmaps)
+        pop[w] = cnt;
+    }
+}
+
+// Features, per pattern: the orbits' popcounts ascending (from pop[] at each orbit's
+// representative) and the pattern-level entries.
+__global__ void features_pat_kernel(int K, const uint32_t *pat_adj, const uint64_t *orbit,
+                                    const unsigned long long *pat_count, int32_t n, float logp, float p, int64_t t,
+                                    int64_t np, const int64_t *aut, const unsigned long long *pop, float *feat) {
+    for (int64_t P = gtid(); P < np; P += gstride()) {
+        float *f = feat + P * 32;
         float pc[8];
         int m = 0;
         unsigned long long mn = ~0ull;
-        for (int cc = 0; cc < K; ++cc) {
-            if ((int)((orbit[P] >> (8 * cc)) & 0xff) != cc) continue;
-            const int64_t o2 = dom_off[P * 8 + cc], n2 = words[P * 8 + cc];
-            unsigned long long q = 0;
-            for (int64_t x = 0; x < n2; ++x) q += __popc(dom[o2 + x]);
+        for (int c = 0; c < K; ++c) {
+            if ((int)((orbit[P] >> (8 * c)) & 0xff) != c) continue;
+            const unsigned long long q = pop[P * 8 + c];
             if (q < mn) mn = q;
             pc[m++] = log1pf((float)q);
         }
@@ -1082,11 +1090,17 @@ cudaError_t launch_features(int K, const unsigned long long *pat_lab, const uint
                             const int32_t *by_rank, const int32_t *row_ptr, int32_t n, double p, int64_t t,
                             int64_t np, const int64_t *aut, float *feat, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
-    LAUNCHED(1);
-    features_kernel<<<blocks_for(np * 8 * 32), kThreads, 0, st>>>(K, pat_lab, pat_adj, orbit, dom_off, words, dom,
-                                                                  pat_count, cls_size, cls_off, by_rank, row_ptr, n,
-                                                                  (float)log(p), (float)p, t, np, aut, feat);
-    return cudaGetLastError();
+    unsigned long long *pop = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&pop, sizeof(unsigned long long) * (size_t)np * 8, st);
+    if (e != cudaSuccess) return e;
+    LAUNCHED(2);
+    features_pos_kernel<<<blocks_for(np * 8 * 32), kThreads, 0, st>>>(K, pat_lab, orbit, dom_off, words, dom, cls_size,
+                                                                      cls_off, by_rank, row_ptr, n, np, pop, feat);
+    features_pat_kernel<<<blocks_for(np), kThreads, 0, st>>>(K, pat_adj, orbit, pat_count, n, (float)log(p), (float)p,
+                                                             t, np, aut, pop, feat);
+    e = cudaGetLastError();
+    cudaFreeAsync(pop, st);
+    return e;
 }
 
 namespace {
@@ -1322,4 +1336,20 @@ cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *ad
     return cudaGetLastError();
 }
 
+} // namespace fsm
+
+namespace fsm {
+namespace {
+__global__ void stamp_time_kernel(unsigned long long *out) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    *out = t;
+}
+} // namespace
+
+cudaError_t launch_stamp_time(unsigned long long *out, cudaStream_t st) {
+    LAUNCHED(1);
+    stamp_time_kernel<<<1, 1, 0, st>>>(out);
+    return cudaGetLastError();
+}
 } // namespace fsm

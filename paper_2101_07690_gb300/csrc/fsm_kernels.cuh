@@ -185,6 +185,9 @@ cudaError_t launch_keep_counts(const unsigned long long *count, const uint8_t *k
 cudaError_t launch_decide(const float *pred, int64_t np, float logt, float delta, uint8_t *keep, uint8_t *uncertain,
                           cudaStream_t st);
 
+// *out = the device's global timer (ns), in stream order: the start of a call's time limit
+cudaError_t launch_stamp_time(unsigned long long *out, cudaStream_t st);
+
 // MNI supports from the one-pass last level: sigma[P] = the smallest orbit popcount of pattern
 // P's bitmap block, found through its entry in the code table (ckeys / coff, cmask + 1 slots)
 cudaError_t launch_fused_support(int K, const unsigned long long *plab, const uint32_t *padj, const uint64_t *orbit,

@@ -290,6 +290,56 @@ int fsm_mlp_set_norm(fsm_mlp *M, const float *mean, const float *stdev) {
     return e == cudaSuccess ? FSM_OK : mlp_fail(FSM_ECUDA, cudaGetErrorString(e));
 }
 
+// Input standardisation from data: one block per input column, mean then the mean squared
+// deviation (population), both accumulated in double; stdev floored at 1e-3.
+__global__ void fit_norm_kernel(const float *X, int64_t n, float *mu, float *sd) {
+    __shared__ double part[256];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)X[i * MLP_IN + c];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double mean = part[0] / (double)n;
+    __syncthreads();
+    double q = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double d = (double)X[i * MLP_IN + c] - mean;
+        q += d * d;
+    }
+    part[threadIdx.x] = q;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        mu[c] = (float)mean;
+        sd[c] = (float)fmax(sqrt(part[0] / (double)n), 1e-3);
+    }
+}
+
+static int mlp_upload(const float *X, const float *Y, int64_t n, float **dX, float **dY);
+
+int fsm_mlp_fit_norm(fsm_mlp *M, const float *X, int64_t n) {
+    if (!M || !X || n < 1) return mlp_fail(FSM_EINVAL, "NULL argument or n < 1");
+    float *dX = nullptr;
+    int rc = mlp_upload(X, nullptr, n, &dX, nullptr);
+    if (rc == FSM_OK) {
+        fit_norm_kernel<<<MLP_IN, 256>>>(dX, n, M->mu, M->sd);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) rc = mlp_fail(FSM_ECUDA, cudaGetErrorString(e));
+    } else {
+        rc = mlp_fail(rc, "could not stage the inputs on the device");
+    }
+    cudaFree(dX);
+    return rc;
+}
+
 static int mlp_upload(const float *X, const float *Y, int64_t n, float **dX, float **dY) {
     *dX = nullptr;
     if (dY) *dY = nullptr;

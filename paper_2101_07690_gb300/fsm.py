@@ -28,7 +28,7 @@ EXPORTS = ["fsm_load_graph", "fsm_set_option", "fsm_mine", "fsm_result_count", "
            "fsm_result_embeddings", "fsm_result_copy", "fsm_result_stat", "fsm_free_result",
            "fsm_free_graph", "fsm_last_error", "fsm_debug_dissect", "fsm_edge_supports_noalloc",
            "fsm_result_exact", "fsm_result_features", "fsm_mlp_create", "fsm_mlp_set_params",
-           "fsm_mlp_get_params", "fsm_mlp_set_norm", "fsm_mlp_gradients", "fsm_mlp_train",
+           "fsm_mlp_get_params", "fsm_mlp_set_norm", "fsm_mlp_fit_norm", "fsm_mlp_gradients", "fsm_mlp_train",
            "fsm_mlp_predict", "fsm_mlp_predict_device", "fsm_mlp_free"]
 
 MLP_NPARAM = 32 * 64 + 64 + 64 * 64 + 64 + 64 + 1
@@ -74,6 +74,7 @@ def load(path: str | None = None):
         "fsm_mlp_set_params": (ctypes.c_int, [vp, P(ctypes.c_float)]),
         "fsm_mlp_get_params": (ctypes.c_int, [vp, P(ctypes.c_float)]),
         "fsm_mlp_set_norm": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float)]),
+        "fsm_mlp_fit_norm": (ctypes.c_int, [vp, P(ctypes.c_float), i64]),
         "fsm_mlp_gradients": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float), i64, P(ctypes.c_float),
                                              P(ctypes.c_float)]),
         "fsm_mlp_train": (ctypes.c_int, [vp, P(ctypes.c_float), P(ctypes.c_float), i64, i32, i32, ctypes.c_float,
@@ -236,6 +237,11 @@ def fsm_mlp_get_params(m: int) -> np.ndarray:
 def fsm_mlp_set_norm(m: int, mean, stdev) -> None:
     mu, sd = _f32(mean).reshape(32), _f32(stdev).reshape(32)
     _check(load().fsm_mlp_set_norm(m, _ptr(mu, ctypes.c_float), _ptr(sd, ctypes.c_float)))
+
+
+def fsm_mlp_fit_norm(m: int, X) -> None:
+    X = _f32(X).reshape(-1, 32)
+    _check(load().fsm_mlp_fit_norm(m, _ptr(X, ctypes.c_float), len(X)))
 
 
 def fsm_mlp_gradients(m: int, X, Y):

@@ -36,9 +36,7 @@ def training_pairs(graph, k: int, t: int, p: float, seed: int = 0, mode: str = "
 def fit(X, y, epochs: int = 300, batch: int = 256, lr: float = 3e-3, seed: int = 0):
     """A trained network handle (free with fsm.fsm_mlp_free)."""
     m = fsm.fsm_mlp_create(seed)
-    mean = X.mean(axis=0)
-    sd = np.maximum(X.std(axis=0), 1e-3)
-    fsm.fsm_mlp_set_norm(m, mean, sd)
+    fsm.fsm_mlp_fit_norm(m, X)   # input standardisation, computed by the library
     fsm.fsm_mlp_train(m, X, y, epochs, batch, lr, seed)
     return m
 

@@ -1,5 +1,5 @@
 """Parity at full size, in the launch configuration bench.py times (persistent launch,
-autotuned chunks), on two workloads:
+autotuned chunks, one-pass last level on the benchmark workload), on two workloads:
 
 * the 3.7M-vertex Chung-Lu graph (16.5M edges, beta 2.3, 37 Zipf(1.0) labels, degree cap 20),
   k = 5, t = 20000 -- the benchmark workload;
@@ -10,8 +10,9 @@ The oracle cannot enumerate 1e10 embeddings, so sampled output patterns (the sma
 and a random draw of light ones) are recomputed one by one by the oracle's pattern matcher
 (support and embedding count, exactly), patterns one label edit away from the output are
 checked to be really infrequent, and properties that hold at any size are checked on the whole
-output: identical results from one launch per frontier pattern, sorted unique rows, supports
-reaching t, and anti-monotone supports against the k = 3 output."""
+output: identical results from one launch per frontier pattern with the other last-level form
+(two passes against one), sorted unique rows, supports reaching t, and anti-monotone supports
+against the k = 3 output."""
 import itertools
 
 import numpy as np
@@ -24,8 +25,8 @@ pytestmark = pytest.mark.gpu
 
 MAX_MAPS = 3_000_000
 WORKLOADS = {
-    "cl3700k_cap20_k5": dict(name="cl3700k", cap=20, k=5, t=20000),
-    "cl100k_cap300_k4": dict(name="cl100k", cap=300, k=4, t=300),
+    "cl3700k_cap20_k5": dict(name="cl3700k", cap=20, k=5, t=20000, fused=1),
+    "cl100k_cap300_k4": dict(name="cl100k", cap=300, k=4, t=300, fused=0),
 }
 
 
@@ -42,9 +43,12 @@ def mined(request):
     G = fsm.Graph.from_graphgen(g)
     G.set_option("launch", 1)
     G.set_option("autotune", 1)
+    G.set_option("fused", w["fused"])
     r = G.mine(w["k"], w["t"], stats=True)
     r3 = G.mine(3, w["t"])
+    # the other launch mode and the other last-level form must agree
     G.set_option("launch", 2)
+    G.set_option("fused", 1 - w["fused"])
     r2 = G.mine(w["k"], w["t"])
     G.close()
     return g, w["k"], w["t"], r, r3, r2
@@ -112,7 +116,7 @@ def test_neighbouring_patterns_absent_are_infrequent(mined):
 
 def test_properties_of_the_whole_output(mined):
     g, K, T, r, r3, r2 = mined
-    # identical with one launch per frontier pattern
+    # identical with one launch per frontier pattern and the other last-level form
     for key in ("labels", "adj", "support", "count"):
         assert np.array_equal(r[key], r2[key])
     # supports reach t, labels nondecreasing, rows sorted by (labels, adjacency sequence)

@@ -331,3 +331,46 @@ def test_one_pass_last_level(fsm, mode):
     G.close()
     assert got["stats"]["fused_fallbacks"] >= 1
     _same(got, oracle_at(_hub_graph(), 5, 40, mode), "fused fallback")
+
+
+def test_debug_option_keeps_results(fsm):
+    """Option debug = 1 bounds-checks every decoded list index in the kernels (flag and skip,
+    never trap); on valid input nothing trips and the result is the oracle's."""
+    for g, k, t in [(gg.workload("er1000"), 4, 10), (_hub_graph(), 5, 40)]:
+        for opts in ({"debug": 1, "launch": 1}, {"debug": 1, "explore": 1}, {"debug": 1, "fused": 1}):
+            check(fsm, g, k, t, "edge", opts)
+
+
+def test_time_limit_returns_etimeout_and_the_handle_recovers(fsm):
+    """A call past option time_limit_ms stops taking work at the next chunk and returns
+    FSM_ETIMEOUT; the same handle then mines normally."""
+    g = gg.workload("cl100k", cap=100)
+    G = fsm.Graph.from_graphgen(g)
+    G.set_option("launch", 1)
+    G.set_option("time_limit_ms", 20)
+    with pytest.raises(fsm.FsmError) as e:
+        G.mine(5, 300)
+    assert e.value.code == fsm.FSM_ETIMEOUT
+    G.set_option("time_limit_ms", 0)
+    after = G.mine(4, 300)
+    G.close()
+    H = fsm.Graph.from_graphgen(g)
+    H.set_option("launch", 1)
+    fresh = H.mine(4, 300)
+    H.close()
+    for key in ("labels", "adj", "support", "count"):
+        assert np.array_equal(after[key], fresh[key])
+
+
+def test_injected_allocation_failure_returns_enomem(fsm):
+    g = gg.workload("er1000")
+    G = fsm.Graph.from_graphgen(g)
+    for n in (1, 5, 20, 40):
+        G.set_option("fail_alloc_after", n)
+        with pytest.raises(fsm.FsmError) as e:
+            G.mine(4, 10)
+        assert e.value.code == fsm.FSM_ENOMEM, n
+    G.set_option("fail_alloc_after", 0)
+    got = G.mine(4, 10)
+    G.close()
+    _same(got, oracle_at(g, 4, 10), "after injected allocation failures")

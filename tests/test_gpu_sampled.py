@@ -214,3 +214,23 @@ def test_learned_sampling_recounts_exactly_and_beats_the_plain_estimator(fsm):
         assert f1_m >= f1_p and rec_m >= rec_p
     finally:
         fsm.fsm_mlp_free(m)
+
+
+def test_fit_norm_matches_the_standardisation_of_the_data(fsm):
+    """fsm_mlp_fit_norm computes the input means and (population) standard deviations on the
+    device, floored at 1e-3: predictions equal those of a network given numpy's."""
+    rng = np.random.default_rng(12)
+    X = rng.normal(3.0, 2.0, (5000, 32)).astype(np.float32)
+    X[:, 7] = 1.5   # a constant column: deviation floored
+    theta = rng.normal(0, 0.25, ref.NPARAM).astype(np.float32)
+    a, b = fsm.fsm_mlp_create(1), fsm.fsm_mlp_create(1)
+    try:
+        for m in (a, b):
+            fsm.fsm_mlp_set_params(m, theta)
+        fsm.fsm_mlp_fit_norm(a, X)
+        x64 = X.astype(np.float64)
+        fsm.fsm_mlp_set_norm(b, x64.mean(axis=0), np.maximum(x64.std(axis=0), 1e-3))
+        assert np.allclose(fsm.fsm_mlp_predict(a, X), fsm.fsm_mlp_predict(b, X), rtol=1e-4, atol=1e-4)
+    finally:
+        fsm.fsm_mlp_free(a)
+        fsm.fsm_mlp_free(b)
