@@ -57,12 +57,16 @@ def parse_args():
     p.add_argument("--autotune", type=int, default=1, choices=[0, 1])
     p.add_argument("--fused", type=int, default=1, choices=[0, 1],
                    help="1: the last level counted and its domains filled in one enumeration; 0: two passes")
+    p.add_argument("--fused-pool", type=int, default=0,
+                   help="bitmap pool of the one-pass last level in 32-bit words (0: sized by the library)")
+    p.add_argument("--scale", type=float, default=1.0,
+                   help="graph scale (n and m shrink together; for small profiler captures, not bench lines)")
     return p.parse_args()
 
 
 def workload_graph(args):
     import graphgen as gg
-    return gg.workload(args.workload, cap=args.cap if args.cap else None)
+    return gg.workload(args.workload, scale=args.scale, cap=args.cap if args.cap else None)
 
 
 def workload_config(args, g):
@@ -70,7 +74,7 @@ def workload_config(args, g):
                         f"labels={g.num_labels} {g.meta.get('label_law')}({g.meta.get('zipf_s')}) "
                         f"seed={g.meta.get('seed')} cap={round(float(g.meta.get('cap')), 1)}",
             "k": args.k, "thresholds": [int(x) for x in args.thresholds.split(",")], "mode": args.mode,
-            "d_max": int(g.degrees().max()), "graph_hash": g.content_hash(),
+            "d_max": int(g.degrees().max()), "graph_hash": g.content_hash(), **({"scale": args.scale} if args.scale != 1.0 else {}),
             "l2": "flushed before every timed step (256 MiB write)"}
 
 
@@ -300,6 +304,7 @@ def run_ours(args, rank, world, local_rank):
     G.set_option("launch", args.launch)
     G.set_option("autotune", args.autotune)
     G.set_option("fused", args.fused)
+    G.set_option("fused_pool", args.fused_pool)
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device="cuda")
     last = {}
 

@@ -214,7 +214,9 @@ int fsm_result_features(const fsm_result *r, float *features);
  *   extended level size l = 1..6), "candidates" (joins
  *   tested), "embeddings" (accepted joins, all levels),
  *   "final_embeddings" (accepted joins of the last level), "qp_grows" (quick-pattern table
- *   overflows, each a grown table and a repeated pass), "quick_patterns" (distinct index
+ *   overflows, each a grown table and a repeated pass), "fused_fallbacks" (one-pass last levels
+ *   redone in two passes), "fused_pool_words" (bitmap pool words the one-pass level used),
+ *   "quick_patterns" (distinct index
  *   based quick patterns, i.e. canonicalisations, all levels), "patterns" (distinct patterns
  *   of the last level), "live_patterns" (last-level patterns given a domain),
  *   "frontier_max" (largest stored level), "kernel_launches", "time_ns" (device time of the

@@ -229,6 +229,7 @@ struct RunStats {
     int64_t recount_patterns = 0, recount_frontier = 0, candidates_sampled = 0, sampled_edges = 0;
     int64_t qp_grows = 0;                  // quick-pattern table overflows (table grown x4, pass repeated)
     int64_t fused_fallbacks = 0;           // one-pass last levels redone as two passes (pool or table full)
+    int64_t fused_pool_words = 0;          // bitmap pool words the one-pass last level used
     int64_t pieces_l[FSM_MAXL + 1] = {};   // pieces enumerated by the count pass, per extended level size
     double pass_ns[FSM_MAXL + 1][4] = {};
     int64_t pass_launches[FSM_MAXL + 1][4] = {}, pass_bytes[FSM_MAXL + 1][4] = {};
@@ -628,7 +629,10 @@ struct Miner {
                 release_pass1();
                 continue;
             }
-            if (fused) G->pool_hint[L] = d2h(ptop, st);
+            if (fused) {
+                G->pool_hint[L] = d2h(ptop, st);
+                rs.fused_pool_words = (int64_t)G->pool_hint[L];
+            }
             break;
         }
         unsigned long long st2[3];
@@ -1360,6 +1364,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         r->stats["sampled_edges"] = rs.sampled_edges;
         r->stats["qp_grows"] = rs.qp_grows;
         r->stats["fused_fallbacks"] = rs.fused_fallbacks;
+        r->stats["fused_pool_words"] = rs.fused_pool_words;
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["chunk_l" + std::to_string(L)] = g->tuned_chunk[L];
         for (int L = 1; L <= FSM_MAXL; ++L) r->stats["pieces_l" + std::to_string(L)] = rs.pieces_l[L];
         const char *pn[4] = {"count", "domain", "emit", "fused"};

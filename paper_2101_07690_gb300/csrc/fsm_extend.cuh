@@ -202,6 +202,8 @@ FSM_HD bool dissect4_keeps(const int32_t (&gid)[4], const uint32_t (&adj)[4], in
 
 // neighbour-adjacency masks of single-unit chunks: key vertices of degree up to 32 * this
 #define FSM_MASK_WORDS 64
+// masks of multi-unit chunks: at most this many units (two words per other position each)
+#define FSM_MASK_UNITS (FSM_MASK_WORDS / 2)
 
 // Per-warp aggregation of quick-pattern counts (PASS_COUNT).  Within one chunk the same few
 // keys repeat (one unit, one pattern, a few piece labels), so each warp sums them in its own
@@ -665,18 +667,19 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
 
 // Cross bits of neighbour number x of the key vertex from the warp's masks (see extend_kernel).
 template <int L>
-__device__ __forceinline__ uint32_t mask_bits(const uint32_t *mk, int32_t x) {
+__device__ __forceinline__ uint32_t mask_bits(const uint32_t *mk, int stride, int32_t x) {
     uint32_t c = 0;
 #pragma unroll
-    for (int pp = 0; pp < L - 1; ++pp) c |= ((mk[pp * FSM_MASK_WORDS + (x >> 5)] >> (x & 31)) & 1u) << pp;
+    for (int pp = 0; pp < L - 1; ++pp) c |= ((mk[pp * stride + (x >> 5)] >> (x & 31)) & 1u) << pp;
     return c;
 }
 
 template <int L, int PASS, int V>
 __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L], const int (&SL)[L],
                                          const int2 (&SR)[L], uint64_t srows, int32_t pid, int i, int64_t lq, Tally &tl,
-                                         CountCache *cc, DomCache &dc, const uint32_t *mk, const int32_t (&RK)[L],
-                                         int32_t cpos, int32_t &ecur, const ulonglong2 qab, uint64_t qc) {
+                                         CountCache *cc, DomCache &dc, const uint32_t *mk, int mstride,
+                                         const int32_t (&RK)[L], int32_t cpos, int32_t &ecur, const ulonglong2 qab,
+                                         uint64_t qc) {
     // quota draw: the j-th candidate run by this unit is candidate (a * j + b) mod c
     if (V == FSM_EXPLORE_TV_QUOTA && qc) lq = (int64_t)((qab.x * (uint64_t)lq + qab.y) % qc);
     const DevGraph &g = A.g;
@@ -778,8 +781,8 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
     else if (A.mode == 1 && is_adj(g, v, b)) return;   // vertex-induced: only the triangle
     const int la = __ldg(g.labels + a), lb = __ldg(g.labels + b);
     const bool hm = mk != nullptr;
-    const uint32_t ca = hm ? mask_bits<L>(mk, xa) : 0u;
-    const uint32_t cb = hm && centre ? mask_bits<L>(mk, xb) : 0u;
+    const uint32_t ca = hm ? mask_bits<L>(mk, mstride, xa) : 0u;
+    const uint32_t cb = hm && centre ? mask_bits<L>(mk, mstride, xb) : 0u;
     const bool have_b = hm && centre;
     // One call site of join_piece (it is large): the wedge (edge-induced, or an open triple)
     // and then the triangle of a closed centre pair.
@@ -825,14 +828,14 @@ __device__ __forceinline__ void do_piece(const ExtArgs &A, const int32_t (&S)[L]
 template <int L, int PASS>
 __device__ __forceinline__ void do_edge(const ExtArgs &A, const int32_t (&S)[L], const int2 (&SR)[L], uint64_t srows,
                                         int32_t pid, int i, int64_t lq, Tally &tl, CountCache *cc, DomCache &dc,
-                                        const uint32_t *mk, const int32_t (&RK)[L]) {
+                                        const uint32_t *mk, int mstride, const int32_t (&RK)[L]) {
     constexpr int K = L + 1;
     const int32_t v = S[i];
     if (A.debug && (lq < 0 || lq >= __ldg(A.g.prow + v + 1) - __ldg(A.g.prow + v))) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
     const int32_t a = __ldg(A.g.pcol + __ldg(A.g.prow + v) + (int32_t)lq);
     if (in_s<L>(S, a)) return;
     uint32_t avail = 0;   // bit p' (p != i, p' = p minus one if p > i): a ~ s[p]
-    if constexpr (L >= 2) avail = mk ? mask_bits<L>(mk, (int32_t)lq) : cross_bits<L>(A, S, SR, i, a);
+    if constexpr (L >= 2) avail = mk ? mask_bits<L>(mk, mstride, (int32_t)lq) : cross_bits<L>(A, S, SR, i, a);
     uint32_t above = 0;   // the same bits for the vertices of s with a larger id than v
 #pragma unroll
     for (int p = 0; p < L; ++p)
@@ -941,8 +944,42 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
         // neighbour of the key vertex v, its adjacency to each other vertex of s as bit masks in
         // shared memory: the cross tests of centre pieces and of the first vertex of end pieces
         // then read a bit instead of searching a neighbour list.
+        // Chunks across several units whose key vertices have at most 64 neighbours build the
+        // same masks for each unit (two words per other position of s): a centre piece then
+        // needs no search, an end piece one for its far vertex only.  Bit j of mvalid: unit
+        // ulo + j has masks, at word j * 2 * (L - 1).
         const uint32_t *mk = nullptr;
+        uint32_t mvalid = 0;
         if constexpr (L >= 2) {
+            if (ulo != uhi && uhi - ulo < FSM_MASK_UNITS) {
+                uint32_t *wm = mask_s + (threadIdx.x >> 5) * ((L - 1) * FSM_MASK_WORDS);
+                const int nu = (int)(uhi - ulo) + 1;
+                for (int j = 0; j < nu; ++j) {
+                    const int64_t u = ulo + j;
+                    const int64_t e = A.e0 + u / L;
+                    const int iu = (int)(u % L);
+                    const int32_t v = __ldg(A.fv + (int64_t)iu * A.fN + e);
+                    const int32_t rb = __ldg(A.g.prow + v), dv = __ldg(A.g.prow + v + 1) - rb;
+                    if (dv > 64) continue;
+                    for (int p = 0; p < L; ++p) {
+                        if (p == iu) continue;
+                        const int pp = p < iu ? p : p - 1;
+                        const int32_t sp = __ldg(A.fv + (int64_t)p * A.fN + e);
+                        const int32_t sb = __ldg(A.g.row_ptr + sp), se = __ldg(A.g.row_ptr + sp + 1);
+                        for (int32_t base = 0; base < dv; base += 32) {
+                            bool bit = false;
+                            if (base + lane < dv) {
+                                const int32_t x = __ldg(A.g.pcol + rb + base + lane);
+                                bit = adj_rows(A.g.col, sb, se, sp, __ldg(A.g.row_ptr + x), __ldg(A.g.row_ptr + x + 1), x);
+                            }
+                            const uint32_t word = __ballot_sync(0xffffffffu, bit);
+                            if (lane == 0) wm[j * 2 * (L - 1) + pp * 2 + (base >> 5)] = word;
+                        }
+                    }
+                    mvalid |= 1u << j;
+                }
+                __syncwarp();
+            }
             if (ulo == uhi) {
                 const int64_t e = A.e0 + ulo / L;
                 const int iu = (int)(ulo % L);
@@ -972,6 +1009,8 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
             }
         }
         int64_t cur = -1, ub = 0;
+        const uint32_t *lmk = mk;                       // this lane's unit's masks (or none)
+        int lstride = FSM_MASK_WORDS;
         ulonglong2 qab = make_ulonglong2(0ull, 0ull);   // quota draw of the current unit
         uint64_t qc = 0;                                // its candidate count, 0 = no draw
         int32_t cpos = 0;   // l = 2: entries of the key vertex's list below the other vertex of s
@@ -1020,11 +1059,18 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
                 }
 #pragma unroll
                 for (int p = 0; p < L; ++p) dc.soff[p] = -1;
+                if (mvalid) {
+                    const int j = (int)(u - ulo);
+                    lmk = (mvalid >> j) & 1u ? mask_s + (threadIdx.x >> 5) * ((L - 1) * FSM_MASK_WORDS) + j * 2 * (L - 1)
+                                             : nullptr;
+                    lstride = 2;
+                }
             }
             if constexpr (V == FSM_EXPLORE_SV)
-                do_edge<L, PASS>(A, S, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK);
+                do_edge<L, PASS>(A, S, SR, srows, pid, i, q - ub, tl, cc, dc, lmk, lstride, RK);
             else
-                do_piece<L, PASS, V>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, mk, RK, cpos, ecur, qab, qc);
+                do_piece<L, PASS, V>(A, S, SL, SR, srows, pid, i, q - ub, tl, cc, dc, lmk, lstride, RK, cpos, ecur, qab,
+                                     qc);
         }
         if (counts) flush_warp_counts<PASS == PASS_FUSED>(A, cc);
     }

@@ -281,7 +281,7 @@ STATS = ["k", "levels", "pieces", "candidates", "embeddings", "final_embeddings"
          "live_patterns", "frontier_max", "kernel_launches", "time_ns", "final_level_ns",
          "count_ns", "domain_ns", "emit_ns", "count_launches", "domain_launches", "emit_launches",
          "count_bytes", "domain_bytes", "emit_bytes", "fused_ns", "fused_launches", "fused_bytes",
-         "sampled_candidates", "recount_patterns", "recount_frontier", "sampled_edges", "qp_grows", "fused_fallbacks"] + [
+         "sampled_candidates", "recount_patterns", "recount_frontier", "sampled_edges", "qp_grows", "fused_fallbacks", "fused_pool_words"] + [
              f"{p}_{f}_l{l}" for p in ("count", "domain", "emit", "fused") for f in ("ns", "launches", "bytes")
              for l in range(1, 7)] + [f"chunk_l{l}" for l in range(1, 7)] + [f"pieces_l{l}" for l in range(1, 7)]
 
