@@ -314,6 +314,7 @@ def run_ours(args, rank, world, local_rank):
         tot.update({f"{p}_{f}_l{l}": 0 for p in ("count", "domain", "emit", "fused") for f in ("ns", "launches", "bytes")
                     for l in range(1, 7)})
         tot.update({f"pieces_l{l}": 0 for l in range(1, 7)})
+        tot.update({"fused_fallbacks": 0, "fused_pool_words": 0})
         for t in ths:
             r = G.mine(args.k, t, stats=True)
             last[t] = r
@@ -427,13 +428,15 @@ def run_ours(args, rank, world, local_rank):
                 "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
                 "data": "synthetic (seeded Chung-Lu graph of the named shape)",
-                "config": dict(workload_config(args, g), parallelism=f"replicas{world}",
-                               launch={0: "batched", 1: "persistent", 2: "per-pattern"}[args.launch],
-                               autotune=bool(args.autotune),
-                               last_level="one pass (count + domains)" if args.fused else "count pass + domain pass"),
+                "config": dict(workload_config(args, g), parallelism=f"replicas{world}"),
+                "run": {"launch": {0: "batched", 1: "persistent", 2: "per-pattern"}[args.launch],
+                        "autotune": bool(args.autotune),
+                        "last_level": "one pass (count + domains)" if args.fused else "count pass + domain pass"},
                 "e2e": e2e, "gpu_launches": int(agg["kernel_launches"]),
                 "embeddings_per_step": int(agg["embeddings"] // args.steps),
                 "patterns_per_step": int(agg["patterns_out"] // args.steps),
+                "last_level": {"fused_fallbacks": int(agg["fused_fallbacks"]),
+                               "pool_words_per_step": int(agg["fused_pool_words"] // args.steps)},
                 "roofline": roofline, "launch_compare": launch_cmp, "cpu_baseline": cpu,
                 "time_to_solution": tts, "clocks": clk}
         print(json.dumps(line), flush=True)
