@@ -406,6 +406,7 @@ def run_ours(args, rank, world, local_rank):
                 "frac": round(achieved / peak, 5), "peak_source": f"{peak_kind} hbm_gbs",
                 "traffic": traffic_for(f"{dom[0]}_l{dom[1]}"), "launches": nl, "avg_launch_ms": round(ns / nl / 1e6, 3) if nl else None,
                 "algorithmic_bytes_per_launch": byts / nl if nl else None,
+                "pieces_per_launch": agg.get(f"pieces_l{dom[1]}", 0) / nl if nl else None,
                 "share_of_step": round(ns / 1e6 / total_ms, 3) if total_ms else None,
                 "pass_ms": {f"{p}_l{l}": round(v[0] / 1e6 / args.steps, 2) for (p, l), v in passes.items() if v[2]}}
     issue = issue_roof(dom, ns, nl, agg.get(f"pieces_l{dom[1]}", 0))

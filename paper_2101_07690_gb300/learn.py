@@ -68,6 +68,7 @@ def quota_rows(G, k: int, t: int, exact: dict, quotas, seed: int = 1) -> list:
     when edges are joined) on an open graph handle, for each x: time, and precision, recall and
     median support error against the exact frequent set.  The drawn supports are lower bounds,
     so precision is 1 by construction."""
+    import sys
     import time
     rows = []
     G.set_option("model", 0)
@@ -79,6 +80,8 @@ def quota_rows(G, k: int, t: int, exact: dict, quotas, seed: int = 1) -> list:
         row = {"join_quota": int(x), "seconds": time.perf_counter() - t0}
         row.update(compare(exact, frequent_set(r, k)))
         rows.append(row)
+        sys.stderr.write(f"[quota] {row}\n")
+        sys.stderr.flush()
     G.set_option("join_quota", 0)
     return rows
 
@@ -90,9 +93,16 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
     plain sampled estimator, with the learned decision plus exact recount for each recount band
     delta, and with Section 5's quotas ST x for each x in quotas; report time and accuracy of
     each against the exact result, and the network's error on held-out training pairs."""
+    import sys
     import time
 
     import graphgen as gg
+
+    t_start = time.perf_counter()
+
+    def note(msg):   # progress on stderr, so a run cut short still shows how far it got
+        sys.stderr.write(f"[study {time.perf_counter() - t_start:8.1f} s] {msg}\n")
+        sys.stderr.flush()
 
     test = gg.workload(workload, scale=test_scale, cap=test_cap)
     Xs, ys = [], []
@@ -103,6 +113,7 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
         X, y, _ = training_pairs(g, k, tt, p, seed=seed, t_label=max(1, int(round(tt * label_frac))))
         Xs.append(X)
         ys.append(y)
+        note(f"training graph seed {s}: n={g.n} t={tt}, {len(y)} pairs")
     X, y = np.concatenate(Xs), np.concatenate(ys)
     rng = np.random.default_rng(seed)
     perm = rng.permutation(len(y))
@@ -122,11 +133,13 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
         exact = frequent_set(G.mine(k, t), k)
         out["exact_s"] = time.perf_counter() - t0
         G.set_option("fused", 0)
+        note(f"exact: {out['exact_s']:.1f} s, {len(exact)} frequent patterns")
         G.set_option("seed", seed)
         t0 = time.perf_counter()
         plain = frequent_set(G.mine(k, t, sample_rate=p), k)
         out["plain_s"] = time.perf_counter() - t0
         out["plain"] = compare(exact, plain)
+        note(f"plain estimator: {out['plain_s']:.1f} s {out['plain']}")
         G.set_option("model", m)
         out["learned"] = []
         for delta in deltas:
@@ -137,6 +150,7 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
                    "recounted": int(r["stats"]["recount_patterns"]), "exactly_counted": int(r["exact"].sum())}
             row.update(compare(exact, frequent_set(r, k)))
             out["learned"].append(row)
+            note(f"learned: {row}")
         G.set_option("delta_milli", 500)
         if quotas:
             out["quota"] = quota_rows(G, k, t, exact, quotas, seed=seed)
