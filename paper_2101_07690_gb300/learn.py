@@ -88,7 +88,7 @@ def quota_rows(G, k: int, t: int, exact: dict, quotas, seed: int = 1) -> list:
 
 def study(workload: str, k: int, t: int, p: float, train_scale: float, train_seeds, cap, test_scale: float = 1.0,
           test_cap=None, deltas=(0.0, 0.1, 0.25, 0.5), epochs: int = 200, seed: int = 1, quotas=(),
-          label_frac: float = 0.0) -> dict:
+          label_frac: float = 0.0, max_pairs: int = 0) -> dict:
     """Train on copies of a workload (other seeds), then mine the test graph exactly, with the
     plain sampled estimator, with the learned decision plus exact recount for each recount band
     delta, and with Section 5's quotas ST x for each x in quotas; report time and accuracy of
@@ -116,6 +116,10 @@ def study(workload: str, k: int, t: int, p: float, train_scale: float, train_see
         note(f"training graph seed {s}: n={g.n} t={tt}, {len(y)} pairs")
     X, y = np.concatenate(Xs), np.concatenate(ys)
     rng = np.random.default_rng(seed)
+    if max_pairs and len(y) > max_pairs:   # large k: millions of candidates; train on a uniform subsample
+        pick = rng.choice(len(y), size=max_pairs, replace=False)
+        X, y = X[pick], y[pick]
+        note(f"training on a uniform subsample of {max_pairs} pairs")
     perm = rng.permutation(len(y))
     nval = len(y) // 10
     val, tr = perm[:nval], perm[nval:]
@@ -179,9 +183,10 @@ if __name__ == "__main__":
     ap.add_argument("--test-scale", type=float, default=1.0)
     ap.add_argument("--label-frac", type=float, default=0.0,
                     help="exact training labels from mining at this fraction of the threshold (0: threshold 1)")
+    ap.add_argument("--max-pairs", type=int, default=0, help="train on at most this many (uniformly drawn) pairs")
     a = ap.parse_args()
     lo, hi = (int(x) for x in a.train_seeds.split("-"))
     print(json.dumps(study(a.workload, a.k, a.t, a.p, a.train_scale, range(lo, hi + 1), a.cap,
                            test_scale=a.test_scale, test_cap=a.test_cap, deltas=[float(x) for x in a.deltas.split(",")],
                            epochs=a.epochs, quotas=[int(x) for x in a.quotas.split(",") if x],
-                           label_frac=a.label_frac)))
+                           label_frac=a.label_frac, max_pairs=a.max_pairs)))
