@@ -86,7 +86,9 @@ int fsm_load_graph(const int32_t *row_ptr, const int32_t *col, const int32_t *la
  *   "autotune"   1 = on the first call per level, time the domain pass on 1/32 of the
  *                frontier for chunk sizes 256, 1024, 4096, 16384 and keep the fastest for later
  *                passes and calls (reported as stat "chunk_l<l>"); 0 = forget tuned values.
- *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default).
+ *   "chunk"      pieces per work-stealing chunk (power of two, 32..65536; 0 = default: the largest
+ *                power of two from 256 to 16384 that leaves at least 64 chunks per warp and spans
+ *                at most about 16 units' pieces).
  *   "batch"      frontier embeddings per batch (>= 1024; 0 = default).
  *   "explore"    0 = two-vertex exploration (default, Section 4.1); 1 = single-vertex
  *                exploration, l -> l+1 (the ablation Section 6 compares against): every level

@@ -363,9 +363,10 @@ struct Miner {
                 if (total == 0) continue;
                 bytes(r);
                 int64_t chunk = chunk_for(L);
-                if (chunk <= 0) {
+                if (chunk <= 0) {   // as the kernel sizes it when the total stays on the device
+                    const int64_t per_unit = total / (r.ne * L);
                     chunk = 256;
-                    while (chunk < 16384 && total / chunk > warps * 64) chunk <<= 1;
+                    while (chunk < 16384 && total / chunk > warps * 64 && chunk * 2 <= 16 * per_unit) chunk <<= 1;
                 }
                 A.e0 = r.e0;
                 A.ne = r.ne;

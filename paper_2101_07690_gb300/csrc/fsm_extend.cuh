@@ -908,9 +908,12 @@ __global__ void __launch_bounds__(256, ExtMinBlocks<PASS>::value) extend_kernel(
         // device-resident size: no host round trip between the prefix sum and this launch
         total = __ldg(A.unit_base + nunits);
         if (chunk <= 0) {
+            // at least 64 chunks per warp, and at most about 16 units' pieces per chunk (a chunk
+            // over at most 32 small units builds their cross masks)
             const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+            const int64_t per_unit = total / (nunits > 0 ? nunits : 1);
             chunk = 256;
-            while (chunk < 16384 && total / chunk > warps * 64) chunk <<= 1;
+            while (chunk < 16384 && total / chunk > warps * 64 && chunk * 2 <= 16 * per_unit) chunk <<= 1;
         }
         nchunks = (total + chunk - 1) / chunk;
     }
