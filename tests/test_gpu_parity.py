@@ -374,3 +374,36 @@ def test_injected_allocation_failure_returns_enomem(fsm):
     got = G.mine(4, 10)
     G.close()
     _same(got, oracle_at(g, 4, 10), "after injected allocation failures")
+
+
+def _degenerate_graphs():
+    return [
+        ("one vertex", gg.from_edges(1, [], np.array([0], np.int32), 1), (1, 2, 3, 5), 1),
+        ("isolated vertices", gg.from_edges(6, [], np.array([0, 1, 0, 1, 0, 1], np.int32), 2), (1, 2, 3, 4), 1),
+        ("one edge", gg.from_edges(2, [(0, 1)], np.array([0, 1], np.int32), 2), (1, 2, 3, 4), 1),
+        ("k above n", gg.path(5), (6, 7, 8), 1),
+        ("nothing frequent", gg.workload("er1000"), (2, 3, 4, 5), 10 ** 6),
+    ]
+
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+def test_degenerate_inputs(fsm, mode):
+    """Graphs without edges, a single edge, k above the vertex count and thresholds no pattern
+    reaches: every exploration form, last-level form, launch mode and sampling mode returns the
+    oracle's (mostly empty) answer."""
+    for name, g, ks, t in _degenerate_graphs():
+        for k in ks:
+            for opts in ({}, {"launch": 0}, {"launch": 2}, {"fused": 1}, {"explore": 1}, {"quick_pattern": 1}):
+                if k > 7 and ("explore" in opts or "quick_pattern" in opts):
+                    continue
+                check(fsm, g, k, t, mode, opts)
+            if k >= 3:
+                G = fsm.Graph.from_graphgen(g, mode)
+                G.set_option("join_quota", 2)
+                got = G.mine(k, t)
+                sampled = G.mine(k, t, sample_rate=0.5) if k <= 8 else None
+                G.close()
+                exp = oracle.mine_quota(g, k, t, mode, seed=0, join_quota=2)
+                for key in ("labels", "adj", "support", "count"):
+                    assert np.array_equal(got[key], exp[key]), (name, k, key)
+                assert sampled is not None and len(sampled["support"]) <= max(1, len(oracle_at(g, k, 1, mode)["support"]))
