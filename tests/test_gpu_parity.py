@@ -401,9 +401,10 @@ def test_degenerate_inputs(fsm, mode):
                 G = fsm.Graph.from_graphgen(g, mode)
                 G.set_option("join_quota", 2)
                 got = G.mine(k, t)
-                sampled = G.mine(k, t, sample_rate=0.5) if k <= 8 else None
+                G.set_option("join_quota", 0)      # rate sampling runs without quotas
+                sampled = G.mine(k, t, sample_rate=0.5)
                 G.close()
                 exp = oracle.mine_quota(g, k, t, mode, seed=0, join_quota=2)
                 for key in ("labels", "adj", "support", "count"):
                     assert np.array_equal(got[key], exp[key]), (name, k, key)
-                assert sampled is not None and len(sampled["support"]) <= max(1, len(oracle_at(g, k, 1, mode)["support"]))
+                assert len(sampled["support"]) <= max(1, len(oracle_at(g, k, 1, mode)["support"]))
