@@ -12,7 +12,8 @@ graphs that follows the MNI definition literally by enumerating injective maps.
 Pattern encoding shared by both oracles' outputs (and by the library's C ABI, which defines
 the same encoding independently):
   * ``labels[k]``: vertex labels in canonical order;
-  * ``adj``: bit ``i*k + j`` (LSB = bit 0) set for each canonical edge i < j;
+  * ``adj``: bit ``i*k + j`` (LSB = bit 0) set for each canonical edge i < j (a uint64 array for
+    k <= 8; for k = 9, whose bits run past 64, an object array of Python ints);
   * patterns sorted ascending by the label sequence, then by the adjacency sequence
     A(0,1), A(0,2), ..., A(k-2,k-1) compared lexicographically (0 < 1).
 """
@@ -84,6 +85,13 @@ def _load():
                                                P(ctypes.c_int64), P(ctypes.c_int64)]
             lib.oracle_free.restype = None
             lib.oracle_free.argtypes = [ctypes.c_void_p]
+            lib.oracle_result_copy_pairs.restype = None
+            lib.oracle_result_copy_pairs.argtypes = [ctypes.c_void_p, P(ctypes.c_uint64)]
+            lib.oracle_pattern_support_rows.restype = ctypes.c_int
+            lib.oracle_pattern_support_rows.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
+                                                        P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32),
+                                                        P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_int64,
+                                                        P(ctypes.c_int64), P(ctypes.c_int64)]
             lib.oracle_pattern_support.restype = ctypes.c_int
             lib.oracle_pattern_support.argtypes = [ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_int32),
                                                    P(ctypes.c_int32), ctypes.c_int32, P(ctypes.c_int32),
@@ -100,6 +108,29 @@ def _ptr(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
+def adj_from_pairs(pairs, k: int):
+    """``adj`` words (bit i*k + j) from pair words (bit q = pair q of (0,1), (0,2), ...,
+    (k-2,k-1)): uint64 for k <= 8, Python ints (object array) for k = 9."""
+    pos = [i * k + j for i in range(k) for j in range(i + 1, k)]
+    out = [sum(1 << pos[q] for q in range(len(pos)) if (int(w) >> q) & 1) for w in pairs]
+    return np.array(out, dtype=np.uint64 if k <= 8 else object)
+
+
+def _result(lib, res, k: int) -> dict:
+    npat = lib.oracle_result_count(res)
+    out = {"labels": np.zeros((npat, k), np.int32), "adj": np.zeros(npat, np.uint64),
+           "support": np.zeros(npat, np.int64), "count": np.zeros(npat, np.int64)}
+    if npat:
+        lib.oracle_result_copy(res, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
+                               _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64))
+    if k > 8:
+        pairs = np.zeros(npat, np.uint64)
+        if npat:
+            lib.oracle_result_copy_pairs(res, _ptr(pairs, ctypes.c_uint64))
+        out["adj"] = adj_from_pairs(pairs, k)
+    return out
+
+
 def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = None,
          max_embeddings: int = 0, sample: tuple[float, int] | None = None) -> dict:
     """All k-vertex patterns of graph ``g`` with MNI support >= t.
@@ -113,8 +144,8 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
     the join vertex; ``ssupport`` and ``scount`` are the MNI support and embedding count over
     kept embeddings, ``spop[P, c]`` the size of canonical position c's sampled image set and
     ``sdeg[P, c]`` the sum of log(1 + degree) over it.
-    Returns a dict of numpy arrays: labels (P, k) int32, adj (P,) uint64, support (P,) int64,
-    count (P,) int64 (number of embeddings of each pattern)."""
+    Returns a dict of numpy arrays: labels (P, k) int32, adj (P,) (uint64, or Python ints for
+    k = 9), support (P,) int64, count (P,) int64 (number of embeddings of each pattern)."""
     lib = _load()
     row_ptr = np.ascontiguousarray(g.row_ptr, dtype=np.int32)
     col = np.ascontiguousarray(g.col, dtype=np.int32)
@@ -129,12 +160,8 @@ def mine(g, k: int, t: int, mode: str = "edge", roots: tuple[int, int] | None = 
     if not res:
         raise ValueError("oracle_mine rejected its arguments")
     try:
-        npat = lib.oracle_result_count(res)
-        out = {"labels": np.zeros((npat, k), np.int32), "adj": np.zeros(npat, np.uint64),
-               "support": np.zeros(npat, np.int64), "count": np.zeros(npat, np.int64)}
-        if npat:
-            lib.oracle_result_copy(res, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
-                                   _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64))
+        out = _result(lib, res, k)
+        npat = len(out["support"])
         if sample is not None:
             out["ssupport"] = np.zeros(npat, np.int64)
             out["scount"] = np.zeros(npat, np.int64)
@@ -160,10 +187,17 @@ def pattern_support(g, labels, adj: int, mode: str = "edge", max_maps: int = 0) 
     col = np.ascontiguousarray(g.col, dtype=np.int32)
     lab = np.ascontiguousarray(g.labels, dtype=np.int32)
     plab = np.ascontiguousarray(labels, dtype=np.int32)
+    rows = np.zeros(max(k, 1), np.uint32)
+    for i in range(k):
+        for j in range(i + 1, k):
+            if (int(adj) >> (i * k + j)) & 1:
+                rows[i] |= np.uint32(1 << j)
+                rows[j] |= np.uint32(1 << i)
     sup, cnt = ctypes.c_int64(), ctypes.c_int64()
-    rc = lib.oracle_pattern_support(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
-                                    _ptr(lab, ctypes.c_int32), k, _ptr(plab, ctypes.c_int32), int(adj),
-                                    MODES[mode], int(max_maps), ctypes.byref(sup), ctypes.byref(cnt))
+    rc = lib.oracle_pattern_support_rows(g.n, _ptr(row_ptr, ctypes.c_int32), _ptr(col, ctypes.c_int32),
+                                         _ptr(lab, ctypes.c_int32), k, _ptr(plab, ctypes.c_int32),
+                                         _ptr(rows, ctypes.c_uint32), MODES[mode], int(max_maps),
+                                         ctypes.byref(sup), ctypes.byref(cnt))
     if rc == -2:
         raise OverflowError("pattern has more than max_maps maps")
     if rc != 0:
@@ -205,13 +239,13 @@ def kept(u, adj_rows, seed: int, p: float) -> bool:
     r = _load().oracle_kept(len(uu), _ptr(uu, ctypes.c_int32), _ptr(rows, ctypes.c_uint32),
                             int(seed) & ((1 << 64) - 1), float(p))
     if r < 0:
-        raise ValueError("kept needs 3 <= k <= 8")
+        raise ValueError("kept needs 3 <= k <= 9")
     return bool(r)
 
 
 def mine_quota(g, k: int, t: int, mode: str = "edge", seed: int = 0, join_quota: int = 0,
                match_quota: int = 0) -> dict:
-    """Patterns of exactly k vertices (3 <= k <= 8) whose MNI support over the embeddings drawn
+    """Patterns of exactly k vertices (3 <= k <= 9) whose MNI support over the embeddings drawn
     under Section 5's sampling quotas reaches t, by the method's own level-wise steps: size-3
     matching with at most ``match_quota`` candidate pieces per vertex, then joins l -> l+2 with at
     most ``join_quota``^2 candidate pieces per key group and, joining edges, ``join_quota`` edges
@@ -226,12 +260,7 @@ def mine_quota(g, k: int, t: int, mode: str = "edge", seed: int = 0, join_quota:
     if not res:
         raise ValueError("oracle_mine_quota rejected its arguments")
     try:
-        npat = lib.oracle_result_count(res)
-        out = {"labels": np.zeros((npat, k), np.int32), "adj": np.zeros(npat, np.uint64),
-               "support": np.zeros(npat, np.int64), "count": np.zeros(npat, np.int64)}
-        if npat:
-            lib.oracle_result_copy(res, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
-                                   _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64))
+        out = _result(lib, res, k)
     finally:
         lib.oracle_free(res)
     return out

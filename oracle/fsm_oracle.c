@@ -41,7 +41,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#define OR_MAXK 8
+#define OR_MAXK 9
 
 /* ------------------------------------------------------------------ small utilities */
 
@@ -92,7 +92,7 @@ static void vset_insert(vset_t *s, int32_t x) {
 
 /* A code is the label sequence plus the adjacency sequence packed into an integer whose most
  * significant used bit is the first pair (0,1); integer order equals sequence order. */
-typedef struct { int32_t lab[OR_MAXK]; uint32_t adj; } code_t;
+typedef struct { int32_t lab[OR_MAXK]; uint64_t adj; } code_t;
 
 static int code_cmp(const code_t *a, const code_t *b, int k) {
     for (int i = 0; i < k; i++)
@@ -137,11 +137,27 @@ static void code_of(const canon_ctx_t *cx, const uint8_t *perm, const int32_t *l
     int k = cx->k;
     for (int c = 0; c < k; c++) out->lab[c] = lab[perm[c]];
     for (int c = k; c < OR_MAXK; c++) out->lab[c] = 0;
-    uint32_t a = 0;
+    uint64_t a = 0;
     for (int c1 = 0; c1 < k; c1++)
         for (int c2 = c1 + 1; c2 < k; c2++)
-            a = (a << 1) | ((adjrow[perm[c1]] >> perm[c2]) & 1u);
+            a = (a << 1) | (uint64_t)((adjrow[perm[c1]] >> perm[c2]) & 1u);
     out->adj = a;
+}
+
+/* code_cmp(code of perm, *c): the label sequence first, then the adjacency sequence, from
+ * the first position and pair on, returning at the first difference */
+static int perm_cmp(const canon_ctx_t *cx, const uint8_t *perm, const int32_t *lab, const uint32_t *adjrow,
+                    const code_t *c) {
+    int k = cx->k;
+    for (int i = 0; i < k; i++)
+        if (lab[perm[i]] != c->lab[i]) return lab[perm[i]] < c->lab[i] ? -1 : 1;
+    int q = cx->npairs - 1;
+    for (int c1 = 0; c1 < k; c1++)
+        for (int c2 = c1 + 1; c2 < k; c2++, q--) {
+            const uint64_t a = (adjrow[perm[c1]] >> perm[c2]) & 1u, b = (c->adj >> q) & 1u;
+            if (a != b) return a < b ? -1 : 1;
+        }
+    return 0;
 }
 
 /* ------------------------------------------------------------------ pattern registry */
@@ -155,7 +171,7 @@ typedef struct {
 } pattern_t;
 
 typedef struct {
-    uint64_t key_lab; uint32_t key_adj; int used;
+    uint64_t key_lab, key_lab2, key_adj; int used;   /* raw key: labels 0..7, labels 8.., pairs */
     int32_t pattern;                /* index into patterns */
     int32_t nopt; int64_t perm_off; /* optimal permutations, k bytes each, in perm pool */
 } memo_t;
@@ -212,26 +228,31 @@ static int32_t pattern_find_or_add(oracle_t *o, const code_t *c) {
     return (int32_t)o->npat++;
 }
 
-static memo_t *memo_lookup(oracle_t *o, uint64_t klab, uint32_t kadj) {
+static uint64_t memo_hash(uint64_t klab, uint64_t klab2, uint64_t kadj) {
+    return mix64(klab ^ mix64(kadj ^ mix64(klab2)));
+}
+
+static memo_t *memo_lookup(oracle_t *o, uint64_t klab, uint64_t klab2, uint64_t kadj) {
     if ((o->memo_size + 1) * 2 > o->memo_cap) {
         int64_t ncap = o->memo_cap ? o->memo_cap * 2 : 1024;
         memo_t *old = o->memo; int64_t ocap = o->memo_cap;
         o->memo = (memo_t *)calloc((size_t)ncap, sizeof(memo_t));
         o->memo_cap = ncap;
         for (int64_t i = 0; i < ocap; i++) if (old[i].used) {
-            uint64_t h = mix64(old[i].key_lab ^ mix64(old[i].key_adj)) & (uint64_t)(ncap - 1);
+            uint64_t h = memo_hash(old[i].key_lab, old[i].key_lab2, old[i].key_adj) & (uint64_t)(ncap - 1);
             while (o->memo[h].used) h = (h + 1) & (uint64_t)(ncap - 1);
             o->memo[h] = old[i];
         }
         free(old);
     }
-    uint64_t h = mix64(klab ^ mix64(kadj)) & (uint64_t)(o->memo_cap - 1);
+    uint64_t h = memo_hash(klab, klab2, kadj) & (uint64_t)(o->memo_cap - 1);
     while (o->memo[h].used) {
-        if (o->memo[h].key_lab == klab && o->memo[h].key_adj == kadj) return &o->memo[h];
+        if (o->memo[h].key_lab == klab && o->memo[h].key_lab2 == klab2 && o->memo[h].key_adj == kadj)
+            return &o->memo[h];
         h = (h + 1) & (uint64_t)(o->memo_cap - 1);
     }
     memo_t *m = &o->memo[h];
-    m->used = 1; m->key_lab = klab; m->key_adj = kadj; m->pattern = -1;
+    m->used = 1; m->key_lab = klab; m->key_lab2 = klab2; m->key_adj = kadj; m->pattern = -1;
     o->memo_size++;
     return m;
 }
@@ -239,38 +260,36 @@ static memo_t *memo_lookup(oracle_t *o, uint64_t klab, uint32_t kadj) {
 /* canonicalise one raw labeled graph (lab, adjrow over positions 0..k-1), memoised */
 static memo_t *canonical(oracle_t *o, const int32_t *lab, const uint32_t *adjrow) {
     int k = o->k;
-    uint64_t klab = 0; uint32_t kadj = 0;
-    for (int i = 0; i < k; i++) klab = (klab << 8) | (uint64_t)(lab[i] & 0xff);
+    uint64_t klab = 0, klab2 = 0, kadj = 0;
+    for (int i = 0; i < k; i++) {
+        if (i < 8) klab = (klab << 8) | (uint64_t)(lab[i] & 0xff);
+        else klab2 = (klab2 << 8) | (uint64_t)(lab[i] & 0xff);
+    }
     /* raw key: the label tuple and the packed upper triangle of the adjacency */
     for (int c1 = 0; c1 < k; c1++)
         for (int c2 = c1 + 1; c2 < k; c2++)
-            kadj = (kadj << 1) | ((adjrow[c1] >> c2) & 1u);
-    memo_t *m = memo_lookup(o, klab, kadj);
+            kadj = (kadj << 1) | (uint64_t)((adjrow[c1] >> c2) & 1u);
+    memo_t *m = memo_lookup(o, klab, klab2, kadj);
     if (m->pattern >= 0) return m;
-    code_t best, cur;
-    int have = 0;
-    for (int p = 0; p < o->cx.nperm; p++) {
-        code_of(&o->cx, o->cx.perms + (size_t)p * k, lab, adjrow, &cur);
-        if (!have || code_cmp(&cur, &best, k) < 0) { best = cur; have = 1; }
+    /* the minimum code over all k! permutations, then every permutation attaining it; each
+     * comparison is lexicographic and stops at the first differing label or pair */
+    code_t best;
+    code_of(&o->cx, o->cx.perms, lab, adjrow, &best);
+    for (int p = 1; p < o->cx.nperm; p++) {
+        const uint8_t *perm = o->cx.perms + (size_t)p * k;
+        if (perm_cmp(&o->cx, perm, lab, adjrow, &best) < 0) code_of(&o->cx, perm, lab, adjrow, &best);
     }
-    int32_t nopt = 0;
+    m->perm_off = o->pool_size; m->nopt = 0;
     for (int p = 0; p < o->cx.nperm; p++) {
-        code_of(&o->cx, o->cx.perms + (size_t)p * k, lab, adjrow, &cur);
-        if (code_cmp(&cur, &best, k) == 0) nopt++;
-    }
-    if (o->pool_size + (int64_t)nopt * k > o->pool_cap) {
-        int64_t ncap = o->pool_cap ? o->pool_cap * 2 : 4096;
-        while (ncap < o->pool_size + (int64_t)nopt * k) ncap *= 2;
-        o->pool = (uint8_t *)realloc(o->pool, (size_t)ncap);
-        o->pool_cap = ncap;
-    }
-    m->perm_off = o->pool_size; m->nopt = nopt;
-    for (int p = 0; p < o->cx.nperm; p++) {
-        code_of(&o->cx, o->cx.perms + (size_t)p * k, lab, adjrow, &cur);
-        if (code_cmp(&cur, &best, k) == 0) {
-            memcpy(o->pool + o->pool_size, o->cx.perms + (size_t)p * k, (size_t)k);
-            o->pool_size += k;
+        const uint8_t *perm = o->cx.perms + (size_t)p * k;
+        if (perm_cmp(&o->cx, perm, lab, adjrow, &best) != 0) continue;
+        if (o->pool_size + k > o->pool_cap) {
+            o->pool_cap = o->pool_cap ? o->pool_cap * 2 : 4096;
+            o->pool = (uint8_t *)realloc(o->pool, (size_t)o->pool_cap);
         }
+        memcpy(o->pool + o->pool_size, perm, (size_t)k);
+        o->pool_size += k;
+        m->nopt++;
     }
     m->pattern = pattern_find_or_add(o, &best);
     return m;
@@ -453,7 +472,8 @@ static void esu_extend(oracle_t *o, int32_t *sub, int depth, const int32_t *ext,
 typedef struct {
     int k; int64_t npat;
     int32_t *labels;     /* npat x k */
-    uint64_t *adj;       /* bit (i*k + j) set for canonical edge i < j */
+    uint64_t *adj;       /* bit (i*k + j) set for canonical edge i < j (k <= 8; 0 for k = 9) */
+    uint64_t *pairs;     /* bit q set when pair q of (0,1), (0,2), ..., (k-2,k-1) is an edge */
     int64_t *support, *count;
     int64_t *ssupport, *scount;   /* sampled mode: min_c |sampled images|, kept embeddings */
     int64_t *spop;                /* sampled mode: |sampled images of position c|, npat x k */
@@ -465,6 +485,21 @@ static const pattern_t *code_sort_base;
 static int idx_cmp(const void *a, const void *b) {
     int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
     return code_cmp(&code_sort_base[x].code, &code_sort_base[y].code, code_sort_k);
+}
+
+/* Unpack a canonical adjacency sequence (first pair most significant) into bit (i*k + j) of
+ * *bits (k <= 8; 0 for k = 9, whose 72 bit positions do not fit) and bit q of *pairs. */
+static void unpack_code(int k, uint64_t code, uint64_t *bits, uint64_t *pairs) {
+    int np = k * (k - 1) / 2, idx = 0;
+    uint64_t b = 0, pr = 0;
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++, idx++)
+            if ((code >> (np - 1 - idx)) & 1u) {
+                if (k <= 8) b |= 1ULL << (i * k + j);
+                pr |= 1ULL << idx;
+            }
+    *bits = b;
+    *pairs = pr;
 }
 
 /*
@@ -538,6 +573,7 @@ oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const in
     r->npat = nk;
     r->labels = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nk * k + 1));
     r->adj = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk + 1));
+    r->pairs = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk + 1));
     r->support = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     r->count = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     r->ssupport = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
@@ -552,13 +588,7 @@ oracle_result_t *oracle_mine_sampled(int32_t n, const int32_t *row_ptr, const in
             if (sigma < 0 || s < sigma) sigma = s;
         }
         for (int c = 0; c < k; c++) r->labels[q * k + c] = p->code.lab[c];
-        /* unpack the row-major adjacency sequence into bit (i*k + j) */
-        uint64_t bits = 0;
-        int np = k * (k - 1) / 2, idx = 0;
-        for (int i = 0; i < k; i++)
-            for (int j = i + 1; j < k; j++, idx++)
-                if ((p->code.adj >> (np - 1 - idx)) & 1u) bits |= 1ULL << (i * k + j);
-        r->adj[q] = bits;
+        unpack_code(k, p->code.adj, &r->adj[q], &r->pairs[q]);
         r->support[q] = sigma;
         r->count[q] = p->count;
         int64_t ss = -1;
@@ -595,6 +625,12 @@ void oracle_result_copy(const oracle_result_t *r, int32_t *labels, uint64_t *adj
     memcpy(count, r->count, sizeof(int64_t) * (size_t)r->npat);
 }
 
+/* pairs[q]: bit q set when pair q of (0,1), (0,2), ..., (k-2,k-1) is a canonical edge (any k) */
+void oracle_result_copy_pairs(const oracle_result_t *r, uint64_t *pairs) {
+    if (!r) return;
+    memcpy(pairs, r->pairs, sizeof(uint64_t) * (size_t)r->npat);
+}
+
 void oracle_result_copy_sampled(const oracle_result_t *r, int64_t *ssupport, int64_t *scount) {
     if (!r) return;
     memcpy(ssupport, r->ssupport, sizeof(int64_t) * (size_t)r->npat);
@@ -611,7 +647,7 @@ void oracle_result_copy_sampled_domains(const oracle_result_t *r, int64_t *spop,
 
 void oracle_free(oracle_result_t *r) {
     if (!r) return;
-    free(r->labels); free(r->adj); free(r->support); free(r->count); free(r->ssupport); free(r->scount);
+    free(r->labels); free(r->adj); free(r->pairs); free(r->support); free(r->count); free(r->ssupport); free(r->scount);
     free(r->spop); free(r->sdeg); free(r);
 }
 
@@ -620,7 +656,8 @@ void oracle_free(oracle_result_t *r) {
 /*
  * oracle_pattern_support: MNI support and embedding count of ONE pattern P in G, by matching.
  *   P has k vertices with labels plab[k] and an edge (i, j), i < j, wherever bit i*k + j of padj
- *   is set; P must be connected.  Every injective map f from P's vertices to G's vertices that
+ *   is set (k <= 8; oracle_pattern_support_rows takes adjacency rows instead, for any k <= 9);
+ *   P must be connected.  Every injective map f from P's vertices to G's vertices that
  *   keeps labels and sends each pattern edge to a graph edge is enumerated (edge-induced mode:
  *   the monomorphisms), or that also sends each pattern non-edge to a non-edge (vertex-induced
  *   mode).  These maps are exactly the isomorphisms from P onto its embeddings, so Definition 2
@@ -674,18 +711,23 @@ static void match_rec(match_t *m, int depth) {
     }
 }
 
-int oracle_pattern_support(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *labels,
-                           int32_t k, const int32_t *plab, uint64_t padj_bits, int32_t mode,
-                           int64_t max_maps, int64_t *support, int64_t *count) {
-    if (k < 1 || k > OR_MAXK || n < 1 || (mode != 0 && mode != 1) || !support || !count) return -1;
+/* The same with P's adjacency given as rows: bit j of prow[i] set for every edge (i, j) (any
+ * k <= 9; the rows must be symmetric and without self-loops). */
+int oracle_pattern_support_rows(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *labels,
+                                int32_t k, const int32_t *plab, const uint32_t *prow, int32_t mode,
+                                int64_t max_maps, int64_t *support, int64_t *count) {
+    if (k < 1 || k > OR_MAXK || n < 1 || (mode != 0 && mode != 1) || !support || !count || !prow) return -1;
     match_t m;
     memset(&m, 0, sizeof(m));
     m.k = k; m.mode = mode; m.row_ptr = row_ptr; m.col = col; m.labels = labels; m.n = n;
     m.max_maps = max_maps;
     for (int i = 0; i < k; i++) m.plab[i] = plab[i];
-    for (int i = 0; i < k; i++)
-        for (int j = i + 1; j < k; j++)
-            if ((padj_bits >> (i * k + j)) & 1ULL) { m.padj[i] |= 1u << j; m.padj[j] |= 1u << i; }
+    for (int i = 0; i < k; i++) {
+        if ((prow[i] >> i) & 1u) return -1;
+        for (int j = 0; j < k; j++)
+            if (((prow[i] >> j) & 1u) != ((prow[j] >> i) & 1u)) return -1;
+        m.padj[i] = prow[i] & ((1u << k) - 1u);
+    }
     if (!spans_connected(k, m.padj)) return -1;
     /* BFS order from position 0: each later position has an already placed neighbour */
     int seen = 1; m.order[0] = 0; m.parent[0] = -1;
@@ -733,6 +775,17 @@ int oracle_pattern_support(int32_t n, const int32_t *row_ptr, const int32_t *col
     for (int c = 0; c < k; c++) free(m.img[c]);
     free(m.img);
     return rc;
+}
+
+int oracle_pattern_support(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *labels,
+                           int32_t k, const int32_t *plab, uint64_t padj_bits, int32_t mode,
+                           int64_t max_maps, int64_t *support, int64_t *count) {
+    if (k < 1 || k > 8) return -1;      /* bit (i*k + j) runs past 64 bits at k = 9 */
+    uint32_t prow[OR_MAXK] = {0};
+    for (int i = 0; i < k; i++)
+        for (int j = i + 1; j < k; j++)
+            if ((padj_bits >> (i * k + j)) & 1ULL) { prow[i] |= 1u << j; prow[j] |= 1u << i; }
+    return oracle_pattern_support_rows(n, row_ptr, col, labels, k, plab, prow, mode, max_maps, support, count);
 }
 
 /* dissection of a connected k-vertex graph given as adjacency rows over positions 0..k-1
@@ -1057,17 +1110,13 @@ static oracle_result_t *q_result(const oracle_t *o, int k, int64_t t) {
     r->npat = nk;
     r->labels = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nk * k + 1));
     r->adj = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk + 1));
+    r->pairs = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk + 1));
     r->support = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     r->count = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nk + 1));
     for (int64_t q = 0; q < nk; q++) {
         const pattern_t *p = &o->pat[keep[q]];
         for (int c = 0; c < k; c++) r->labels[q * k + c] = p->code.lab[c];
-        uint64_t bits = 0;
-        int np = k * (k - 1) / 2, idx = 0;
-        for (int i = 0; i < k; i++)
-            for (int j = i + 1; j < k; j++, idx++)
-                if ((p->code.adj >> (np - 1 - idx)) & 1u) bits |= 1ULL << (i * k + j);
-        r->adj[q] = bits;
+        unpack_code(k, p->code.adj, &r->adj[q], &r->pairs[q]);
         r->support[q] = q_sigma(p, k);
         r->count[q] = p->count;
     }
@@ -1076,7 +1125,7 @@ static oracle_result_t *q_result(const oracle_t *o, int k, int64_t t) {
 }
 
 /*
- * oracle_mine_quota: the patterns of exactly k vertices (3 <= k <= 8) whose MNI support over
+ * oracle_mine_quota: the patterns of exactly k vertices (3 <= k <= 9) whose MNI support over
  * the embeddings drawn under Section 5's quotas reaches t, with those supports and counts (see
  * the steps above).  join_quota = 0 and match_quota = 0 draw everything, which is exact mining
  * by the method's own steps.
