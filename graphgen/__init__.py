@@ -234,6 +234,21 @@ def random_small(n: int, p: float, num_labels: int, seed: int) -> Graph:
     return from_edges(n, np.stack([iu[keep], ju[keep]], 1), labels, num_labels)
 
 
+def tree_plus(n: int, extra: int, num_labels: int, seed: int) -> Graph:
+    """A random labeled tree on n vertices (vertex v > 0 hangs off a uniform earlier vertex) plus
+    `extra` further distinct edges: sparse and connected, so the connected 9-vertex subgraphs
+    stay few enough for brute force."""
+    rng = np.random.default_rng(seed)
+    edges = set()
+    for v in range(1, n):
+        edges.add((int(rng.integers(v)), v))
+    while len(edges) < n - 1 + extra:
+        a, b = sorted(int(x) for x in rng.choice(n, 2, replace=False))
+        edges.add((a, b))
+    labels = rng.integers(num_labels, size=n).astype(np.int32)
+    return from_edges(n, sorted(edges), labels, num_labels)
+
+
 def relabel_vertices(g: Graph, perm: np.ndarray) -> Graph:
     """Same graph with vertex v renamed perm[v]."""
     perm = np.asarray(perm, dtype=np.int64)

@@ -3,7 +3,7 @@
  *
  * The library finds every size-k pattern of one labeled, undirected input graph whose MNI
  * support is at least t (the FSM problem of Section 2.2).  Mining runs level by level
- * (sizes 1 -> 3 -> 5 -> 7 for odd k, 2 -> 4 -> 6 -> 8 for even k): every embedding of every
+ * (sizes 1 -> 3 -> 5 -> 7 -> 9 for odd k, 2 -> 4 -> 6 -> 8 for even k): every embedding of every
  * frequent size-l pattern is joined with every frequent size-3 subgraph (wedge or triangle)
  * that shares exactly one vertex with it (two-vertex exploration, Section 4.1, Theorem 1),
  * duplicates are removed by smallest-vertex-first dissection (Section 4.3, Algorithm 1),
@@ -21,11 +21,13 @@
  *   - A graph handle owns device memory until fsm_free_graph(); a result handle owns host
  *     memory until fsm_free_result().  Handles are not thread-safe: one thread per handle.
  *   - Vertex ids are int32 in [0, n); labels are int32 in [0, num_labels), num_labels <= 64.
- *   - Pattern encoding (output): labels[k] in canonical order, and adj_bits with bit
- *     (i*k + j), LSB = bit 0, set for every canonical edge i < j.  The canonical form of a
- *     labeled graph is the lexicographically smallest (label sequence, adjacency sequence
- *     A(0,1), A(0,2), ..., A(k-2,k-1)) over all vertex orders; results are sorted ascending by
- *     that same (label sequence, adjacency sequence) key.
+ *   - Pattern encoding (output): labels[k] in canonical order, and the canonical edges as
+ *     adj_bits (k <= 8) with bit (i*k + j), LSB = bit 0, set for every canonical edge i < j, or
+ *     as pair bits (any k <= 9; fsm_result_pairs) with bit q set when the q-th pair of
+ *     (0,1), (0,2), ..., (k-2,k-1) is an edge.  The canonical form of a labeled graph is the
+ *     lexicographically smallest (label sequence, adjacency sequence A(0,1), A(0,2), ...,
+ *     A(k-2,k-1)) over all vertex orders; results are sorted ascending by that same (label
+ *     sequence, adjacency sequence) key.
  */
 #ifndef FSM_H
 #define FSM_H
@@ -153,7 +155,10 @@ int fsm_set_option(fsm_graph *g, const char *key, int64_t value);
 /*
  * fsm_mine -- every pattern with exactly k vertices and MNI support >= min_support
  * (Section 2.2 problem statement; Definition 2).
- *   1 <= k <= 8, min_support >= 1, sample_rate in (0, 1]; 1.0 means exact mining.
+ *   1 <= k <= 9, min_support >= 1, sample_rate in (0, 1]; 1.0 means exact mining.  k = 9
+ *   (Section 6 mines 9-vertex patterns) runs with two-vertex exploration and index-based quick
+ *   patterns, exactly or with sampling quotas; the single-vertex and edge-list ablations stop
+ *   at k = 7 and rate-sampled mining at k = 8 (FSM_EUNSUPPORTED above).
  * Exact mining (sample_rate = 1) returns exact MNI supports and embedding counts.
  * Sampled mining (sample_rate = p < 1, k >= 3; Section 5's subgraph sampling, here at a rate
  * instead of a per-key quota): every level but the last is mined exactly; in the last level a
@@ -178,7 +183,8 @@ int64_t fsm_result_count(const fsm_result *r);
 /*
  * fsm_result_get -- pattern i (0 <= i < count) of a result.
  *   labels_k  int32[k] written with the canonical labels (may be NULL).
- *   adj_bits  bit (i*k + j) set per canonical edge i < j (may be NULL).
+ *   adj_bits  bit (i*k + j) set per canonical edge i < j (may be NULL); k <= 8 only: a k = 9
+ *             result gives FSM_EUNSUPPORTED for a non-NULL adj_bits (use fsm_result_pairs).
  *   support   MNI support (may be NULL).
  */
 int fsm_result_get(const fsm_result *r, int64_t i, int32_t *labels_k, uint64_t *adj_bits,
@@ -189,10 +195,18 @@ int fsm_result_embeddings(const fsm_result *r, int64_t i, int64_t *count);
 
 /*
  * fsm_result_copy -- all patterns at once: labels int32[count*k] (row-major), adj_bits
- * uint64[count], support int64[count], embeddings int64[count]; any pointer may be NULL.
+ * uint64[count] (k <= 8 only, as in fsm_result_get), support int64[count], embeddings
+ * int64[count]; any pointer may be NULL.
  */
 int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, int64_t *support,
                     int64_t *embeddings);
+
+/*
+ * fsm_result_pairs -- the canonical edges of every pattern as pair bits, for any k <= 9:
+ * pairs[i] (uint64[count]) has bit q set when the q-th pair of (0,1), (0,2), ..., (k-2,k-1)
+ * (row-major, q from 0) is an edge of pattern i.  FSM_EINVAL for NULL arguments.
+ */
+int fsm_result_pairs(const fsm_result *r, uint64_t *pairs);
 
 /*
  * fsm_result_exact -- exact[i] = 1 when pattern i's support and count were counted exactly, 0

@@ -201,7 +201,8 @@ struct fsm_graph {
 struct fsm_result {
     int k = 0;
     std::vector<int32_t> labels;
-    std::vector<uint64_t> adj;
+    std::vector<uint64_t> adj;           // bit (i*k + j) per canonical edge (k <= 8; 0 for k = 9)
+    std::vector<uint64_t> pairs;         // bit q per canonical edge q of (0,1), (0,2), ..., (k-2,k-1)
     std::vector<int64_t> support, count;
     std::vector<int32_t> exact;          // 1: support counted exactly, 0: estimated (sampled mining)
     std::vector<float> features;         // 32 per pattern, sampled mining with "candidates" only
@@ -216,7 +217,7 @@ struct LevelSet {
     int64_t P = 0;                      // frequent patterns
     uint64_t *lab8 = nullptr, *adj8 = nullptr;
     unsigned long long *clab = nullptr, *sigma = nullptr, *count = nullptr;
-    uint32_t *cadj = nullptr;
+    uint64_t *cadj = nullptr;
     int32_t *fv = nullptr, *fpid = nullptr;
     int64_t N = 0;                      // stored embeddings
     float *feat = nullptr;              // sampled level: 32 features per pattern
@@ -653,7 +654,7 @@ struct Miner {
         rs.qps += nq;
         G->qp_hint[L] = std::max(G->qp_hint[L], nq);
         int32_t *qpat = mem.get<int32_t>(cap);
-        uint32_t *qperm = mem.get<uint32_t>(cap);
+        uint64_t *qperm = mem.get<uint64_t>(cap);
         int64_t M = 1;
         while (M < nq) M <<= 1;
         CodeRec *recs = mem.get<CodeRec>(M);
@@ -663,7 +664,7 @@ struct Miner {
         int64_t *ids = mem.get<int64_t>(nq + 1);
         void *stmp = mem.get<char>((int64_t)scan_temp_bytes(nq) + 16);
         unsigned long long *plab = mem.get<unsigned long long>(nq);
-        uint32_t *padj = mem.get<uint32_t>(nq);
+        uint64_t *padj = mem.get<uint64_t>(nq);
         ck(launch_assign_patterns(recs, nq, slots, flag, ids, stmp, qpat, plab, padj, st), "assign patterns");
         const int64_t np = nq > 0 ? d2h(ids + nq, st) : 0;
         mem.release(recs);
@@ -675,10 +676,10 @@ struct Miner {
         ck(launch_orbits(K, plab, padj, np, orbit, minorb, st), "orbits");
         ck(launch_pattern_counts(slots, nq, qpat, qcount, pcount, st), "pattern counts");
         uint8_t *live = mem.get<uint8_t>(np);
-        int64_t *words = mem.get<int64_t>(np * 8);
-        int64_t *woff = mem.get<int64_t>(np * 8 + 1);
-        int64_t *doff = mem.get<int64_t>(np * 8);
-        void *stmp2 = mem.get<char>((int64_t)scan_temp_bytes(np * 8) + 16);
+        int64_t *words = mem.get<int64_t>(np * FSM_MAXK);
+        int64_t *woff = mem.get<int64_t>(np * FSM_MAXK + 1);
+        int64_t *doff = mem.get<int64_t>(np * FSM_MAXK);
+        void *stmp2 = mem.get<char>((int64_t)scan_temp_bytes(np * FSM_MAXK) + 16);
         unsigned long long *sigma = mem.get<unsigned long long>(np);
         ck(launch_fill_u64(sigma, ~0ull, np, st), "fill");
         uint32_t *dom = nullptr;
@@ -692,9 +693,9 @@ struct Miner {
             if (G->profile) rs.pass_bytes[L][PASS_FUSED] += rs.final_accepted * 4 * K;   // one bitmap word per position
         } else {
             ck(launch_domain_sizes(K, plab, orbit, minorb, pcount, np, t_live, G->cls_size, live, words, st), "domain sizes");
-            ck(launch_scan_i64(words, woff, np * 8, stmp2, st), "domain scan");
-            ck(launch_domain_offsets(words, woff, np * 8, doff, st), "domain offsets");
-            const int64_t nwords = d2h(woff + np * 8, st);
+            ck(launch_scan_i64(words, woff, np * FSM_MAXK, stmp2, st), "domain scan");
+            ck(launch_domain_offsets(words, woff, np * FSM_MAXK, doff, st), "domain offsets");
+            const int64_t nwords = d2h(woff + np * FSM_MAXK, st);
             dom = mem.get<uint32_t>(nwords);
             ck(cudaMemsetAsync(dom, 0, sizeof(uint32_t) * std::max<int64_t>(nwords, 1), st), "memset");
             // live pattern count (for statistics)
@@ -711,7 +712,7 @@ struct Miner {
             A.orbit = orbit;
             A.dom_off = doff;
             A.dom = dom;
-            sbase = mem.get<int64_t>(cap * 8);
+            sbase = mem.get<int64_t>(cap * FSM_MAXK);
             ck(launch_slot_bases(K, slots, nq, qpat, qperm, live, orbit, doff, sbase, st), "slot bases");
             A.slot_base = sbase;
             A.stats = nullptr;
@@ -759,7 +760,7 @@ struct Miner {
         out.lab8 = mem.get<uint64_t>(nf);
         out.adj8 = mem.get<uint64_t>(nf);
         out.clab = mem.get<unsigned long long>(nf);
-        out.cadj = mem.get<uint32_t>(nf);
+        out.cadj = mem.get<uint64_t>(nf);
         out.sigma = mem.get<unsigned long long>(nf);
         out.count = mem.get<unsigned long long>(nf);
         ck(launch_gather_frequent(K, newid, np, plab, padj, sigma, pcount, out.clab, out.cadj, out.sigma,
@@ -813,7 +814,7 @@ struct Miner {
         s.lab8 = mem.get<uint64_t>(NL);
         s.adj8 = mem.get<uint64_t>(NL);
         s.clab = mem.get<unsigned long long>(NL);
-        s.cadj = mem.get<uint32_t>(NL);
+        s.cadj = mem.get<uint64_t>(NL);
         s.sigma = mem.get<unsigned long long>(NL);
         s.count = mem.get<unsigned long long>(NL);
         unsigned long long *nf = mem.get<unsigned long long>(1);
@@ -857,7 +858,7 @@ struct Miner {
         s.lab8 = mem.get<uint64_t>(NP);
         s.adj8 = mem.get<uint64_t>(NP);
         s.clab = mem.get<unsigned long long>(NP);
-        s.cadj = mem.get<uint32_t>(NP);
+        s.cadj = mem.get<uint64_t>(NP);
         s.sigma = mem.get<unsigned long long>(NP);
         s.count = mem.get<unsigned long long>(NP);
         unsigned long long *nf = mem.get<unsigned long long>(1);
@@ -893,31 +894,41 @@ struct Miner {
     }
 };
 
+// Append one pattern's labels and adjacency (both encodings) from its label and adjacency words.
+void push_pattern(fsm_result *r, int k, unsigned long long clab, uint64_t code) {
+    const int np = k * (k - 1) / 2;
+    for (int c = 0; c < k; ++c) r->labels.push_back((int32_t)clab_get(clab, c));
+    uint64_t bits = 0, pairs = 0;
+    int q = 0;
+    for (int i = 0; i < k; ++i)
+        for (int j = i + 1; j < k; ++j, ++q)
+            if ((code >> (np - 1 - q)) & 1ull) {
+                if (k <= 8) bits |= 1ull << (i * k + j);
+                pairs |= 1ull << q;
+            }
+    r->adj.push_back(bits);
+    r->pairs.push_back(pairs);
+}
+
 void fill_result(fsm_result *r, const LevelSet &s, int k, cudaStream_t st) {
     const int64_t P = s.P;
     std::vector<unsigned long long> lab((size_t)P), sig((size_t)P), cnt((size_t)P);
-    std::vector<uint32_t> adj((size_t)P);
+    std::vector<uint64_t> adj((size_t)P);
     if (P) {
         ck(cudaMemcpyAsync(lab.data(), s.clab, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, st), "copy");
-        ck(cudaMemcpyAsync(adj.data(), s.cadj, sizeof(uint32_t) * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(adj.data(), s.cadj, sizeof(uint64_t) * P, cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaMemcpyAsync(sig.data(), s.sigma, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaMemcpyAsync(cnt.data(), s.count, sizeof(unsigned long long) * P, cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaStreamSynchronize(st), "sync");
     }
     r->k = k;
-    r->labels.resize((size_t)P * k);
-    r->adj.resize((size_t)P);
+    r->labels.clear();
+    r->adj.clear();
+    r->pairs.clear();
     r->support.resize((size_t)P);
     r->count.resize((size_t)P);
-    const int np = k * (k - 1) / 2;
     for (int64_t p = 0; p < P; ++p) {
-        for (int c = 0; c < k; ++c) r->labels[(size_t)p * k + c] = (int32_t)((lab[p] >> (8 * (7 - c))) & 0xff);
-        uint64_t bits = 0;
-        int q = 0;
-        for (int i = 0; i < k; ++i)
-            for (int j = i + 1; j < k; ++j, ++q)
-                if ((adj[p] >> (np - 1 - q)) & 1u) bits |= 1ull << (i * k + j);
-        r->adj[p] = bits;
+        push_pattern(r, k, lab[p], adj[p]);
         r->support[p] = (int64_t)sig[p];
         r->count[p] = (int64_t)cnt[p];
     }
@@ -937,19 +948,19 @@ void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSe
     cudaStream_t st = m.st;
     const int64_t P = cand.P;
     std::vector<unsigned long long> lab((size_t)P), sig((size_t)P), cnt((size_t)P);
-    std::vector<uint32_t> adj((size_t)P);
+    std::vector<uint64_t> adj((size_t)P);
     std::vector<float> pred((size_t)P, 0.f), feat;
     std::vector<uint8_t> keep((size_t)P, 0), unc((size_t)P, 0);
     std::vector<int32_t> cls(64, 0);
     ck(cudaMemcpyAsync(cls.data(), G->cls_size, sizeof(int32_t) * 64, cudaMemcpyDeviceToHost, st), "copy");
     if (P) {
         ck(cudaMemcpyAsync(lab.data(), cand.clab, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
-        ck(cudaMemcpyAsync(adj.data(), cand.cadj, 4 * P, cudaMemcpyDeviceToHost, st), "copy");
+        ck(cudaMemcpyAsync(adj.data(), cand.cadj, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaMemcpyAsync(sig.data(), cand.sigma, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
         ck(cudaMemcpyAsync(cnt.data(), cand.count, 8 * P, cudaMemcpyDeviceToHost, st), "copy");
     }
     // exact results of the recount, by canonical code
-    std::map<std::pair<unsigned long long, uint32_t>, std::pair<int64_t, int64_t>> exact;
+    std::map<std::pair<unsigned long long, uint64_t>, std::pair<int64_t, int64_t>> exact;
     const bool use_model = !G->candidates && G->model != nullptr;
     if (G->candidates && P) {
         feat.resize((size_t)P * 32);
@@ -999,10 +1010,10 @@ void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSe
             m.rs.recount_frontier = N2;
             LevelSet ex = m.extend(sub, pf, true, false, 1.0, need_p);
             std::vector<unsigned long long> el((size_t)ex.P), es((size_t)ex.P), ec((size_t)ex.P);
-            std::vector<uint32_t> ea((size_t)ex.P);
+            std::vector<uint64_t> ea((size_t)ex.P);
             if (ex.P) {
                 ck(cudaMemcpyAsync(el.data(), ex.clab, 8 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
-                ck(cudaMemcpyAsync(ea.data(), ex.cadj, 4 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
+                ck(cudaMemcpyAsync(ea.data(), ex.cadj, 8 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
                 ck(cudaMemcpyAsync(es.data(), ex.sigma, 8 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
                 ck(cudaMemcpyAsync(ec.data(), ex.count, 8 * ex.P, cudaMemcpyDeviceToHost, st), "copy");
             }
@@ -1012,7 +1023,6 @@ void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSe
     }
     ck(cudaStreamSynchronize(st), "sync");
     r->k = k;
-    const int np = k * (k - 1) / 2;
     for (int64_t q = 0; q < P; ++q) {
         const double est = (double)sig[q] / p;
         int64_t sup = 0, c = 0;
@@ -1026,7 +1036,7 @@ void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSe
                 // of the true ones (lower bound) and no orbit outgrows its label class (upper)
                 double hi = 1e300;
                 for (int cc = 0; cc < k; ++cc)
-                    hi = std::min(hi, (double)cls[(lab[q] >> (8 * (7 - cc))) & 0xff]);
+                    hi = std::min(hi, (double)cls[clab_get(lab[q], cc)]);
                 const double lo = (double)sig[q];
                 const double pr = std::exp(std::min((double)pred[q], 60.0));
                 sup = (int64_t)std::llround(std::max(lo, std::min(hi, pr)));
@@ -1045,13 +1055,7 @@ void finish_sampled(Miner &m, fsm_result *r, const LevelSet &cand, const LevelSe
             sup = (int64_t)std::llround(est);
             c = (int64_t)std::llround((double)cnt[q] / p);
         }
-        for (int cc = 0; cc < k; ++cc) r->labels.push_back((int32_t)((lab[q] >> (8 * (7 - cc))) & 0xff));
-        uint64_t bits = 0;
-        int qq = 0;
-        for (int i = 0; i < k; ++i)
-            for (int j = i + 1; j < k; ++j, ++qq)
-                if ((adj[q] >> (np - 1 - qq)) & 1u) bits |= 1ull << (i * k + j);
-        r->adj.push_back(bits);
+        push_pattern(r, k, lab[q], adj[q]);
         r->support.push_back(sup);
         r->count.push_back(c);
         r->exact.push_back(ex);
@@ -1234,7 +1238,7 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
         if (!out) fail(FSM_EINVAL, "out is NULL");
         *out = nullptr;
         if (!g) fail(FSM_EINVAL, "graph is NULL");
-        if (k < 1 || k > FSM_MAXK) fail(FSM_EINVAL, "k must be in [1, 8]");
+        if (k < 1 || k > FSM_MAXK) fail(FSM_EINVAL, "k must be in [1, 9]");
         if (min_support < 1) fail(FSM_EINVAL, "min_support must be >= 1");
         if (!(sample_rate > 0.0 && sample_rate <= 1.0)) fail(FSM_EINVAL, "sample_rate must be in (0, 1]");
         const bool sampled = sample_rate < 1.0 && k >= 3;   // levels 1 and 2 join no pieces
@@ -1248,6 +1252,8 @@ int fsm_mine(fsm_graph *g, int32_t k, int64_t min_support, double sample_rate, f
                                    "without sampling quotas, only");
         if ((V == FSM_EXPLORE_SV || V == FSM_EXPLORE_TV_EDGELIST) && k > 7)
             fail(FSM_EUNSUPPORTED, "the exploration ablations support k <= 7");
+        if (sampled && k > 8)
+            fail(FSM_EUNSUPPORTED, "rate-sampled mining (32 features over at most 8 positions) supports k <= 8");
         ck(cudaSetDevice(g->device), "cudaSetDevice");
         cudaStream_t st = g->stream;
         cudaEvent_t ev0, ev1, evf;
@@ -1400,6 +1406,7 @@ int64_t fsm_result_count(const fsm_result *r) {
 
 int fsm_result_get(const fsm_result *r, int64_t i, int32_t *labels_k, uint64_t *adj_bits, int64_t *support) {
     if (!r || i < 0 || i >= (int64_t)r->support.size()) { g_last_error = "bad result or index"; return FSM_EINVAL; }
+    if (adj_bits && r->k > 8) { g_last_error = "adj_bits holds k <= 8: use fsm_result_pairs"; return FSM_EUNSUPPORTED; }
     if (labels_k) std::memcpy(labels_k, r->labels.data() + (size_t)i * r->k, sizeof(int32_t) * r->k);
     if (adj_bits) *adj_bits = r->adj[(size_t)i];
     if (support) *support = r->support[(size_t)i];
@@ -1414,11 +1421,18 @@ int fsm_result_embeddings(const fsm_result *r, int64_t i, int64_t *count) {
 
 int fsm_result_copy(const fsm_result *r, int32_t *labels, uint64_t *adj_bits, int64_t *support, int64_t *embeddings) {
     if (!r) { g_last_error = "result is NULL"; return FSM_EINVAL; }
+    if (adj_bits && r->k > 8) { g_last_error = "adj_bits holds k <= 8: use fsm_result_pairs"; return FSM_EUNSUPPORTED; }
     const size_t P = r->support.size();
     if (labels && P) std::memcpy(labels, r->labels.data(), sizeof(int32_t) * P * r->k);
     if (adj_bits && P) std::memcpy(adj_bits, r->adj.data(), sizeof(uint64_t) * P);
     if (support && P) std::memcpy(support, r->support.data(), sizeof(int64_t) * P);
     if (embeddings && P) std::memcpy(embeddings, r->count.data(), sizeof(int64_t) * P);
+    return FSM_OK;
+}
+
+int fsm_result_pairs(const fsm_result *r, uint64_t *pairs) {
+    if (!r || !pairs) { g_last_error = "NULL argument"; return FSM_EINVAL; }
+    if (!r->pairs.empty()) std::memcpy(pairs, r->pairs.data(), sizeof(uint64_t) * r->pairs.size());
     return FSM_OK;
 }
 

@@ -1,16 +1,31 @@
 // fsm_canon.cuh -- canonical codes of small labeled graphs on the device.
 //
-// The canonical code of a labeled K-vertex graph (K <= 8) is the lexicographically smallest
+// The canonical code of a labeled K-vertex graph (K <= 9) is the lexicographically smallest
 // (label sequence, adjacency sequence A(0,1), A(0,2), ..., A(K-2,K-1)) over all vertex orders
-// (Section 4.4's isomorphism check, done once per distinct quick pattern).  Only label-
-// preserving orders of the label-sorted positions can be smallest, so only those are
-// enumerated (at most 8! = 40320).
+// (Section 4.4's isomorphism check, done once per distinct quick pattern).  The smallest label
+// sequence is the sorted one, so only orders that keep each label's positions can be smallest.
+// When there are few of those (at most FSM_ENUM_MAX) they are enumerated; otherwise (up to
+// 9! = 362880 for an unlabeled 9-vertex graph) a depth-first search over ordered cells finds
+// the minimum:
+//   * positions are filled in order; the vertex at position c is taken from the cell that
+//     holds position c (initially the cells are the label segments);
+//   * once it is chosen, row c of the code (its adjacency to positions c+1..K-1) is smallest
+//     when, inside every later cell, its non-neighbours come before its neighbours, so each
+//     cell is split that way, which fixes row c;
+//   * a branch whose code prefix is above the best complete code so far is cut, and of two
+//     twins in one cell (same neighbours apart from each other; swapping them is an
+//     automorphism fixing everything chosen) only the first is tried.
+// Every order the search can complete is label-sorted and row-by-row minimal given the rows
+// before, which is where the lexicographic minimum lies, and pruning only drops branches that
+// cannot beat or differ from what is kept; so both ways give the same code.
 #pragma once
 #include "fsm_device.cuh"
 
+#define FSM_ENUM_MAX 5040   // label-preserving orders enumerated directly (7!)
+
 namespace fsm {
 
-__device__ __forceinline__ bool next_perm(int *a, int n) {
+FSM_HD bool next_perm(int *a, int n) {
     int i = n - 2;
     while (i >= 0 && a[i] >= a[i + 1]) --i;
     if (i < 0) {
@@ -26,7 +41,7 @@ __device__ __forceinline__ bool next_perm(int *a, int n) {
 
 // Advance perm to the next permutation that keeps every position's label (positions with equal
 // labels form contiguous segments seg_start[c]..); false after the last one.
-__device__ __forceinline__ bool next_label_perm(int K, const int *seg_start, int *perm) {
+FSM_HD bool next_label_perm(int K, const int *seg_start, int *perm) {
     int c = K - 1;
     while (c >= 0) {
         const int s = seg_start[c];
@@ -36,41 +51,155 @@ __device__ __forceinline__ bool next_label_perm(int K, const int *seg_start, int
     return false;
 }
 
-__device__ __forceinline__ uint32_t adj_code(int K, const uint32_t *adj, const int *perm) {
-    uint32_t code = 0;
+FSM_HD uint64_t adj_code(int K, const uint32_t *adj, const int *perm) {
+    uint64_t code = 0;
     for (int c1 = 0; c1 < K; ++c1) {
         const uint32_t row = adj[perm[c1]];
-        for (int c2 = c1 + 1; c2 < K; ++c2) code = (code << 1) | ((row >> perm[c2]) & 1u);
+        for (int c2 = c1 + 1; c2 < K; ++c2) code = (code << 1) | (uint64_t)((row >> perm[c2]) & 1u);
     }
     return code;
 }
 
-// Canonical code of a labeled K-vertex graph: the smallest (label sequence, adjacency
-// sequence) over all vertex orders.  The smallest label sequence is the sorted one, so only
-// label-preserving orders of the sorted positions are enumerated.  inv[h] = canonical
-// position of vertex h in the first optimal order.
-static __device__ __noinline__ void canonicalise(int K, const int *lab, const uint32_t *adj, unsigned long long &clab,
-                             uint32_t &cadj, uint32_t &inv) {
-    int perm[FSM_MAXK], seg[FSM_MAXK], best[FSM_MAXK];
+// Vertices sorted by (label, index) into perm; seg[c] = first position of c's label segment.
+// Returns the number of label-preserving orders (product of the segments' factorials).
+FSM_HD int64_t label_sort(int K, const int *lab, int *perm, int *seg) {
     for (int h = 0; h < K; ++h) perm[h] = h;
     for (int a = 1; a < K; ++a)          // insertion sort by label (stable)
         for (int b = a; b > 0 && lab[perm[b - 1]] > lab[perm[b]]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
-    for (int c = 0; c < K; ++c) seg[c] = (c > 0 && lab[perm[c]] == lab[perm[c - 1]]) ? seg[c - 1] : c;
-    // within each segment start from ascending vertex index (next_perm enumerates from there)
-    for (int c = 0; c < K; ++c)
-        for (int b = c; b > seg[c] && perm[b - 1] > perm[b]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
-    uint32_t bc = 0xffffffffu;
-    do {
-        const uint32_t code = adj_code(K, adj, perm);
-        if (code < bc) {
-            bc = code;
-            for (int c = 0; c < K; ++c) best[c] = perm[c];
+    int64_t orders = 1;
+    for (int c = 0; c < K; ++c) {
+        seg[c] = (c > 0 && lab[perm[c]] == lab[perm[c - 1]]) ? seg[c - 1] : c;
+        orders *= (int64_t)(c - seg[c] + 1);
+    }
+    return orders;
+}
+
+// The depth-first search of the header.  lab / adj: the graph; first >= 0 forces that vertex to
+// position 0 (the graph with that vertex marked by a label of its own below all others).  Returns
+// the smallest adjacency code; best[c] = the vertex at position c of one order attaining it.
+static __host__ __device__ __noinline__ uint64_t canon_search(int K, const int *lab, const uint32_t *adj, int first,
+                                                              int *best) {
+    int ord[FSM_MAXK + 1][FSM_MAXK];   // per depth: the vertices by position, grouped in cells
+    uint32_t bnd[FSM_MAXK + 1];        // per depth: bit p set when position p ends its cell
+    uint32_t seen[FSM_MAXK + 1];       // per depth: vertices already taken up at that position
+    uint32_t expd[FSM_MAXK + 1];       // per depth: those of them whose branch was searched
+    uint64_t pre[FSM_MAXK + 1];        // per depth: the code rows above it
+    const int np = K * (K - 1) / 2;
+    {
+        int n0 = 0;
+        if (first >= 0) ord[0][n0++] = first;
+        for (int h = 0; h < K; ++h)
+            if (h != first) ord[0][n0++] = h;
+        const int s0 = first >= 0 ? 1 : 0;
+        for (int a = s0 + 1; a < K; ++a)
+            for (int b = a; b > s0 && lab[ord[0][b - 1]] > lab[ord[0][b]]; --b) {
+                const int t = ord[0][b]; ord[0][b] = ord[0][b - 1]; ord[0][b - 1] = t;
+            }
+        bnd[0] = 1u << (K - 1);
+        if (first >= 0) bnd[0] |= 1u;
+        for (int p = s0; p + 1 < K; ++p)
+            if (lab[ord[0][p]] != lab[ord[0][p + 1]]) bnd[0] |= 1u << p;
+    }
+    seen[0] = expd[0] = 0;
+    pre[0] = 0;
+    bool have = false;
+    uint64_t bc = 0;
+    int c = 0;
+    for (;;) {
+        if (c >= K - 1) {
+            // every row is known (the last position is what is left)
+            if (!have || pre[c] < bc) {
+                bc = pre[c];
+                have = true;
+                for (int p = 0; p < K; ++p) best[p] = ord[c][p];
+            }
+            if (c == 0) break;
+            --c;
+            continue;
         }
-    } while (next_label_perm(K, seg, perm));
+        int e = c;
+        while (!((bnd[c] >> e) & 1u)) ++e;
+        // next candidate for position c: not taken up yet, and no twin of a searched one (twins
+        // of twins need not be twins, so only searched vertices are compared)
+        int x = -1;
+        for (int y = c; y <= e && x < 0; ++y) {
+            const int w = ord[c][y];
+            if ((seen[c] >> w) & 1u) continue;
+            seen[c] |= 1u << w;
+            bool twin = false;
+            for (int w2 = 0; w2 < K && !twin; ++w2)
+                if (((expd[c] >> w2) & 1u) && (adj[w] & ~(1u << w2)) == (adj[w2] & ~(1u << w))) twin = true;
+            if (!twin) x = y;
+        }
+        if (x < 0) {
+            if (c == 0) break;
+            --c;
+            continue;
+        }
+        const int w = ord[c][x];
+        expd[c] |= 1u << w;
+        int *o = ord[c + 1];
+        for (int p = 0; p < K; ++p) o[p] = ord[c][p];
+        o[x] = o[c];
+        o[c] = w;
+        uint32_t nb = bnd[c] | (1u << c);
+        // split every later cell: non-neighbours of w first; row c follows
+        uint64_t row = 0;
+        for (int a = c + 1; a < K;) {
+            int b = a;
+            while (!((nb >> b) & 1u)) ++b;
+            int tmp[FSM_MAXK], n0 = 0;
+            for (int p = a; p <= b; ++p)
+                if (!((adj[w] >> o[p]) & 1u)) tmp[n0++] = o[p];
+            const int nn = n0;
+            for (int p = a; p <= b; ++p)
+                if ((adj[w] >> o[p]) & 1u) tmp[n0++] = o[p];
+            for (int p = a; p <= b; ++p) {
+                o[p] = tmp[p - a];
+                row = (row << 1) | (uint64_t)(p - a >= nn ? 1u : 0u);
+            }
+            if (nn > 0 && nn <= b - a) nb |= 1u << (a + nn - 1);
+            a = b + 1;
+        }
+        const int len = K - 1 - c;
+        const uint64_t prefix = (pre[c] << len) | row;
+        const int used = np - (K - 1 - c) * (K - 2 - c) / 2;   // bits in rows 0..c
+        if (have && prefix > (bc >> (np - used))) continue;    // cannot reach the best: next candidate
+        bnd[c + 1] = nb;
+        pre[c + 1] = prefix;
+        seen[c + 1] = expd[c + 1] = 0;
+        ++c;
+    }
+    return bc;
+}
+
+// Canonical code of a labeled K-vertex graph: the smallest (label sequence, adjacency
+// sequence) over all vertex orders.  clab: label word; cadj: adjacency word; inv: vertex h ->
+// canonical position (4 bits each) in one optimal order.
+static __host__ __device__ __noinline__ void canonicalise(int K, const int *lab, const uint32_t *adj,
+                                                          unsigned long long &clab, uint64_t &cadj, uint64_t &inv) {
+    int perm[FSM_MAXK], seg[FSM_MAXK], best[FSM_MAXK];
+    const int64_t orders = label_sort(K, lab, perm, seg);
+    uint64_t bc;
+    if (orders <= FSM_ENUM_MAX) {
+        // within each segment start from ascending vertex index (next_perm enumerates from there)
+        for (int c = 0; c < K; ++c)
+            for (int b = c; b > seg[c] && perm[b - 1] > perm[b]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
+        bc = ~0ull;
+        do {
+            const uint64_t code = adj_code(K, adj, perm);
+            if (code < bc) {
+                bc = code;
+                for (int c = 0; c < K; ++c) best[c] = perm[c];
+            }
+        } while (next_label_perm(K, seg, perm));
+    } else {
+        bc = canon_search(K, lab, adj, -1, best);
+    }
     unsigned long long l = 0;
-    for (int c = 0; c < K; ++c) l |= (unsigned long long)(lab[best[c]] & 0xff) << (8 * (7 - c));
-    uint32_t iv = 0;
-    for (int c = 0; c < K; ++c) iv |= (uint32_t)c << (3 * best[c]);
+    for (int c = 0; c < K; ++c) l |= clab_put(c, lab[best[c]]);
+    uint64_t iv = 0;
+    for (int c = 0; c < K; ++c) iv |= nib_put(best[c], c);
     clab = l;
     cadj = bc;
     inv = iv;
@@ -123,40 +252,62 @@ static __device__ __noinline__ void key_graph(int V, int L, uint64_t key, const 
     join_graph(L, srows, i, tj0, tj1, txx, cross, adjH);
 }
 
-__device__ __forceinline__ void decode_code(int K, unsigned long long clab, uint32_t cadj, int *lab, uint32_t *adj) {
+FSM_HD void decode_code(int K, unsigned long long clab, uint64_t cadj, int *lab, uint32_t *adj) {
     const int np = K * (K - 1) / 2;
-    for (int c = 0; c < K; ++c) { lab[c] = (int)(clab >> (8 * (7 - c))) & 0xff; adj[c] = 0; }
+    for (int c = 0; c < K; ++c) { lab[c] = clab_get(clab, c); adj[c] = 0; }
     int q = 0;
     for (int c1 = 0; c1 < K; ++c1)
         for (int c2 = c1 + 1; c2 < K; ++c2, ++q)
-            if ((cadj >> (np - 1 - q)) & 1u) { adj[c1] |= 1u << c2; adj[c2] |= 1u << c1; }
+            if ((cadj >> (np - 1 - q)) & 1ull) { adj[c1] |= 1u << c2; adj[c2] |= 1u << c1; }
 }
 
 
+// Orbit representatives by marking: c and c' (of one label) share an orbit exactly when the
+// graph with c marked and the graph with c' marked have the same canonical code.  seg[c] = the
+// first position of c's label segment.
+static __host__ __device__ __noinline__ void orbit_reps_search(int K, const int *lab, const uint32_t *adj,
+                                                               const int *seg, int *rep) {
+    uint64_t mark[FSM_MAXK];
+    int tmp[FSM_MAXK];
+    for (int c = 0; c < K; ++c) {
+        rep[c] = c;
+        mark[c] = canon_search(K, lab, adj, c, tmp);
+        for (int c2 = seg[c]; c2 < c; ++c2)
+            if (rep[c2] == c2 && mark[c2] == mark[c]) { rep[c] = c2; break; }
+    }
+}
+
 // Orbit representatives of a canonical pattern: rep[c] = the smallest canonical position that
-// an automorphism (a label-preserving order with the same adjacency sequence) maps c to.
-static __device__ __noinline__ void orbit_reps(int K, unsigned long long clab, uint32_t cadj, int *rep) {
+// an automorphism (a label-preserving order with the same adjacency sequence) maps c to.  With
+// few label-preserving orders they are enumerated, otherwise found by marking.
+static __host__ __device__ __noinline__ void orbit_reps(int K, unsigned long long clab, uint64_t cadj, int *rep) {
     int lab[FSM_MAXK], perm[FSM_MAXK], seg[FSM_MAXK];
     uint32_t adj[FSM_MAXK];
     decode_code(K, clab, cadj, lab, adj);
+    int64_t orders = 1;
     for (int c = 0; c < K; ++c) {
         perm[c] = c;
         rep[c] = c;
         seg[c] = (c > 0 && lab[c] == lab[c - 1]) ? seg[c - 1] : c;
+        orders *= (int64_t)(c - seg[c] + 1);
     }
-    do {
-        if (adj_code(K, adj, perm) == cadj)
-            for (int c = 0; c < K; ++c) if (perm[c] < rep[c]) rep[c] = perm[c];
-    } while (next_label_perm(K, seg, perm));
+    if (orders <= FSM_ENUM_MAX) {
+        do {
+            if (adj_code(K, adj, perm) == cadj)
+                for (int c = 0; c < K; ++c) if (perm[c] < rep[c]) rep[c] = perm[c];
+        } while (next_label_perm(K, seg, perm));
+        return;
+    }
+    orbit_reps_search(K, lab, adj, seg, rep);
 }
 
 // A canonical code of K <= 7 vertices in 63 bits: label of canonical position c at bits
 // 6c..6c+5, the adjacency sequence (as canonicalise returns it) from bit 42.  Bit 63 stays clear,
 // so no packed code equals FSM_EMPTY_KEY.
-FSM_HD uint64_t pack_code(int K, unsigned long long clab, uint32_t cadj) {
+FSM_HD uint64_t pack_code(int K, unsigned long long clab, uint64_t cadj) {
     uint64_t k = 0;
-    for (int c = 0; c < K; ++c) k |= ((clab >> (8 * (7 - c))) & 63ull) << (6 * c);
-    return k | ((uint64_t)cadj << 42);
+    for (int c = 0; c < K; ++c) k |= (uint64_t)clab_get(clab, c) << (6 * c);
+    return k | (cadj << 42);
 }
 
 } // namespace fsm

@@ -15,8 +15,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#define FSM_MAXK 8
-#define FSM_MAXL 6               // largest stored level that is still extended (k <= 8)
+#define FSM_MAXK 9
+#define FSM_MAXL 7               // largest stored level that is still extended (k <= 9)
 
 // exploration variants of the extension kernel (option "explore" and "quick_pattern")
 #define FSM_EXPLORE_TV 0           // two-vertex exploration, index-based quick patterns (the method)
@@ -127,22 +127,40 @@ FSM_HD uint32_t tri_index(int x, int y, int z) {
 
 // ---------------------------------------------------------------------------- QP keys
 //
-// 64-bit key: pid_s (24 bits) | piece index (19) | i (3) | j (2) | cross bits (2*(l-1) <= 10).
+// 64-bit key: pid_s (24 bits) | piece index (19) | i (3) | j (2) | cross bits (2*(l-1) <= 12).
 // Cross bit (p', q): s position p (p' = p minus one if p > i) adjacent to the piece's q-th
-// non-joining vertex, bit index p' * 2 + q.
+// non-joining vertex, bit index p' * 2 + q.  The top four bits stay clear, so no key equals
+// FSM_EMPTY_KEY.
 
 #define FSM_PID_BITS 24
 FSM_HD uint64_t make_key(uint32_t pid_s, uint32_t pidx, int i, int j, uint32_t cross) {
-    return ((uint64_t)pid_s << 34) | ((uint64_t)pidx << 15) | ((uint64_t)i << 12) |
-           ((uint64_t)j << 10) | (uint64_t)cross;
+    return ((uint64_t)pid_s << 36) | ((uint64_t)pidx << 17) | ((uint64_t)i << 14) |
+           ((uint64_t)j << 12) | (uint64_t)cross;
 }
 FSM_HD void split_key(uint64_t key, uint32_t &pid_s, uint32_t &pidx, int &i, int &j, uint32_t &cross) {
-    pid_s = (uint32_t)(key >> 34);
-    pidx = (uint32_t)(key >> 15) & ((1u << 19) - 1);
-    i = (int)(key >> 12) & 7;
-    j = (int)(key >> 10) & 3;
-    cross = (uint32_t)key & 1023u;
+    pid_s = (uint32_t)(key >> 36) & ((1u << FSM_PID_BITS) - 1);
+    pidx = (uint32_t)(key >> 17) & ((1u << 19) - 1);
+    i = (int)(key >> 14) & 7;
+    j = (int)(key >> 12) & 3;
+    cross = (uint32_t)key & 4095u;
 }
+
+// ---------------------------------------------------------------------------- pattern words
+//
+// A pattern of K <= 9 vertices in canonical order is held as
+//   a label word: the label of canonical position c (6 bits; labels are below 64) at bits
+//     6 (8 - c) .. 6 (8 - c) + 5, so that integer order is label-sequence order;
+//   an adjacency word: the adjacency sequence A(0,1), A(0,2), ..., A(K-2,K-1), first pair most
+//     significant (at most 36 bits), so that integer order is sequence order;
+//   an orbit word: the orbit representative of canonical position c at bits 4c .. 4c + 3;
+// and a vertex order (local vertex h -> canonical position) as 4 bits per vertex, at 4h.
+
+FSM_HD int clab_get(unsigned long long clab, int c) { return (int)(clab >> (6 * (FSM_MAXK - 1 - c))) & 63; }
+FSM_HD unsigned long long clab_put(int c, int lab) {
+    return (unsigned long long)(lab & 63) << (6 * (FSM_MAXK - 1 - c));
+}
+FSM_HD int nib_get(uint64_t w, int h) { return (int)(w >> (4 * h)) & 15; }
+FSM_HD uint64_t nib_put(int h, int v) { return (uint64_t)(v & 15) << (4 * h); }
 
 FSM_HD uint64_t mix64(uint64_t x) {
     x ^= x >> 31; x *= 0x7fb5d329728ea185ull;

@@ -37,7 +37,7 @@ struct QPTab {
     unsigned long long *keys;      // [cap], FSM_EMPTY_KEY when free
     unsigned long long *count;     // [cap] accepted joins per key
     int32_t *pattern;              // [cap] pattern id of the key (after canonicalisation)
-    uint32_t *perm;                // [cap] local vertex h -> canonical position, 3 bits each
+    uint64_t *perm;                // [cap] local vertex h -> canonical position, 4 bits each (nib_get)
     uint64_t mask;                 // cap - 1 (cap a power of two)
     unsigned long long *used;      // occupied slots
     unsigned long long max_used;   // overflow threshold (load factor 1/2)
@@ -64,10 +64,10 @@ struct ExtArgs {
     QPTab qp;
     // domains (PASS_DOMAIN)
     const uint8_t *live;           // [P'] pattern has domains
-    const uint64_t *orbit;         // [P'] 8 bytes: orbit representative per canonical position
-    const int64_t *dom_off;        // [P'*8] word offset per orbit representative
+    const uint64_t *orbit;         // [P'] orbit word: representative per canonical position
+    const int64_t *dom_off;        // [P'*FSM_MAXK] word offset per orbit representative
     uint32_t *dom;
-    const int64_t *slot_base;      // [cap*8] bitmap word offset per (key slot, local position), -1 none
+    const int64_t *slot_base;      // [cap*FSM_MAXK] bitmap word offset per (key slot, local position), -1 none
     // emission (PASS_EMIT)
     const int32_t *newid;          // [P'] id among frequent patterns, -1 otherwise
     int32_t *out_v;                // SoA [K][out_N]
@@ -319,13 +319,13 @@ static __device__ __noinline__ void resolve_slot(const ResolveArgs A, int64_t sl
     uint32_t adj[FSM_MAXK];
     key_graph(A.explore, A.level, key, A.pat_lab, A.pat_adj, K, lab, adj);
     unsigned long long clab;
-    uint32_t cadj, inv;
+    uint64_t cadj, inv;
     canonicalise(K, lab, adj, clab, cadj, inv);
     orbit_reps(K, clab, cadj, rep);
     int64_t pre[FSM_MAXK], words = 0;
     for (int c = 0; c < K; ++c) {
         pre[c] = words;
-        if (rep[c] == c) words += ((int64_t)__ldg(A.cls_size + ((clab >> (8 * (7 - c))) & 0xff)) + 31) / 32;
+        if (rep[c] == c) words += ((int64_t)__ldg(A.cls_size + clab_get(clab, c)) + 31) / 32;
     }
     const uint64_t pk = pack_code(K, clab, cadj);
     uint64_t h = mix64(pk) & A.code_mask;
@@ -346,7 +346,7 @@ static __device__ __noinline__ void resolve_slot(const ResolveArgs A, int64_t sl
     }
     long long *so = A.slot_off + slot * 8;
     for (int hh = K - 1; hh >= 0; --hh) {
-        const long long v = (long long)(off - 1ull) + pre[rep[(inv >> (3 * hh)) & 7]];
+        const long long v = (long long)(off - 1ull) + pre[rep[nib_get(inv, hh)]];
         if (hh) st_relaxed_s64(so + hh, v); else st_release_s64(so, v);
     }
 }
@@ -429,7 +429,7 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
     if (slot < 0) { atomicOr(A.err, FSM_ERR_QP_MISSING); return; }
     if (PASS == PASS_DOMAIN) {
         // one load per position: the bitmap of the orbit this key's position h lands in
-        const int64_t *sb = A.slot_base + slot * 8;
+        const int64_t *sb = A.slot_base + slot * FSM_MAXK;
         if (__ldg(sb) < 0) return;   // pattern without domains
 #pragma unroll
         for (int h = 0; h < L; ++h) {
@@ -455,7 +455,7 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
         return;
     }
     const int32_t P = __ldg(A.qp.pattern + slot);
-    const uint32_t perm = __ldg(A.qp.perm + slot);
+    const uint64_t perm = __ldg(A.qp.perm + slot);
     {
         // PASS_EMIT
         const int32_t nid = __ldg(A.newid + P);
@@ -469,10 +469,7 @@ __device__ __forceinline__ void accept(const ExtArgs &A, CountCache *cc, DomCach
         const int64_t pos = (int64_t)base + __popc(act & ((1u << lane) - 1u));
         if (pos >= A.out_N) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
 #pragma unroll
-        for (int h = 0; h < K; ++h) {
-            const int c = (perm >> (3 * h)) & 7;
-            A.out_v[(int64_t)c * A.out_N + pos] = gid[h];
-        }
+        for (int h = 0; h < K; ++h) A.out_v[(int64_t)nib_get(perm, h) * A.out_N + pos] = gid[h];
         A.out_pid[pos] = nid;
     }
 }
@@ -518,7 +515,7 @@ __device__ __forceinline__ void accept_sorted(const ExtArgs &A, CountCache *cc, 
     const int64_t slot = qp_find(A.qp, key);
     if (slot < 0) { atomicOr(A.err, FSM_ERR_QP_MISSING); return; }
     if (PASS == PASS_DOMAIN) {
-        const int64_t *sb = A.slot_base + slot * 8;
+        const int64_t *sb = A.slot_base + slot * FSM_MAXK;
         if (__ldg(sb) < 0) return;
 #pragma unroll
         for (int h = 0; h < K; ++h) {
@@ -531,13 +528,13 @@ __device__ __forceinline__ void accept_sorted(const ExtArgs &A, CountCache *cc, 
     }
     if (PASS == PASS_EMIT) {
         const int32_t P = __ldg(A.qp.pattern + slot);
-        const uint32_t perm = __ldg(A.qp.perm + slot);
+        const uint64_t perm = __ldg(A.qp.perm + slot);
         const int32_t nid = __ldg(A.newid + P);
         if (nid < 0) return;
         const unsigned long long pos = atomicAdd(A.out_cursor, 1ull);
         if ((int64_t)pos >= A.out_N) { atomicOr(A.err, FSM_ERR_BOUNDS); return; }
 #pragma unroll
-        for (int h = 0; h < K; ++h) A.out_v[(int64_t)((perm >> (3 * h)) & 7) * A.out_N + (int64_t)pos] = sg[h];
+        for (int h = 0; h < K; ++h) A.out_v[(int64_t)nib_get(perm, h) * A.out_N + (int64_t)pos] = sg[h];
         A.out_pid[pos] = nid;
     }
 }
@@ -1108,5 +1105,8 @@ cudaError_t launch_extend_edgelist(int pass, int L, const ExtArgs &A, int grid, 
 cudaError_t occupancy_extend_edgelist(int pass, int L, int *blocks_per_sm);
 cudaError_t launch_extend_quota(int pass, int L, const ExtArgs &A, int grid, cudaStream_t st);
 cudaError_t occupancy_extend_quota(int pass, int L, int *blocks_per_sm);
+// size 7 -> 9 (count and domain passes of the method's own form)
+cudaError_t launch_extend_l7(int pass, const ExtArgs &A, int grid, cudaStream_t st);
+cudaError_t occupancy_extend_l7(int pass, int *blocks_per_sm);
 
 } // namespace fsm

@@ -14,6 +14,7 @@ cudaError_t launch_extend_count(int L, int V, const ExtArgs &A, int grid, cudaSt
     case 4: extend_kernel<4, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
     case 5: extend_kernel<5, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
     case 6: extend_kernel<6, PASS_COUNT><<<grid, 256, FSM_COUNT_SMEM, st>>>(A); break;
+    case 7: return launch_extend_l7(PASS_COUNT, A, grid, st);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -30,6 +31,7 @@ cudaError_t occupancy_extend_count(int L, int V, int *blocks_per_sm) {
     case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<4, PASS_COUNT>, 256, FSM_COUNT_SMEM);
     case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<5, PASS_COUNT>, 256, FSM_COUNT_SMEM);
     case 6: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<6, PASS_COUNT>, 256, FSM_COUNT_SMEM);
+    case 7: return occupancy_extend_l7(PASS_COUNT, blocks_per_sm);
     default: return cudaErrorInvalidValue;
     }
 }

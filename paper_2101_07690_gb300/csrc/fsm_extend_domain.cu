@@ -14,6 +14,7 @@ cudaError_t launch_extend_domain(int L, int V, const ExtArgs &A, int grid, cudaS
     case 4: extend_kernel<4, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
     case 5: extend_kernel<5, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
     case 6: extend_kernel<6, PASS_DOMAIN><<<grid, 256, 0, st>>>(A); break;
+    case 7: return launch_extend_l7(PASS_DOMAIN, A, grid, st);
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -30,6 +31,7 @@ cudaError_t occupancy_extend_domain(int L, int V, int *blocks_per_sm) {
     case 4: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<4, PASS_DOMAIN>, 256, 0);
     case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<5, PASS_DOMAIN>, 256, 0);
     case 6: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, extend_kernel<6, PASS_DOMAIN>, 256, 0);
+    case 7: return occupancy_extend_l7(PASS_DOMAIN, blocks_per_sm);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -17,6 +17,9 @@ cudaError_t launch_variant_pass(int L, const ExtArgs &A, int grid, cudaStream_t 
     case 6:
         if constexpr (MAXL >= 6) { extend_kernel<6, PASS, V><<<grid, 256, smem, st>>>(A); break; }
         return cudaErrorInvalidValue;
+    case 7:   // a size-9 level is the last one: no emission pass
+        if constexpr (MAXL >= 7 && PASS != PASS_EMIT) { extend_kernel<7, PASS, V><<<grid, 256, smem, st>>>(A); break; }
+        return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -33,6 +36,10 @@ cudaError_t occupancy_variant_pass(int L, int *bps) {
     case 5: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, extend_kernel<5, PASS, V>, 256, smem);
     case 6:
         if constexpr (MAXL >= 6) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, extend_kernel<6, PASS, V>, 256, smem);
+        return cudaErrorInvalidValue;
+    case 7:
+        if constexpr (MAXL >= 7 && PASS != PASS_EMIT)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, extend_kernel<7, PASS, V>, 256, smem);
         return cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
     }

@@ -355,14 +355,14 @@ namespace {
 
 __global__ void qp_canon_kernel(int L, int V, const unsigned long long *keys, const int64_t *slots, int64_t nq,
                                 const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
-                                uint32_t *perm_out) {
+                                uint64_t *perm_out) {
     for (int64_t q = gtid(); q < nq; q += gstride()) {
         const int64_t slot = slots[q];
         int K, labH[FSM_MAXK];
         uint32_t adjH[FSM_MAXK];
         key_graph(V, L, keys[slot], pat_lab8, pat_adj8, K, labH, adjH);
         unsigned long long cl;
-        uint32_t ca, inv;
+        uint64_t ca, inv;
         canonicalise(K, labH, adjH, cl, ca, inv);
         recs[q].lab = cl;
         recs[q].adj = ca;
@@ -389,7 +389,7 @@ __global__ void bitonic_step_kernel(CodeRec *r, int64_t M, int64_t j, int64_t k)
 
 __global__ void pad_recs_kernel(CodeRec *r, int64_t n, int64_t M) {
     for (int64_t t = n + gtid(); t < M; t += gstride()) {
-        r[t].lab = ~0ull; r[t].adj = ~0u; r[t].idx = ~0u;
+        r[t].lab = ~0ull; r[t].adj = ~0ull; r[t].idx = ~0u;
     }
 }
 
@@ -400,7 +400,7 @@ __global__ void boundary_flags_kernel(const CodeRec *r, int64_t n, int64_t *flag
 
 __global__ void assign_kernel(const CodeRec *r, int64_t n, const int64_t *slots, const int64_t *flag,
                               const int64_t *ids, int32_t *qp_pattern, unsigned long long *pat_lab,
-                              uint32_t *pat_adj) {
+                              uint64_t *pat_adj) {
     for (int64_t t = gtid(); t < n; t += gstride()) {
         const int64_t pid = ids[t] + flag[t] - 1;
         qp_pattern[slots[r[t].idx]] = (int32_t)pid;
@@ -408,27 +408,15 @@ __global__ void assign_kernel(const CodeRec *r, int64_t n, const int64_t *slots,
     }
 }
 
-__global__ void orbits_kernel(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+__global__ void orbits_kernel(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, int64_t np,
                               uint64_t *orbit, int32_t *min_orbit) {
     for (int64_t P = gtid(); P < np; P += gstride()) {
-        int lab[FSM_MAXK], perm[FSM_MAXK], seg[FSM_MAXK], rep[FSM_MAXK];
-        uint32_t adj[FSM_MAXK];
-        decode_code(K, pat_lab[P], pat_adj[P], lab, adj);
-        const uint32_t code = pat_adj[P];
-        for (int c = 0; c < K; ++c) {
-            perm[c] = c;
-            rep[c] = c;
-            seg[c] = (c > 0 && lab[c] == lab[c - 1]) ? seg[c - 1] : c;
-        }
-        // automorphisms are the label-preserving orders with the same adjacency sequence
-        do {
-            if (adj_code(K, adj, perm) == code)
-                for (int c = 0; c < K; ++c) if (perm[c] < rep[c]) rep[c] = perm[c];
-        } while (next_label_perm(K, seg, perm));
+        int rep[FSM_MAXK];
+        orbit_reps(K, pat_lab[P], pat_adj[P], rep);
         uint64_t o = 0;
         int mn = K;
         for (int c = 0; c < K; ++c) {
-            o |= (uint64_t)rep[c] << (8 * c);
+            o |= nib_put(c, rep[c]);
             if (rep[c] == c) {
                 int sz = 0;
                 for (int x = 0; x < K; ++x) sz += rep[x] == c;
@@ -454,13 +442,10 @@ __global__ void domain_sizes_kernel(int K, const unsigned long long *pat_lab, co
     for (int64_t P = gtid(); P < np; P += gstride()) {
         const bool lv = (unsigned long long)min_orbit[P] * pat_count[P] >= (unsigned long long)t;
         live[P] = lv ? 1 : 0;
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < FSM_MAXK; ++c) {
             int64_t w = 0;
-            if (lv && c < K && (int)((orbit[P] >> (8 * c)) & 0xff) == c) {
-                const int lab = (int)(pat_lab[P] >> (8 * (7 - c))) & 0xff;
-                w = ((int64_t)cls_size[lab] + 31) / 32;
-            }
-            words[P * 8 + c] = w;
+            if (lv && c < K && nib_get(orbit[P], c) == c) w = ((int64_t)cls_size[clab_get(pat_lab[P], c)] + 31) / 32;
+            words[P * FSM_MAXK + c] = w;
         }
     }
 }
@@ -474,11 +459,11 @@ __global__ void support_kernel(int K, const uint64_t *orbit, const uint8_t *live
                                const int64_t *words, const uint32_t *dom, int64_t np,
                                unsigned long long *sigma) {
     const int lane = threadIdx.x & 31;
-    const int64_t nw = np * 8;
+    const int64_t nw = np * FSM_MAXK;
     for (int64_t w = gtid() >> 5; w < nw; w += gstride() >> 5) {
-        const int64_t P = w >> 3;
-        const int c = (int)(w & 7);
-        if (!live[P] || c >= K || (int)((orbit[P] >> (8 * c)) & 0xff) != c) continue;
+        const int64_t P = w / FSM_MAXK;
+        const int c = (int)(w % FSM_MAXK);
+        if (!live[P] || c >= K || nib_get(orbit[P], c) != c) continue;
         const uint32_t *b = dom + dom_off[w];
         const int64_t n = words[w];
         unsigned long long s = 0;
@@ -499,9 +484,9 @@ __global__ void new_ids_kernel(const int64_t *flag, const int64_t *scanned, int6
 }
 
 __global__ void gather_frequent_kernel(int K, const int32_t *newid, int64_t np, const unsigned long long *pat_lab,
-                                       const uint32_t *pat_adj, const unsigned long long *sigma,
+                                       const uint64_t *pat_adj, const unsigned long long *sigma,
                                        const unsigned long long *pat_count, unsigned long long *o_lab,
-                                       uint32_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
+                                       uint64_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
                                        uint64_t *o_lab8, uint64_t *o_adj8) {
     for (int64_t P = gtid(); P < np; P += gstride()) {
         const int32_t id = newid[P];
@@ -510,7 +495,7 @@ __global__ void gather_frequent_kernel(int K, const int32_t *newid, int64_t np, 
         o_adj[id] = pat_adj[P];
         o_sigma[id] = sigma[P];
         o_count[id] = pat_count[P];
-        if (o_lab8) {
+        if (o_lab8 && K <= 8) {
             int lab[FSM_MAXK];
             uint32_t adj[FSM_MAXK];
             decode_code(K, pat_lab[P], pat_adj[P], lab, adj);
@@ -539,7 +524,7 @@ __global__ void sum_frequent_kernel(const int32_t *newid, const unsigned long lo
 
 cudaError_t launch_qp_canon(int L, int V, const unsigned long long *keys, const int64_t *slots, int64_t nq,
                             const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
-                            uint32_t *perm, cudaStream_t st) {
+                            uint64_t *perm, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     LAUNCHED(1);
     qp_canon_kernel<<<blocks_for(nq, 128), 128, 0, st>>>(L, V, keys, slots, nq, pat_lab8, pat_adj8, recs, perm);
@@ -562,7 +547,7 @@ cudaError_t launch_sort_codes(CodeRec *recs, int64_t n, cudaStream_t st) {
 
 cudaError_t launch_assign_patterns(const CodeRec *recs, int64_t n, const int64_t *slots, int64_t *flag,
                                    int64_t *ids, void *scan_tmp, int32_t *qp_pattern,
-                                   unsigned long long *pat_lab, uint32_t *pat_adj, cudaStream_t st) {
+                                   unsigned long long *pat_lab, uint64_t *pat_adj, cudaStream_t st) {
     if (n <= 0) return cudaMemsetAsync(ids, 0, sizeof(int64_t), st);
     LAUNCHED(1);
     boundary_flags_kernel<<<blocks_for(n), kThreads, 0, st>>>(recs, n, flag);
@@ -573,7 +558,7 @@ cudaError_t launch_assign_patterns(const CodeRec *recs, int64_t n, const int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_orbits(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+cudaError_t launch_orbits(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, int64_t np,
                           uint64_t *orbit, int32_t *min_orbit, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     LAUNCHED(1);
@@ -614,7 +599,7 @@ cudaError_t launch_support(int K, const uint64_t *orbit, const uint8_t *live, co
                            unsigned long long *sigma, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     LAUNCHED(1);
-    support_kernel<<<blocks_for(np * 8 * 32), kThreads, 0, st>>>(K, orbit, live, dom_off, words, dom, np, sigma);
+    support_kernel<<<blocks_for(np * FSM_MAXK * 32), kThreads, 0, st>>>(K, orbit, live, dom_off, words, dom, np, sigma);
     return cudaGetLastError();
 }
 
@@ -635,9 +620,9 @@ cudaError_t launch_new_ids(const int64_t *flag, const int64_t *scanned, int64_t 
 }
 
 cudaError_t launch_gather_frequent(int K, const int32_t *newid, int64_t np, const unsigned long long *pat_lab,
-                                   const uint32_t *pat_adj, const unsigned long long *sigma,
+                                   const uint64_t *pat_adj, const unsigned long long *sigma,
                                    const unsigned long long *pat_count, unsigned long long *o_lab,
-                                   uint32_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
+                                   uint64_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
                                    uint64_t *o_lab8, uint64_t *o_adj8, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     LAUNCHED(1);
@@ -780,9 +765,9 @@ __global__ void level2_write_kernel(const DevGraph g, int32_t NL, const int32_t 
     }
 }
 
-__global__ void piece_table_kernel(const unsigned long long *lab, const uint32_t *adj, int64_t n, uint8_t *pf) {
+__global__ void piece_table_kernel(const unsigned long long *lab, const uint64_t *adj, int64_t n, uint8_t *pf) {
     for (int64_t P = gtid(); P < n; P += gstride()) {
-        const int l0 = (int)(lab[P] >> 56) & 0xff, l1 = (int)(lab[P] >> 48) & 0xff, l2 = (int)(lab[P] >> 40) & 0xff;
+        const int l0 = clab_get(lab[P], 0), l1 = clab_get(lab[P], 1), l2 = clab_get(lab[P], 2);
         const uint32_t a01 = (adj[P] >> 2) & 1u, a02 = (adj[P] >> 1) & 1u, a12 = adj[P] & 1u;
         uint32_t idx;
         if (a01 && a02 && a12) idx = tri_index(l0, l1, l2);
@@ -842,7 +827,7 @@ cudaError_t launch_level2_frontier(const DevGraph &g, int32_t NL, const int32_t 
 
 namespace {
 __global__ void level1_tables_kernel(int32_t NL, const int32_t *cls_size, int64_t t, int32_t *label_newid,
-                                     uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                     uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint64_t *cadj,
                                      unsigned long long *sigma, unsigned long long *count,
                                      unsigned long long *n_freq) {
     if (gtid() != 0) return;
@@ -854,7 +839,7 @@ __global__ void level1_tables_kernel(int32_t NL, const int32_t *cls_size, int64_
             label_newid[l] = id;
             lab8[id] = (uint64_t)l;
             adj8[id] = 0;
-            clab[id] = (unsigned long long)l << 56;
+            clab[id] = clab_put(0, l);
             cadj[id] = 0;
             sigma[id] = (unsigned long long)s;
             count[id] = (unsigned long long)s;
@@ -868,7 +853,7 @@ __global__ void level1_tables_kernel(int32_t NL, const int32_t *cls_size, int64_
 
 __global__ void level2_tables_kernel(int32_t NL, const unsigned long long *pair_sigma,
                                      const unsigned long long *pair_count, int64_t t, int32_t *pair_newid,
-                                     uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                     uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint64_t *cadj,
                                      unsigned long long *sigma, unsigned long long *count,
                                      unsigned long long *n_freq) {
     if (gtid() != 0) return;
@@ -880,8 +865,8 @@ __global__ void level2_tables_kernel(int32_t NL, const unsigned long long *pair_
                 pair_newid[x] = id;
                 lab8[id] = (uint64_t)lo | ((uint64_t)hi << 8);
                 adj8[id] = 0x0102ull;                  // row 0 = {1}, row 1 = {0}
-                clab[id] = ((unsigned long long)lo << 56) | ((unsigned long long)hi << 48);
-                cadj[id] = 1u;
+                clab[id] = clab_put(0, lo) | clab_put(1, hi);
+                cadj[id] = 1ull;
                 sigma[id] = pair_sigma[x];
                 count[id] = pair_count[x];
                 ++id;
@@ -894,7 +879,7 @@ __global__ void level2_tables_kernel(int32_t NL, const unsigned long long *pair_
 } // namespace
 
 cudaError_t launch_level1_tables(int32_t NL, const int32_t *cls_size, int64_t t, int32_t *label_newid,
-                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint64_t *cadj,
                                  unsigned long long *sigma, unsigned long long *count,
                                  unsigned long long *n_freq, cudaStream_t st) {
     LAUNCHED(1);
@@ -904,7 +889,7 @@ cudaError_t launch_level1_tables(int32_t NL, const int32_t *cls_size, int64_t t,
 
 cudaError_t launch_level2_tables(int32_t NL, const unsigned long long *pair_sigma,
                                  const unsigned long long *pair_count, int64_t t, int32_t *pair_newid,
-                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint64_t *cadj,
                                  unsigned long long *sigma, unsigned long long *count,
                                  unsigned long long *n_freq, cudaStream_t st) {
     LAUNCHED(1);
@@ -936,6 +921,7 @@ __global__ void features_pos_kernel(int K, const unsigned long long *pat_lab, co
                                     const int32_t *row_ptr, int32_t n, int64_t np, unsigned long long *pop,
                                     float *feat) {
     const int lane = threadIdx.x & 31;
+    // sampled levels have K <= 8: eight feature slots per block
     const int64_t nw = np * 8;
     for (int64_t w = gtid() >> 5; w < nw; w += gstride() >> 5) {
         const int64_t P = w >> 3;
@@ -945,9 +931,9 @@ __global__ void features_pos_kernel(int K, const unsigned long long *pat_lab, co
             if (lane == 0) { f[8 + c] = 0.f; f[16 + c] = 0.f; pop[w] = 0; }
             continue;
         }
-        const int o = (int)((orbit[P] >> (8 * c)) & 0xff);
-        const int lab = (int)(pat_lab[P] >> (8 * (7 - c))) & 0xff;
-        const int64_t off = dom_off[P * 8 + o], nwd = words[P * 8 + o];
+        const int o = nib_get(orbit[P], c);
+        const int lab = clab_get(pat_lab[P], c);
+        const int64_t off = dom_off[P * FSM_MAXK + o], nwd = words[P * FSM_MAXK + o];
         float sdeg = 0.f;
         unsigned long long cnt = 0;
         for (int64_t x = lane; x < nwd; x += 32) {
@@ -974,7 +960,7 @@ __global__ void features_pos_kernel(int K, const unsigned long long *pat_lab, co
 
 // Features, per pattern: the orbits' popcounts ascending (from pop[] at each orbit's
 // representative) and the pattern-level entries.
-__global__ void features_pat_kernel(int K, const uint32_t *pat_adj, const uint64_t *orbit,
+__global__ void features_pat_kernel(int K, const uint64_t *pat_adj, const uint64_t *orbit,
                                     const unsigned long long *pat_count, int32_t n, float logp, float p, int64_t t,
                                     int64_t np, const int64_t *aut, const unsigned long long *pop, float *feat) {
     for (int64_t P = gtid(); P < np; P += gstride()) {
@@ -983,7 +969,7 @@ __global__ void features_pat_kernel(int K, const uint32_t *pat_adj, const uint64
         int m = 0;
         unsigned long long mn = ~0ull;
         for (int c = 0; c < K; ++c) {
-            if ((int)((orbit[P] >> (8 * c)) & 0xff) != c) continue;
+            if (nib_get(orbit[P], c) != c) continue;
             const unsigned long long q = pop[P * 8 + c];
             if (q < mn) mn = q;
             pc[m++] = log1pf((float)q);
@@ -992,7 +978,7 @@ __global__ void features_pat_kernel(int K, const uint32_t *pat_adj, const uint64
             for (int b = a; b > 0 && pc[b - 1] > pc[b]; --b) { float tt = pc[b]; pc[b] = pc[b - 1]; pc[b - 1] = tt; }
         for (int a = 0; a < 8; ++a) f[a] = a < m ? pc[a] : 0.f;
         f[24] = (float)K;
-        f[25] = (float)__popc(pat_adj[P]);
+        f[25] = (float)__popcll(pat_adj[P]);
         f[26] = logp;
         f[27] = log1pf((float)pat_count[P]);
         f[28] = logf((float)t / (float)n);
@@ -1002,7 +988,7 @@ __global__ void features_pat_kernel(int K, const uint32_t *pat_adj, const uint64
     }
 }
 
-__global__ void aut_size_kernel(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+__global__ void aut_size_kernel(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, int64_t np,
                                 int64_t *aut) {
     for (int64_t P = gtid(); P < np; P += gstride()) {
         int lab[FSM_MAXK], perm[FSM_MAXK], seg[FSM_MAXK];
@@ -1076,7 +1062,7 @@ cudaError_t launch_by_rank(const DevGraph &g, int32_t NL, const int32_t *cls_siz
     return cudaGetLastError();
 }
 
-cudaError_t launch_aut_size(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+cudaError_t launch_aut_size(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, int64_t np,
                             int64_t *aut, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     LAUNCHED(1);
@@ -1084,7 +1070,7 @@ cudaError_t launch_aut_size(int K, const unsigned long long *pat_lab, const uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_features(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, const uint64_t *orbit,
+cudaError_t launch_features(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, const uint64_t *orbit,
                             const int64_t *dom_off, const int64_t *words, const uint32_t *dom,
                             const unsigned long long *pat_count, const int32_t *cls_size, const int64_t *cls_off,
                             const int32_t *by_rank, const int32_t *row_ptr, int32_t n, double p, int64_t t,
@@ -1107,8 +1093,8 @@ namespace {
 
 __device__ bool mask_conn(uint32_t m, const uint32_t *adj, int K) { return mask_connected(m, adj, K); }
 
-__global__ void needed_parts_kernel(int K, const unsigned long long *lab, const uint32_t *adj, const uint8_t *uncertain,
-                                    int64_t np, const unsigned long long *s_lab, const uint32_t *s_adj, int64_t s_np,
+__global__ void needed_parts_kernel(int K, const unsigned long long *lab, const uint64_t *adj, const uint8_t *uncertain,
+                                    int64_t np, const unsigned long long *s_lab, const uint64_t *s_adj, int64_t s_np,
                                     uint8_t *need_s, uint8_t *need_piece) {
     for (int64_t P = gtid(); P < np; P += gstride()) {
         if (!uncertain[P]) continue;
@@ -1146,7 +1132,7 @@ __global__ void needed_parts_kernel(int K, const unsigned long long *lab, const 
                         if ((r >> h2 & 1u) && (ad[h] >> h2 & 1u)) sa[map[h]] |= 1u << map[h2];
                 }
                 unsigned long long cl;
-                uint32_t ca, inv;
+                uint64_t ca, inv;
                 canonicalise(m, sl, sa, cl, ca, inv);
                 int64_t lo = 0, hi = s_np;
                 while (lo < hi) {
@@ -1179,8 +1165,8 @@ __global__ void and_u8_kernel(uint8_t *a, const uint8_t *b, int64_t n) {
 
 } // namespace
 
-cudaError_t launch_needed_parts(int K, const unsigned long long *lab, const uint32_t *adj, const uint8_t *uncertain,
-                                int64_t np, const unsigned long long *s_lab, const uint32_t *s_adj, int64_t s_np,
+cudaError_t launch_needed_parts(int K, const unsigned long long *lab, const uint64_t *adj, const uint8_t *uncertain,
+                                int64_t np, const unsigned long long *s_lab, const uint64_t *s_adj, int64_t s_np,
                                 uint8_t *need_s, uint8_t *need_piece, cudaStream_t st) {
     if (np <= 0) return cudaSuccess;
     LAUNCHED(1);
@@ -1248,7 +1234,7 @@ namespace {
 // MNI support of each pattern from the one-pass last level's orbit bitmaps: the pattern's entry
 // in the code table gives its bitmap block; orbit representatives (ascending canonical
 // position) hold ceil(|V_label| / 32) words each, in that order.  One warp per pattern.
-__global__ void fused_support_kernel(int K, const unsigned long long *plab, const uint32_t *padj, const uint64_t *orbit,
+__global__ void fused_support_kernel(int K, const unsigned long long *plab, const uint64_t *padj, const uint64_t *orbit,
                                      int64_t np, const unsigned long long *ckeys, const unsigned long long *coff,
                                      uint64_t cmask, const int32_t *cls_size, const uint32_t *pool,
                                      unsigned long long *sigma) {
@@ -1271,9 +1257,8 @@ __global__ void fused_support_kernel(int K, const unsigned long long *plab, cons
         uint64_t pre = 0;
         unsigned long long mn = ~0ull;
         for (int c = 0; c < K; ++c) {
-            if ((int)((orbit[P] >> (8 * c)) & 0xff) != c) continue;
-            const int lab = (int)((plab[P] >> (8 * (7 - c))) & 0xff);
-            const uint64_t nw = ((uint64_t)cls_size[lab] + 31) / 32;
+            if (nib_get(orbit[P], c) != c) continue;
+            const uint64_t nw = ((uint64_t)cls_size[clab_get(plab[P], c)] + 31) / 32;
             unsigned long long cnt = 0;
             for (uint64_t x = lane; x < nw; x += 32) cnt += __popc(pool[off + pre + x]);
 #pragma unroll
@@ -1287,7 +1272,7 @@ __global__ void fused_support_kernel(int K, const unsigned long long *plab, cons
 
 } // namespace
 
-cudaError_t launch_fused_support(int K, const unsigned long long *plab, const uint32_t *padj, const uint64_t *orbit,
+cudaError_t launch_fused_support(int K, const unsigned long long *plab, const uint64_t *padj, const uint64_t *orbit,
                                  int64_t np, const unsigned long long *ckeys, const unsigned long long *coff,
                                  uint64_t cmask, const int32_t *cls_size, const uint32_t *pool, unsigned long long *sigma,
                                  cudaStream_t st) {
@@ -1300,26 +1285,22 @@ cudaError_t launch_fused_support(int K, const unsigned long long *plab, const ui
 
 namespace {
 __global__ void slot_bases_kernel(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
-                                  const uint32_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
+                                  const uint64_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
                                   const int64_t *dom_off, int64_t *slot_base) {
     for (int64_t q = gtid(); q < nq; q += gstride()) {
         const int64_t slot = slots[q];
         const int32_t P = qp_pattern[slot];
-        for (int h = 0; h < 8; ++h) {
+        for (int h = 0; h < FSM_MAXK; ++h) {
             int64_t b = -1;
-            if (h < K && live[P]) {
-                const int c = (int)((qp_perm[slot] >> (3 * h)) & 7u);
-                const int o = (int)((orbit[P] >> (8 * c)) & 0xff);
-                b = dom_off[(int64_t)P * 8 + o];
-            }
-            slot_base[slot * 8 + h] = b;
+            if (h < K && live[P]) b = dom_off[(int64_t)P * FSM_MAXK + nib_get(orbit[P], nib_get(qp_perm[slot], h))];
+            slot_base[slot * FSM_MAXK + h] = b;
         }
     }
 }
 } // namespace
 
 cudaError_t launch_slot_bases(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
-                              const uint32_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
+                              const uint64_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
                               const int64_t *dom_off, int64_t *slot_base, cudaStream_t st) {
     if (nq <= 0) return cudaSuccess;
     LAUNCHED(1);
@@ -1328,7 +1309,7 @@ cudaError_t launch_slot_bases(int K, const int64_t *slots, int64_t nq, const int
     return cudaGetLastError();
 }
 
-cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
+cudaError_t launch_piece_table(const unsigned long long *lab, const uint64_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     LAUNCHED(1);

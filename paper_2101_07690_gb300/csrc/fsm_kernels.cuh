@@ -6,13 +6,12 @@
 
 namespace fsm {
 
-// One pattern's canonical code: labels in canonical order packed big-endian (byte 7 = first
-// position) and the adjacency sequence A(0,1), A(0,2), ..., A(k-2,k-1) with A(0,1) as the most
-// significant of the k(k-1)/2 used bits.  Integer order on (lab, adj) is the lexicographic
-// order of the code.  idx carries a payload through sorting.
+// One pattern's canonical code: the label word and the adjacency word of fsm_device.cuh
+// (integer order on (lab, adj) is the lexicographic order of the code).  idx carries a payload
+// through sorting.
 struct CodeRec {
     unsigned long long lab;
-    uint32_t adj;
+    uint64_t adj;
     uint32_t idx;
 };
 
@@ -61,16 +60,16 @@ cudaError_t launch_qp_compact(const unsigned long long *keys, int64_t cap, int64
 // canonical code of each distinct key; writes recs[q] (idx = q) and perm[slot]
 cudaError_t launch_qp_canon(int L, int V, const unsigned long long *keys, const int64_t *slots, int64_t nq,
                             const uint64_t *pat_lab8, const uint64_t *pat_adj8, CodeRec *recs,
-                            uint32_t *perm, cudaStream_t st);
+                            uint64_t *perm, cudaStream_t st);
 // sort recs[0..n) ascending by (lab, adj, idx); recs must have room for next_pow2(n) entries
 cudaError_t launch_sort_codes(CodeRec *recs, int64_t n, cudaStream_t st);
 // after sorting: pattern ids.  flags/ids scratch of n+1 entries.  Writes qp_pattern[slot],
 // pattern codes pat_lab/pat_adj, and *n_pat.
 cudaError_t launch_assign_patterns(const CodeRec *recs, int64_t n, const int64_t *slots, int64_t *flag,
                                    int64_t *ids, void *scan_tmp, int32_t *qp_pattern,
-                                   unsigned long long *pat_lab, uint32_t *pat_adj, cudaStream_t st);
-// per pattern: orbit representatives (8 bytes), smallest orbit size
-cudaError_t launch_orbits(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+                                   unsigned long long *pat_lab, uint64_t *pat_adj, cudaStream_t st);
+// per pattern: orbit word (representative per canonical position), smallest orbit size
+cudaError_t launch_orbits(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, int64_t np,
                           uint64_t *orbit, int32_t *min_orbit, cudaStream_t st);
 // pattern embedding counts: pat_count[pattern[slot]] += count[slot]
 cudaError_t launch_pattern_counts(const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
@@ -95,9 +94,9 @@ cudaError_t launch_new_ids(const int64_t *flag, const int64_t *scanned, int64_t 
                            cudaStream_t st);
 // gather frequent patterns: codes, sigma, counts -> compact arrays; also level tables (lab8/adj8)
 cudaError_t launch_gather_frequent(int K, const int32_t *newid, int64_t np, const unsigned long long *pat_lab,
-                                   const uint32_t *pat_adj, const unsigned long long *sigma,
+                                   const uint64_t *pat_adj, const unsigned long long *sigma,
                                    const unsigned long long *pat_count, unsigned long long *o_lab,
-                                   uint32_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
+                                   uint64_t *o_adj, unsigned long long *o_sigma, unsigned long long *o_count,
                                    uint64_t *o_lab8, uint64_t *o_adj8, cudaStream_t st);
 // sum of counts of frequent patterns (the next frontier's size)
 cudaError_t launch_sum_frequent(const int32_t *newid, const unsigned long long *pat_count, int64_t np,
@@ -124,12 +123,12 @@ cudaError_t launch_level2_frontier(const DevGraph &g, int32_t NL, const int32_t 
 // size-1 and size-2 pattern tables (single-block kernels over the <= 64 labels / label pairs):
 // frequent ids in code order, level tables, codes, supports, counts; *n_freq = frequent count
 cudaError_t launch_level1_tables(int32_t NL, const int32_t *cls_size, int64_t t, int32_t *label_newid,
-                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint64_t *cadj,
                                  unsigned long long *sigma, unsigned long long *count,
                                  unsigned long long *n_freq, cudaStream_t st);
 cudaError_t launch_level2_tables(int32_t NL, const unsigned long long *pair_sigma,
                                  const unsigned long long *pair_count, int64_t t, int32_t *pair_newid,
-                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint32_t *cadj,
+                                 uint64_t *lab8, uint64_t *adj8, unsigned long long *clab, uint64_t *cadj,
                                  unsigned long long *sigma, unsigned long long *count,
                                  unsigned long long *n_freq, cudaStream_t st);
 
@@ -153,21 +152,21 @@ cudaError_t launch_by_rank(const DevGraph &g, int32_t NL, const int32_t *cls_siz
 //   [16..24) mean log1p(degree) over the sampled domain of each canonical position's orbit
 //   [24..32) k, edges, log p, log1p(sampled embeddings), log(t / n), log |Aut|,
 //            log((smallest popcount + 1) / p), log n
-cudaError_t launch_features(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, const uint64_t *orbit,
+cudaError_t launch_features(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, const uint64_t *orbit,
                             const int64_t *dom_off, const int64_t *words, const uint32_t *dom,
                             const unsigned long long *pat_count, const int32_t *cls_size, const int64_t *cls_off,
                             const int32_t *by_rank, const int32_t *row_ptr, int32_t n, double p, int64_t t,
                             int64_t np, const int64_t *aut, float *feat, cudaStream_t st);
 // Automorphism group size of each pattern (the orbits kernel enumerates the same orders)
-cudaError_t launch_aut_size(int K, const unsigned long long *pat_lab, const uint32_t *pat_adj, int64_t np,
+cudaError_t launch_aut_size(int K, const unsigned long long *pat_lab, const uint64_t *pat_adj, int64_t np,
                             int64_t *aut, cudaStream_t st);
 
 // Exact recount of sampled mining: for every pattern with uncertain[P], every dissection of
 // its canonical graph into a connected 3-vertex part and a connected (K-2)-vertex part sharing
 // one vertex: mark the part's size-(K-2) pattern (its id found by binary search among the
 // sorted codes s_lab/s_adj of the stored level) in need_s and the piece in need_piece.
-cudaError_t launch_needed_parts(int K, const unsigned long long *lab, const uint32_t *adj, const uint8_t *uncertain,
-                                int64_t np, const unsigned long long *s_lab, const uint32_t *s_adj, int64_t s_np,
+cudaError_t launch_needed_parts(int K, const unsigned long long *lab, const uint64_t *adj, const uint8_t *uncertain,
+                                int64_t np, const unsigned long long *s_lab, const uint64_t *s_adj, int64_t s_np,
                                 uint8_t *need_s, uint8_t *need_piece, cudaStream_t st);
 // keep the stored embeddings whose pattern is flagged: out has room for N rows
 cudaError_t launch_compact_frontier(const int32_t *fv, const int32_t *fpid, int64_t N, int L, const uint8_t *keep,
@@ -190,7 +189,7 @@ cudaError_t launch_stamp_time(unsigned long long *out, cudaStream_t st);
 
 // MNI supports from the one-pass last level: sigma[P] = the smallest orbit popcount of pattern
 // P's bitmap block, found through its entry in the code table (ckeys / coff, cmask + 1 slots)
-cudaError_t launch_fused_support(int K, const unsigned long long *plab, const uint32_t *padj, const uint64_t *orbit,
+cudaError_t launch_fused_support(int K, const unsigned long long *plab, const uint64_t *padj, const uint64_t *orbit,
                                  int64_t np, const unsigned long long *ckeys, const unsigned long long *coff,
                                  uint64_t cmask, const int32_t *cls_size, const uint32_t *pool, unsigned long long *sigma,
                                  cudaStream_t st);
@@ -199,11 +198,11 @@ cudaError_t launch_fused_support(int K, const unsigned long long *plab, const ui
 // the bitmap its vertex goes to (the orbit of canonical position perm[h] of its pattern), or -1
 // when the pattern has no domains.
 cudaError_t launch_slot_bases(int K, const int64_t *slots, int64_t nq, const int32_t *qp_pattern,
-                              const uint32_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
+                              const uint64_t *qp_perm, const uint8_t *live, const uint64_t *orbit,
                               const int64_t *dom_off, int64_t *slot_base, cudaStream_t st);
 
 // ---- pieces: mark the frequent size-3 patterns by piece index
-cudaError_t launch_piece_table(const unsigned long long *lab, const uint32_t *adj, int64_t n,
+cudaError_t launch_piece_table(const unsigned long long *lab, const uint64_t *adj, int64_t n,
                                uint8_t *piece_freq, cudaStream_t st);
 
 } // namespace fsm

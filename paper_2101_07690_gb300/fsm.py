@@ -25,7 +25,7 @@ _NAMES = {FSM_EINVAL: "FSM_EINVAL", FSM_ENOMEM: "FSM_ENOMEM", FSM_ECUDA: "FSM_EC
 
 # every entry point that include/fsm.h declares
 EXPORTS = ["fsm_load_graph", "fsm_set_option", "fsm_mine", "fsm_result_count", "fsm_result_get",
-           "fsm_result_embeddings", "fsm_result_copy", "fsm_result_stat", "fsm_free_result",
+           "fsm_result_embeddings", "fsm_result_copy", "fsm_result_pairs", "fsm_result_stat", "fsm_free_result",
            "fsm_free_graph", "fsm_last_error", "fsm_debug_dissect", "fsm_edge_supports_noalloc",
            "fsm_result_exact", "fsm_result_features", "fsm_mlp_create", "fsm_mlp_set_params",
            "fsm_mlp_get_params", "fsm_mlp_set_norm", "fsm_mlp_fit_norm", "fsm_mlp_gradients", "fsm_mlp_train",
@@ -62,6 +62,7 @@ def load(path: str | None = None):
         "fsm_result_get": (ctypes.c_int, [vp, i64, P(i32), P(u64), P(i64)]),
         "fsm_result_embeddings": (ctypes.c_int, [vp, i64, P(i64)]),
         "fsm_result_copy": (ctypes.c_int, [vp, P(i32), P(u64), P(i64), P(i64)]),
+        "fsm_result_pairs": (ctypes.c_int, [vp, P(u64)]),
         "fsm_result_stat": (ctypes.c_int, [vp, ctypes.c_char_p, P(i64)]),
         "fsm_free_result": (None, [vp]),
         "fsm_free_graph": (None, [vp]),
@@ -158,12 +159,32 @@ def fsm_result_embeddings(r: int, i: int) -> int:
     return int(c.value)
 
 
+def fsm_result_pairs(r: int) -> np.ndarray:
+    """Pair bits of every pattern: bit q set when pair q of (0,1), (0,2), ... is an edge."""
+    out = np.zeros(fsm_result_count(r), np.uint64)
+    _check(load().fsm_result_pairs(r, _ptr(out, ctypes.c_uint64)))
+    return out
+
+
+def adj_from_pairs(pairs, k: int) -> np.ndarray:
+    """Bit (i*k + j) words from pair bits: uint64 for k <= 8, Python ints (object array) for
+    k = 9, whose bits run past 64."""
+    pos = [i * k + j for i in range(k) for j in range(i + 1, k)]
+    out = [sum(1 << pos[q] for q in range(len(pos)) if (int(w) >> q) & 1) for w in pairs]
+    return np.array(out, dtype=np.uint64 if k <= 8 else object)
+
+
 def fsm_result_copy(r: int, k: int) -> dict:
+    """labels (n, k), adj (bit i*k + j; Python ints for k = 9), support, count."""
     n = fsm_result_count(r)
     out = {"labels": np.zeros((n, k), np.int32), "adj": np.zeros(n, np.uint64),
            "support": np.zeros(n, np.int64), "count": np.zeros(n, np.int64)}
-    _check(load().fsm_result_copy(r, _ptr(out["labels"], ctypes.c_int32), _ptr(out["adj"], ctypes.c_uint64),
+    wide = k > 8
+    _check(load().fsm_result_copy(r, _ptr(out["labels"], ctypes.c_int32),
+                                  None if wide else _ptr(out["adj"], ctypes.c_uint64),
                                   _ptr(out["support"], ctypes.c_int64), _ptr(out["count"], ctypes.c_int64)))
+    if wide:
+        out["adj"] = adj_from_pairs(fsm_result_pairs(r), k)
     return out
 
 

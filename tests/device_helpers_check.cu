@@ -1,15 +1,155 @@
 // Host checks of the index and key helpers the extension kernel shares with the host
 // (fsm_device.cuh), against brute force: count_below, centre_pairs (the four-vertex cut of the
-// centre pairs), quick-pattern key packing, join-graph symmetry, size-3 pattern indices.  It
-// also prints the sampling hash of a grid of (seed, x, y) for tests/test_device_helpers.py to
-// compare with splitmix64 written from its published definition.  Host code only.
-#include "fsm_device.cuh"
+// centre pairs), quick-pattern key packing, join-graph symmetry, size-3 pattern indices; and of
+// the canonicaliser (fsm_canon.cuh: label-order enumeration and the cell search) and its orbit
+// representatives, against the minimum over all K! vertex orders and the automorphisms found
+// among them, for K up to 9.  It also prints the sampling hash of a grid of (seed, x, y) for
+// tests/test_device_helpers.py to compare with splitmix64 written from its published
+// definition.  Host code only.
+#include "fsm_canon.cuh"
 #include <cstdio>
 #include <cstdlib>
 using namespace fsm;
 
 static int fails = 0;
 #define CHECK(c) do { if (!(c)) { ++fails; printf("FAIL %s:%d %s\n", __FILE__, __LINE__, #c); } } while (0)
+
+// ---- canonicaliser against brute force over all K! orders
+static uint32_t rng_state = 2463534242u;
+static uint32_t xrand() {
+    rng_state ^= rng_state << 13; rng_state ^= rng_state >> 17; rng_state ^= rng_state << 5;
+    return rng_state;
+}
+
+// (label sequence, adjacency sequence) of one order, compared lexicographically
+static bool order_less(int K, const int *lab, const uint32_t *adj, const int *pa, const int *pb, int &cmp) {
+    for (int c = 0; c < K; ++c)
+        if (lab[pa[c]] != lab[pb[c]]) { cmp = lab[pa[c]] < lab[pb[c]] ? -1 : 1; return cmp < 0; }
+    const uint64_t a = adj_code(K, adj, pa), b = adj_code(K, adj, pb);
+    cmp = a < b ? -1 : (a > b ? 1 : 0);
+    return cmp < 0;
+}
+
+static void check_canon() {
+    int graphs = 0;
+    for (int K = 1; K <= FSM_MAXK; ++K) {
+        const int reps = K <= 6 ? 400 : (K == 7 ? 200 : (K == 8 ? 60 : 25));
+        for (int r = 0; r < reps; ++r) {
+            // labels from 1-3 values, a random spanning tree plus random extra edges; some
+            // graphs are highly symmetric (all labels equal, complete or empty beyond the tree)
+            const int nl = 1 + (int)(xrand() % 3);
+            int lab[FSM_MAXK];
+            uint32_t adj[FSM_MAXK] = {0};
+            for (int h = 0; h < K; ++h) lab[h] = (r % 4 == 0) ? 0 : (int)(xrand() % nl) * 7;
+            for (int h = 1; h < K; ++h) {
+                const int u = (int)(xrand() % h);
+                adj[h] |= 1u << u; adj[u] |= 1u << h;
+            }
+            const int dens = (int)(xrand() % 5);   // 0: tree; 4: complete
+            for (int a = 0; a < K; ++a)
+                for (int b = a + 1; b < K; ++b)
+                    if ((int)(xrand() % 4) < dens) { adj[a] |= 1u << b; adj[b] |= 1u << a; }
+            // brute force: the smallest order over all K! of them, and the automorphisms
+            int p[FSM_MAXK], bp[FSM_MAXK];
+            for (int h = 0; h < K; ++h) p[h] = bp[h] = h;
+            int cmp;
+            do {
+                if (order_less(K, lab, adj, p, bp, cmp))
+                    for (int h = 0; h < K; ++h) bp[h] = p[h];
+            } while (next_perm(p, K));
+            const uint64_t want = adj_code(K, adj, bp);
+            unsigned long long wl = 0;
+            for (int c = 0; c < K; ++c) wl |= clab_put(c, lab[bp[c]]);
+            // both ways, through canonicalise and the cell search directly
+            unsigned long long cl;
+            uint64_t ca, inv;
+            canonicalise(K, lab, adj, cl, ca, inv);
+            CHECK(ca == want && cl == wl);
+            int ord[FSM_MAXK], best[FSM_MAXK];
+            CHECK(canon_search(K, lab, adj, -1, best) == want);
+            for (int c = 0; c < K; ++c) ord[c] = best[c];
+            CHECK(adj_code(K, adj, ord) == want);
+            for (int c = 0; c < K; ++c) CHECK(lab[best[c]] == clab_get(wl, c));
+            // inv maps every vertex to its position in an optimal order
+            uint32_t used = 0;
+            for (int h = 0; h < K; ++h) {
+                const int c = nib_get(inv, h);
+                CHECK(c < K && !((used >> c) & 1u));
+                used |= 1u << c;
+                ord[c] = h;
+            }
+            CHECK(adj_code(K, adj, ord) == want);
+            // an isomorphic copy (vertices renamed) has the same code
+            int q[FSM_MAXK], lab2[FSM_MAXK];
+            uint32_t adj2[FSM_MAXK] = {0};
+            for (int h = 0; h < K; ++h) q[h] = h;
+            for (int h = K - 1; h > 0; --h) { const int j = (int)(xrand() % (h + 1)); const int t = q[h]; q[h] = q[j]; q[j] = t; }
+            for (int h = 0; h < K; ++h) {
+                lab2[q[h]] = lab[h];
+                for (int w = 0; w < K; ++w) if ((adj[h] >> w) & 1u) adj2[q[h]] |= 1u << q[w];
+            }
+            unsigned long long cl2;
+            uint64_t ca2, inv2;
+            canonicalise(K, lab2, adj2, cl2, ca2, inv2);
+            CHECK(ca2 == want && cl2 == wl);
+            // orbit representatives against the automorphisms of the canonical graph
+            int clb[FSM_MAXK], rep[FSM_MAXK], wrep[FSM_MAXK];
+            uint32_t cad[FSM_MAXK];
+            decode_code(K, cl, ca, clb, cad);
+            for (int c = 0; c < K; ++c) { p[c] = c; wrep[c] = c; }
+            do {
+                bool aut = true;
+                for (int c = 0; c < K && aut; ++c) aut = clb[p[c]] == clb[c];
+                if (aut && adj_code(K, cad, p) == ca)
+                    for (int c = 0; c < K; ++c) if (p[c] < wrep[c]) wrep[c] = p[c];
+            } while (next_perm(p, K));
+            orbit_reps(K, cl, ca, rep);
+            for (int c = 0; c < K; ++c) CHECK(rep[c] == wrep[c]);
+            ++graphs;
+        }
+    }
+    // the search and the marked orbits against label-order enumeration, on many more graphs
+    // with two or three labels (few enough label-preserving orders to enumerate)
+    for (int K = 4; K <= FSM_MAXK; ++K)
+        for (int r = 0; r < 3000; ++r) {
+            const int nl = 2 + (int)(xrand() % 2);
+            int lab[FSM_MAXK];
+            uint32_t adj[FSM_MAXK] = {0};
+            for (int h = 0; h < K; ++h) lab[h] = (int)(xrand() % nl);
+            for (int h = 1; h < K; ++h) {
+                const int u = (int)(xrand() % h);
+                adj[h] |= 1u << u; adj[u] |= 1u << h;
+            }
+            const int dens = (int)(xrand() % 5);
+            for (int a = 0; a < K; ++a)
+                for (int b = a + 1; b < K; ++b)
+                    if ((int)(xrand() % 4) < dens) { adj[a] |= 1u << b; adj[b] |= 1u << a; }
+            int perm[FSM_MAXK], seg[FSM_MAXK], best[FSM_MAXK];
+            label_sort(K, lab, perm, seg);
+            uint64_t bc = ~0ull;
+            do { const uint64_t x = adj_code(K, adj, perm); if (x < bc) bc = x; } while (next_label_perm(K, seg, perm));
+            CHECK(canon_search(K, lab, adj, -1, best) == bc);
+            // orbits of the canonical graph: enumeration and marking
+            unsigned long long cl;
+            uint64_t ca, inv;
+            canonicalise(K, lab, adj, cl, ca, inv);
+            int clb[FSM_MAXK], cseg[FSM_MAXK], p[FSM_MAXK], rep[FSM_MAXK], wrep[FSM_MAXK];
+            uint32_t cad[FSM_MAXK];
+            decode_code(K, cl, ca, clb, cad);
+            for (int c = 0; c < K; ++c) {
+                p[c] = c; wrep[c] = c;
+                cseg[c] = (c > 0 && clb[c] == clb[c - 1]) ? cseg[c - 1] : c;
+            }
+            do {
+                if (adj_code(K, cad, p) == ca)
+                    for (int c = 0; c < K; ++c) if (p[c] < wrep[c]) wrep[c] = p[c];
+            } while (next_label_perm(K, cseg, p));
+            orbit_reps_search(K, clb, cad, cseg, rep);
+            for (int c = 0; c < K; ++c) CHECK(rep[c] == wrep[c]);
+            ++graphs;
+        }
+    printf("canonical codes checked on %d graphs\n", graphs);
+}
 
 int main() {
     // count_below on sorted lists with gaps
@@ -36,7 +176,7 @@ int main() {
         s = s * 1103515245u + 12345u; const uint32_t pid = (s >> 4) & ((1u << 24) - 1);
         s = s * 1103515245u + 12345u; const uint32_t pidx = (s >> 3) & ((1u << 19) - 1);
         s = s * 1103515245u + 12345u; const int i = (int)((s >> 5) % 7), j = (int)((s >> 9) % 3);
-        s = s * 1103515245u + 12345u; const uint32_t cross = (s >> 7) & 1023u;
+        s = s * 1103515245u + 12345u; const uint32_t cross = (s >> 7) & 4095u;
         const uint64_t key = make_key(pid, pidx, i, j, cross);
         uint32_t p2, x2, c2; int i2, j2;
         split_key(key, p2, x2, i2, j2, c2);
@@ -45,7 +185,7 @@ int main() {
     }
     // join graphs are symmetric and loop-free for every level size, shape, join position,
     // key position and cross subset (s = a path over its l positions)
-    for (int L = 2; L <= 6; ++L)
+    for (int L = 2; L <= 7; ++L)
         for (int shape = 0; shape < 2; ++shape)
             for (int jpos = 0; jpos < 3; ++jpos)
                 for (int i = 0; i < L; ++i)
@@ -55,7 +195,7 @@ int main() {
                             srows |= (uint64_t)(1u << (h + 1)) << (8 * h);
                             srows |= (uint64_t)(1u << h) << (8 * (h + 1));
                         }
-                        uint32_t tj0, tj1, txx, adj[8];
+                        uint32_t tj0, tj1, txx, adj[FSM_MAXK];
                         piece_join_edges(shape, jpos, tj0, tj1, txx);
                         join_graph(L, srows, i, tj0, tj1, txx, sub, adj);
                         const int K = L + 2;
@@ -75,6 +215,16 @@ int main() {
                       t == tri_index(c, a, b) && t == tri_index(c, b, a));
                 CHECK(t != wedge_index(a, b, c));
             }
+    // pattern words round-trip
+    for (int c = 0; c < FSM_MAXK; ++c)
+        for (int l = 0; l < 64; ++l) {
+            CHECK(clab_get(clab_put(c, l), c) == l);
+            for (int c2 = 0; c2 < FSM_MAXK; ++c2)
+                if (c2 != c) CHECK(clab_get(clab_put(c, l), c2) == 0);
+        }
+    for (int h = 0; h < FSM_MAXK; ++h)
+        for (int v = 0; v < 16; ++v) CHECK(nib_get(nib_put(h, v) | nib_put((h + 1) % FSM_MAXK, 15 - v), h) == v);
+    check_canon();
     // sampling hash of a grid, for the splitmix64 comparison
     const uint64_t seeds[3] = {0ull, 1ull, 0x123456789abcdefull};
     const int32_t xs[4] = {0, 1, 77, 2147483647};

@@ -18,19 +18,6 @@ import oracle.brute as brute
 K = 9
 
 
-def tree_plus(n, extra, num_labels, seed):
-    """A random labeled tree on n vertices plus `extra` further edges (sparse, connected)."""
-    rng = np.random.default_rng(seed)
-    edges = set()
-    for v in range(1, n):
-        edges.add((int(rng.integers(v)), v))
-    while len(edges) < n - 1 + extra:
-        a, b = sorted(int(x) for x in rng.choice(n, 2, replace=False))
-        edges.add((a, b))
-    lab = rng.integers(num_labels, size=n).astype(np.int32)
-    return gg.from_edges(n, sorted(edges), lab, num_labels)
-
-
 def _edges_of(g):
     return [(v, int(w)) for v in range(g.n) for w in g.col[g.row_ptr[v]:g.row_ptr[v + 1]] if v < w]
 
@@ -96,7 +83,7 @@ def test_matcher_closed_forms():
 @pytest.mark.parametrize("mode", ["edge", "vertex"])
 @pytest.mark.parametrize("seed", [0, 1])
 def test_matcher_agrees_with_enumeration(mode, seed):
-    g = tree_plus(12, 3, 3, seed)
+    g = gg.tree_plus(12, 3, 3, seed)
     o = oracle.mine(g, K, 1, mode)
     assert len(o["support"]) > 5
     for lab, adj, s, c in zip(o["labels"], o["adj"], o["support"], o["count"]):
@@ -107,7 +94,7 @@ def test_matcher_agrees_with_enumeration(mode, seed):
 def test_embedding_totals_by_brute_force(seed):
     """Vertex-induced: one embedding per connected 9-vertex set; edge-induced: one per connected
     spanning edge subset of such a set."""
-    g = tree_plus(12, 3, 2, seed)
+    g = gg.tree_plus(12, 3, 2, seed)
     edges = _edges_of(g)
     n_sets = n_subsets = 0
     for vs in itertools.combinations(range(g.n), K):
@@ -124,7 +111,7 @@ def test_embedding_totals_by_brute_force(seed):
 
 
 def test_canonical_code_is_minimal():
-    g = tree_plus(11, 2, 2, 3)
+    g = gg.tree_plus(11, 2, 2, 3)
     o = oracle.mine(g, K, 1, "vertex")
     pairs = [(i, j) for i in range(K) for j in range(i + 1, K)]
     for q in (0, len(o["support"]) - 1):
@@ -141,7 +128,7 @@ def test_canonical_code_is_minimal():
 
 @pytest.mark.parametrize("mode", ["edge", "vertex"])
 def test_anti_monotone(mode):
-    g = tree_plus(12, 3, 2, 5)
+    g = gg.tree_plus(12, 3, 2, 5)
     big = oracle.mine(g, K, 1, mode)
     small = oracle.mine(g, K - 1, 1, mode)
     sup = {(tuple(int(x) for x in l), int(a)): int(s) for l, a, s in zip(small["labels"], small["adj"], small["support"])}
@@ -164,7 +151,7 @@ def test_anti_monotone(mode):
 
 @pytest.mark.parametrize("mode", ["edge", "vertex"])
 def test_quota_oracle_without_quotas_is_exact(mode):
-    g = tree_plus(13, 3, 2, 7)
+    g = gg.tree_plus(13, 3, 2, 7)
     for t in (1, 2):
         a = oracle.mine(g, K, t, mode)
         b = oracle.mine_quota(g, K, t, mode, seed=0, join_quota=0, match_quota=0)
