@@ -203,6 +203,15 @@ def read_peaks():
     return 6800.0, "fallback"
 
 
+def kernel_source_sha() -> str:
+    """sha256 prefix of the extension kernel's source: fsm_extend.cuh and the two headers it
+    compiles in (the canonicaliser and the device helpers)."""
+    h = hashlib.sha256()
+    for f in ("fsm_extend.cuh", "fsm_canon.cuh", "fsm_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2101_07690_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def traffic_for(kernel_pass: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
     source of the extension kernel (else None)."""
@@ -210,10 +219,8 @@ def traffic_for(kernel_pass: str):
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    src = os.path.join(ROOT, "paper_2101_07690_gb300", "csrc", "fsm_extend.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     ent = d.get(kernel_pass)
-    if not ent or d.get("source_sha") != h:
+    if not ent or d.get("source_sha") != kernel_source_sha():
         return None
     return ent.get("dram_bytes_per_full_launch")
 
@@ -228,8 +235,7 @@ def issue_roof(dom, ns: float, nl: int, pieces: int):
     if not os.path.exists(path) or nl == 0 or ns <= 0 or pieces <= 0:
         return None
     d = json.load(open(path))
-    src = os.path.join(ROOT, "paper_2101_07690_gb300", "csrc", "fsm_extend.cuh")
-    if d.get("source_sha") != hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]:
+    if d.get("source_sha") != kernel_source_sha():
         return None
     ent = d.get(f"{dom[0]}_l{dom[1]}")
     if not ent:

@@ -271,6 +271,9 @@ WORKLOADS = {
     # Chung-Lu 3.7M vertices, 16.5M edges, beta 2.3, 37 Zipf(1.0) labels.
     "cl3700k": dict(family="cl", n=3_700_000, m=16_500_000, beta=2.3, seed=2, num_labels=37,
                     label_law="zipf", zipf_s=1.0, cap=None),
+    # CiteSeer-shaped: Chung-Lu 3312 vertices, 4732 edges, beta 2.5, degree cap 99, 6 uniform
+    # labels (the shape of the citation graph the 9-vertex experiments of Section 6 use).
+    "ci3k": dict(family="cl", n=3312, m=4732, beta=2.5, seed=4, num_labels=6, label_law="uniform", cap=99),
     # Chung-Lu 1.1M vertices, 3M edges, beta 2.0, 16 uniform labels.
     "cl1100k": dict(family="cl", n=1_100_000, m=3_000_000, beta=2.0, seed=3, num_labels=16,
                     label_law="uniform", cap=None),

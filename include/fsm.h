@@ -227,7 +227,7 @@ int fsm_result_features(const fsm_result *r, float *features);
 /*
  * fsm_result_stat -- a run counter of the mining call that made r:
  *   "k", "levels", "pieces" (size-3 pieces enumerated by the count passes; "pieces_l<l>" per
- *   extended level size l = 1..6), "candidates" (joins
+ *   extended level size l = 1..7), "candidates" (joins
  *   tested), "embeddings" (accepted joins, all levels),
  *   "final_embeddings" (accepted joins of the last level), "qp_grows" (quick-pattern table
  *   overflows, each a grown table and a repeated pass), "fused_fallbacks" (one-pass last levels
@@ -242,7 +242,7 @@ int fsm_result_features(const fsm_result *r, float *features);
  *   per (embedding, key position) unit, 4 * (l + 1) per embedding read, for domain also
  *   4 * (l + 2) per accepted join of a pattern given a domain (one bitmap word per position),
  *   and for emit 4 * (l + 3) per embedding written), and the same per extended level size l as
- *   "P_ns_l<l>", "P_launches_l<l>", "P_bytes_l<l>" (l = 1..6); "chunk_l<l>" (autotuned chunk
+ *   "P_ns_l<l>", "P_launches_l<l>", "P_bytes_l<l>" (l = 1..7); "chunk_l<l>" (autotuned chunk
  *   size of level l, 0 if none).  In launch modes 1 and 2 a pass's time covers its CUDA graph
  *   (the prefix-sum kernels included).
  */

@@ -127,22 +127,26 @@ FSM_HD uint32_t tri_index(int x, int y, int z) {
 
 // ---------------------------------------------------------------------------- QP keys
 //
-// 64-bit key: pid_s (24 bits) | piece index (19) | i (3) | j (2) | cross bits (2*(l-1) <= 12).
-// Cross bit (p', q): s position p (p' = p minus one if p > i) adjacent to the piece's q-th
-// non-joining vertex, bit index p' * 2 + q.  The top four bits stay clear, so no key equals
-// FSM_EMPTY_KEY.
+// 64-bit key of a join from a size-l embedding: pid_s (24 bits) | piece index (19) | i (3) |
+// j (2) | cross bits (2*(l-1)).  Cross bit (p', q): s position p (p' = p minus one if p > i)
+// adjacent to the piece's q-th non-joining vertex, bit index p' * 2 + q.  Up to l = 6 the cross
+// field has 10 bits; from l = 7 it has 12 and every other field sits two bits higher
+// (key_shift).  The top bits stay clear, so no key equals FSM_EMPTY_KEY.
 
 #define FSM_PID_BITS 24
-FSM_HD uint64_t make_key(uint32_t pid_s, uint32_t pidx, int i, int j, uint32_t cross) {
-    return ((uint64_t)pid_s << 36) | ((uint64_t)pidx << 17) | ((uint64_t)i << 14) |
-           ((uint64_t)j << 12) | (uint64_t)cross;
+FSM_HD int key_shift(int L) { return L >= 7 ? 2 : 0; }
+FSM_HD uint64_t make_key(uint32_t pid_s, uint32_t pidx, int i, int j, uint32_t cross, int L) {
+    const int w = key_shift(L);
+    return ((uint64_t)pid_s << (34 + w)) | ((uint64_t)pidx << (15 + w)) | ((uint64_t)i << (12 + w)) |
+           ((uint64_t)j << (10 + w)) | (uint64_t)cross;
 }
-FSM_HD void split_key(uint64_t key, uint32_t &pid_s, uint32_t &pidx, int &i, int &j, uint32_t &cross) {
-    pid_s = (uint32_t)(key >> 36) & ((1u << FSM_PID_BITS) - 1);
-    pidx = (uint32_t)(key >> 17) & ((1u << 19) - 1);
-    i = (int)(key >> 14) & 7;
-    j = (int)(key >> 12) & 3;
-    cross = (uint32_t)key & 4095u;
+FSM_HD void split_key(uint64_t key, int L, uint32_t &pid_s, uint32_t &pidx, int &i, int &j, uint32_t &cross) {
+    const int w = key_shift(L);
+    pid_s = (uint32_t)(key >> (34 + w)) & ((1u << FSM_PID_BITS) - 1);
+    pidx = (uint32_t)(key >> (15 + w)) & ((1u << 19) - 1);
+    i = (int)(key >> (12 + w)) & 7;
+    j = (int)(key >> (10 + w)) & 3;
+    cross = (uint32_t)key & ((1u << (10 + w)) - 1u);
 }
 
 // ---------------------------------------------------------------------------- pattern words

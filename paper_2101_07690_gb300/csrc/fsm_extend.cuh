@@ -315,14 +315,15 @@ struct ResolveArgs {
 };
 
 static __device__ __noinline__ void resolve_slot(const ResolveArgs A, int64_t slot, uint64_t key) {
-    int K, lab[FSM_MAXK], rep[FSM_MAXK];
-    uint32_t adj[FSM_MAXK];
+    int K, lab[8], rep[8];   // the one-pass last level has K <= 7
+    uint32_t adj[8];
     key_graph(A.explore, A.level, key, A.pat_lab, A.pat_adj, K, lab, adj);
+    // K <= 7 here: enumeration with 32-bit words (no cell search in this kernel)
     unsigned long long clab;
-    uint64_t cadj, inv;
-    canonicalise(K, lab, adj, clab, cadj, inv);
-    orbit_reps(K, clab, cadj, rep);
-    int64_t pre[FSM_MAXK], words = 0;
+    uint32_t cadj, inv;
+    canonicalise_enum<uint32_t, 8>(K, lab, adj, clab, cadj, inv);
+    orbit_reps_enum<uint32_t, 8>(K, clab, cadj, rep);
+    int64_t pre[8], words = 0;
     for (int c = 0; c < K; ++c) {
         pre[c] = words;
         if (rep[c] == c) words += ((int64_t)__ldg(A.cls_size + clab_get(clab, c)) + 31) / 32;
@@ -346,7 +347,7 @@ static __device__ __noinline__ void resolve_slot(const ResolveArgs A, int64_t sl
     }
     long long *so = A.slot_off + slot * 8;
     for (int hh = K - 1; hh >= 0; --hh) {
-        const long long v = (long long)(off - 1ull) + pre[rep[nib_get(inv, hh)]];
+        const long long v = (long long)(off - 1ull) + pre[rep[(inv >> (4 * hh)) & 15u]];
         if (hh) st_relaxed_s64(so + hh, v); else st_release_s64(so, v);
     }
 }
@@ -654,7 +655,7 @@ __device__ __forceinline__ void join_piece(const ExtArgs &A, const int32_t (&S)[
                 const uint64_t key = edge_list_key<K>(gid, labK, adjK, sg);
                 accept_sorted<K, PASS>(A, cc, key, sg);
             } else {
-                accept<L, K, PASS>(A, cc, dc, make_key((uint32_t)pid, pidx, i, jpos, sub), gid, RK);
+                accept<L, K, PASS>(A, cc, dc, make_key((uint32_t)pid, pidx, i, jpos, sub, L), gid, RK);
             }
         }
         if (A.mode == 1 || sub == 0) break;
@@ -865,7 +866,7 @@ __device__ __forceinline__ void do_edge(const ExtArgs &A, const int32_t (&S)[L],
             if (keep && S[h] > a && mask_connected(all & ~(1u << h), adjK, K)) keep = false;
         if (keep) {
             ++tl.accepted;
-            accept<L, K, PASS>(A, cc, dc, make_key((uint32_t)pid, (uint32_t)la, i, 3, sub), gid, RK);
+            accept<L, K, PASS>(A, cc, dc, make_key((uint32_t)pid, (uint32_t)la, i, 3, sub, L), gid, RK);
         }
         if (A.mode == 1 || sub == 0) break;
         sub = (sub - 1) & cand;

@@ -170,18 +170,23 @@ int main() {
                 for (int x = 0; x < y; ++x) brute += x < c;
             CHECK(centre_pairs(d, c) == brute);
         }
-    // quick-pattern keys: fields round-trip and the packed key never equals the empty key
+    // quick-pattern keys: fields round-trip at every level size (10 cross bits up to l = 6, 12
+    // at l = 7), the narrow layout is the one of 10-bit cross fields, and the packed key never
+    // equals the empty key
     unsigned s = 12345u;
     for (int it = 0; it < 100000; ++it) {
+        const int L = 1 + it % 7;
         s = s * 1103515245u + 12345u; const uint32_t pid = (s >> 4) & ((1u << 24) - 1);
         s = s * 1103515245u + 12345u; const uint32_t pidx = (s >> 3) & ((1u << 19) - 1);
-        s = s * 1103515245u + 12345u; const int i = (int)((s >> 5) % 7), j = (int)((s >> 9) % 3);
-        s = s * 1103515245u + 12345u; const uint32_t cross = (s >> 7) & 4095u;
-        const uint64_t key = make_key(pid, pidx, i, j, cross);
+        s = s * 1103515245u + 12345u; const int i = (int)((s >> 5) % 7), j = (int)((s >> 9) % 4);
+        s = s * 1103515245u + 12345u; const uint32_t cross = (s >> 7) & ((1u << (L >= 7 ? 12 : 10)) - 1u);
+        const uint64_t key = make_key(pid, pidx, i, j, cross, L);
         uint32_t p2, x2, c2; int i2, j2;
-        split_key(key, p2, x2, i2, j2, c2);
+        split_key(key, L, p2, x2, i2, j2, c2);
         CHECK(p2 == pid && x2 == pidx && i2 == i && j2 == j && c2 == cross);
         CHECK(key != FSM_EMPTY_KEY);
+        if (L <= 6)
+            CHECK(key == (((uint64_t)pid << 34) | ((uint64_t)pidx << 15) | ((uint64_t)i << 12) | ((uint64_t)j << 10) | cross));
     }
     // join graphs are symmetric and loop-free for every level size, shape, join position,
     // key position and cross subset (s = a path over its l positions)
