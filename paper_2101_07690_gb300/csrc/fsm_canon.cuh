@@ -231,8 +231,8 @@ static __host__ __device__ __noinline__ void canonicalise(int K, const int *lab,
 
 // The labeled graph a quick-pattern key denotes, in the key's local vertex order (the order the
 // extension kernel's accept step uses for that key's positions).
-static __device__ __noinline__ void key_graph(int V, int L, uint64_t key, const uint64_t *pat_lab8, const uint64_t *pat_adj8, int &K,
-                          int *labH, uint32_t *adjH) {
+static __host__ __device__ __noinline__ void key_graph(int V, int L, uint64_t key, const uint64_t *pat_lab8,
+                                                       const uint64_t *pat_adj8, int &K, int *labH, uint32_t *adjH) {
     if (V == FSM_EXPLORE_TV_EDGELIST) {
         // labels and edges listed over the vertices in ascending id order
         K = L + 2;

@@ -27,7 +27,7 @@
 // `unit_base`); warps take fixed-size chunks of it from an atomic counter, so hub vertices
 // with millions of pieces are split across many warps and light units share a warp.
 #pragma once
-#include "fsm_canon.cuh"
+#include "fsm_canon7.cuh"
 
 namespace fsm {
 
@@ -315,20 +315,20 @@ struct ResolveArgs {
 };
 
 static __device__ __noinline__ void resolve_slot(const ResolveArgs A, int64_t slot, uint64_t key) {
-    int K, lab[8], rep[8];   // the one-pass last level has K <= 7
+    // K <= 7 here: the compact words of fsm_canon7.cuh
+    int K, lab[8], rep[8];
     uint32_t adj[8];
-    key_graph(A.explore, A.level, key, A.pat_lab, A.pat_adj, K, lab, adj);
-    // K <= 7 here: enumeration with 32-bit words (no cell search in this kernel)
+    key_graph7(A.explore, A.level, key, A.pat_lab, A.pat_adj, K, lab, adj);
     unsigned long long clab;
     uint32_t cadj, inv;
-    canonicalise_enum<uint32_t, 8>(K, lab, adj, clab, cadj, inv);
-    orbit_reps_enum<uint32_t, 8>(K, clab, cadj, rep);
+    canonicalise7(K, lab, adj, clab, cadj, inv);
+    orbit_reps7(K, clab, cadj, rep);
     int64_t pre[8], words = 0;
     for (int c = 0; c < K; ++c) {
         pre[c] = words;
-        if (rep[c] == c) words += ((int64_t)__ldg(A.cls_size + clab_get(clab, c)) + 31) / 32;
+        if (rep[c] == c) words += ((int64_t)__ldg(A.cls_size + ((clab >> (8 * (7 - c))) & 0xff)) + 31) / 32;
     }
-    const uint64_t pk = pack_code(K, clab, cadj);
+    const uint64_t pk = pack_code7(K, clab, cadj);
     uint64_t h = mix64(pk) & A.code_mask;
     int64_t ci = -1;
     for (int probe = 0; probe < FSM_MAX_PROBES; ++probe) {
@@ -347,7 +347,7 @@ static __device__ __noinline__ void resolve_slot(const ResolveArgs A, int64_t sl
     }
     long long *so = A.slot_off + slot * 8;
     for (int hh = K - 1; hh >= 0; --hh) {
-        const long long v = (long long)(off - 1ull) + pre[rep[(inv >> (4 * hh)) & 15u]];
+        const long long v = (long long)(off - 1ull) + pre[rep[(inv >> (3 * hh)) & 7]];
         if (hh) st_relaxed_s64(so + hh, v); else st_release_s64(so, v);
     }
 }

@@ -3,10 +3,11 @@
 // centre pairs), quick-pattern key packing, join-graph symmetry, size-3 pattern indices; and of
 // the canonicaliser (fsm_canon.cuh: label-order enumeration and the cell search) and its orbit
 // representatives, against the minimum over all K! vertex orders and the automorphisms found
-// among them, for K up to 9.  It also prints the sampling hash of a grid of (seed, x, y) for
+// among them, for K up to 9; and of the one-pass level's compact copies (fsm_canon7.cuh)
+// against the general ones.  It also prints the sampling hash of a grid of (seed, x, y) for
 // tests/test_device_helpers.py to compare with splitmix64 written from its published
 // definition.  Host code only.
-#include "fsm_canon.cuh"
+#include "fsm_canon7.cuh"
 #include <cstdio>
 #include <cstdlib>
 using namespace fsm;
@@ -148,6 +149,76 @@ static void check_canon() {
             for (int c = 0; c < K; ++c) CHECK(rep[c] == wrep[c]);
             ++graphs;
         }
+    // the one-pass level's compact routines (K <= 7) give the same codes, orders, orbits and
+    // packed codes as the general ones, and decode keys to the same graphs
+    for (int K = 1; K <= 7; ++K)
+        for (int r = 0; r < 3000; ++r) {
+            const int nl = 1 + (int)(xrand() % 3);
+            int lab[FSM_MAXK];
+            uint32_t adj[FSM_MAXK] = {0};
+            for (int h = 0; h < K; ++h) lab[h] = (int)(xrand() % nl) * 21;
+            for (int h = 1; h < K; ++h) {
+                const int u = (int)(xrand() % h);
+                adj[h] |= 1u << u; adj[u] |= 1u << h;
+            }
+            const int dens = (int)(xrand() % 5);
+            for (int a = 0; a < K; ++a)
+                for (int b = a + 1; b < K; ++b)
+                    if ((int)(xrand() % 4) < dens) { adj[a] |= 1u << b; adj[b] |= 1u << a; }
+            unsigned long long cl, cl7;
+            uint64_t ca, iv;
+            uint32_t ca7, iv7;
+            canonicalise(K, lab, adj, cl, ca, iv);
+            canonicalise7(K, lab, adj, cl7, ca7, iv7);
+            CHECK((uint64_t)ca7 == ca);
+            for (int c = 0; c < K; ++c) CHECK((int)((cl7 >> (8 * (7 - c))) & 0xff) == clab_get(cl, c));
+            for (int h = 0; h < K; ++h) CHECK((int)((iv7 >> (3 * h)) & 7u) == nib_get(iv, h));
+            CHECK(pack_code7(K, cl7, ca7) == pack_code(K, cl, ca));
+            int rep[FSM_MAXK], rep7[8];
+            orbit_reps(K, cl, ca, rep);
+            orbit_reps7(K, cl7, ca7, rep7);
+            for (int c = 0; c < K; ++c) CHECK(rep[c] == rep7[c]);
+            ++graphs;
+        }
+    {
+        // keys of joins from size-l embeddings (l <= 5) decode to the same graph both ways
+        uint64_t plab[16], padj[16];
+        for (int P = 0; P < 16; ++P) {
+            const int L = 1 + P % 5;
+            uint32_t rows[8] = {0};
+            for (int h = 1; h < L; ++h) {
+                const int u = (int)(xrand() % h);
+                rows[h] |= 1u << u; rows[u] |= 1u << h;
+            }
+            plab[P] = padj[P] = 0;
+            for (int h = 0; h < L; ++h) {
+                plab[P] |= (uint64_t)(xrand() % 64) << (8 * h);
+                padj[P] |= (uint64_t)rows[h] << (8 * h);
+            }
+        }
+        for (int it = 0; it < 20000; ++it) {
+            const int P = (int)(xrand() % 16), L = 1 + P % 5;
+            const int V = (int)(xrand() % 3);   // two-vertex, single-vertex, edge-list
+            const int i = (int)(xrand() % L);
+            uint64_t key;
+            if (V == FSM_EXPLORE_TV_EDGELIST) {
+                key = xrand() & ((1ull << 42) - 1);
+                key |= ((uint64_t)xrand() & ((1u << ((L + 2) * (L + 1) / 2)) - 1u)) << 42;
+            } else if (V == FSM_EXPLORE_SV) {
+                key = make_key((uint32_t)P, xrand() % 64, i, 3, xrand() & ((1u << (L - 1)) - 1u), L);
+            } else {
+                const int shape = (int)(xrand() % 2), jpos = (int)(xrand() % 3);
+                const uint32_t pidx = piece_index(shape, xrand() % 64, xrand() % 64, xrand() % 64);
+                key = make_key((uint32_t)P, pidx, i, jpos, xrand() & ((1u << (2 * (L - 1))) - 1u), L);
+            }
+            int K1, K2, l1[FSM_MAXK], l2[8];
+            uint32_t a1[FSM_MAXK], a2[8];
+            key_graph(V, L, key, plab, padj, K1, l1, a1);
+            key_graph7(V, L, key, plab, padj, K2, l2, a2);
+            CHECK(K1 == K2);
+            for (int h = 0; h < K1 && h < 8; ++h) CHECK(l1[h] == l2[h] && a1[h] == a2[h]);
+        }
+    }
     printf("canonical codes checked on %d graphs\n", graphs);
 }
 
