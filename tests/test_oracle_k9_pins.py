@@ -157,3 +157,21 @@ def test_quota_oracle_without_quotas_is_exact(mode):
         b = oracle.mine_quota(g, K, t, mode, seed=0, join_quota=0, match_quota=0)
         for key in ("labels", "adj", "support", "count"):
             assert np.array_equal(a[key], b[key]), (t, key)
+
+
+@pytest.mark.parametrize("mode", ["edge", "vertex"])
+def test_quota_supports_are_lower_bounds(mode):
+    """Section 5's quotas draw a subset of the embeddings: every pattern they report is truly
+    frequent, with a support and count no larger than the exact ones."""
+    g = gg.tree_plus(14, 4, 2, 3)
+    exact = oracle.mine(g, K, 1, mode)
+    ex = {(tuple(int(x) for x in l), int(a)): (int(s), int(c))
+          for l, a, s, c in zip(exact["labels"], exact["adj"], exact["support"], exact["count"])}
+    checked = 0
+    for x in (2, 3):
+        q = oracle.mine_quota(g, K, 1, mode, seed=7, join_quota=x)
+        for l, a, s, c in zip(q["labels"], q["adj"], q["support"], q["count"]):
+            key = (tuple(int(v) for v in l), int(a))
+            assert key in ex and int(s) <= ex[key][0] and int(c) <= ex[key][1]
+            checked += 1
+    assert checked > 0
