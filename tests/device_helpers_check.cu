@@ -219,6 +219,56 @@ static void check_canon() {
             for (int h = 0; h < K1 && h < 8; ++h) CHECK(l1[h] == l2[h] && a1[h] == a2[h]);
         }
     }
+    // highly symmetric unlabeled 9-vertex graphs (the cell search's hardest cases): K_9, C_9,
+    // the 3x3 rook graph, K_{3,3,3}, the Petersen graph minus a vertex, the 3-cube plus a hub;
+    // each against the brute-force minimum, with its orbits
+    {
+        const int K = 9;
+        uint32_t g[6][9] = {};
+        for (int a = 0; a < K; ++a)
+            for (int b = 0; b < K; ++b) {
+                if (a == b) continue;
+                g[0][a] |= 1u << b;                                                  // K_9
+                if ((a + 1) % K == b || (b + 1) % K == a) g[1][a] |= 1u << b;        // C_9
+                if (a / 3 == b / 3 || a % 3 == b % 3) g[2][a] |= 1u << b;            // rook 3x3
+                if (a / 3 != b / 3) g[3][a] |= 1u << b;                              // K_{3,3,3}
+            }
+        // Petersen graph (outer 5-cycle 0..4, spokes i - i+5, inner pentagram) minus vertex 9
+        const int pe[15][2] = {{0,1},{1,2},{2,3},{3,4},{4,0},{0,5},{1,6},{2,7},{3,8},{4,9},{5,7},{7,9},{9,6},{6,8},{8,5}};
+        for (auto &e : pe)
+            if (e[0] < 9 && e[1] < 9) { g[4][e[0]] |= 1u << e[1]; g[4][e[1]] |= 1u << e[0]; }
+        // 3-cube on 0..7 plus vertex 8 joined to all of it
+        for (int a = 0; a < 8; ++a) {
+            for (int bit = 0; bit < 3; ++bit) g[5][a] |= 1u << (a ^ (1 << bit));
+            g[5][a] |= 1u << 8;
+            g[5][8] |= 1u << a;
+        }
+        int lab[9] = {0};
+        for (int q = 0; q < 6; ++q) {
+            int p[9];
+            for (int h = 0; h < K; ++h) p[h] = h;
+            uint64_t want = adj_code(K, g[q], p);
+            do {
+                const uint64_t x = adj_code(K, g[q], p);
+                if (x < want) want = x;
+            } while (next_perm(p, K));
+            unsigned long long cl;
+            uint64_t ca, inv;
+            canonicalise(K, lab, g[q], cl, ca, inv);
+            CHECK(ca == want);
+            int clb[9], rep[9], wrep[9];
+            uint32_t cad[9];
+            decode_code(K, cl, ca, clb, cad);
+            for (int c = 0; c < K; ++c) { p[c] = c; wrep[c] = c; }
+            do {
+                if (adj_code(K, cad, p) == ca)
+                    for (int c = 0; c < K; ++c) if (p[c] < wrep[c]) wrep[c] = p[c];
+            } while (next_perm(p, K));
+            orbit_reps(K, cl, ca, rep);
+            for (int c = 0; c < K; ++c) CHECK(rep[c] == wrep[c]);
+            ++graphs;
+        }
+    }
     printf("canonical codes checked on %d graphs\n", graphs);
 }
 
