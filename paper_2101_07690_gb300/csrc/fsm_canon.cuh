@@ -51,17 +51,15 @@ FSM_HD bool next_label_perm(int K, const int *seg_start, int *perm) {
     return false;
 }
 
-// Adjacency word of an order, in a code type C wide enough for K (K <= 7 fits 32 bits).
-template <typename C>
-FSM_HD C adj_code_t(int K, const uint32_t *adj, const int *perm) {
-    C code = 0;
+// Adjacency word of an order: pair (perm[c1], perm[c2]) of the order at bit np - 1 - q.
+FSM_HD uint64_t adj_code(int K, const uint32_t *adj, const int *perm) {
+    uint64_t code = 0;
     for (int c1 = 0; c1 < K; ++c1) {
         const uint32_t row = adj[perm[c1]];
-        for (int c2 = c1 + 1; c2 < K; ++c2) code = (code << 1) | (C)((row >> perm[c2]) & 1u);
+        for (int c2 = c1 + 1; c2 < K; ++c2) code = (code << 1) | (uint64_t)((row >> perm[c2]) & 1u);
     }
     return code;
 }
-FSM_HD uint64_t adj_code(int K, const uint32_t *adj, const int *perm) { return adj_code_t<uint64_t>(K, adj, perm); }
 
 // Vertices sorted by (label, index) into perm; seg[c] = first position of c's label segment.
 // Returns the number of label-preserving orders (product of the segments' factorials).
@@ -176,43 +174,38 @@ static __host__ __device__ __noinline__ uint64_t canon_search(int K, const int *
     return bc;
 }
 
-// Label word and vertex order (4 bits per vertex, in C) of the optimal order best[] (vertex at
-// each canonical position).
-template <typename C>
-FSM_HD void canon_words(int K, const int *lab, const int *best, unsigned long long &clab, C &inv) {
+// Label word and vertex order (4 bits per vertex) of the optimal order best[] (vertex at each
+// canonical position).
+FSM_HD void canon_words(int K, const int *lab, const int *best, unsigned long long &clab, uint64_t &inv) {
     unsigned long long l = 0;
-    C iv = 0;
+    uint64_t iv = 0;
     for (int c = 0; c < K; ++c) {
         l |= clab_put(c, lab[best[c]]);
-        iv |= (C)c << (4 * best[c]);
+        iv |= nib_put(best[c], c);
     }
     clab = l;
     inv = iv;
 }
 
 // The canonical code by enumerating the label-preserving orders: what canonicalise does when
-// there are at most FSM_ENUM_MAX of them, which is always the case for K <= 7 (at most 7!).
-// The one-pass last level (K <= 7) calls it directly with 32-bit words (C = uint32_t: 21 code
-// bits, 28 order bits), which keeps its kernel's registers and stack what they are without the
-// cell search and the wider words.
-template <typename C, int N = FSM_MAXK>   // N >= K: scratch array size
+// there are at most FSM_ENUM_MAX of them (always for K <= 7).
 static __host__ __device__ __noinline__ void canonicalise_enum(int K, const int *lab, const uint32_t *adj,
-                                                               unsigned long long &clab, C &cadj, C &inv) {
-    int perm[N], seg[N], best[N];
+                                                               unsigned long long &clab, uint64_t &cadj, uint64_t &inv) {
+    int perm[FSM_MAXK], seg[FSM_MAXK], best[FSM_MAXK];
     label_sort(K, lab, perm, seg);
     // within each segment start from ascending vertex index (next_perm enumerates from there)
     for (int c = 0; c < K; ++c)
         for (int b = c; b > seg[c] && perm[b - 1] > perm[b]; --b) { int t = perm[b]; perm[b] = perm[b - 1]; perm[b - 1] = t; }
-    C bc = (C)~(C)0;
+    uint64_t bc = ~0ull;
     do {
-        const C code = adj_code_t<C>(K, adj, perm);
+        const uint64_t code = adj_code(K, adj, perm);
         if (code < bc) {
             bc = code;
             for (int c = 0; c < K; ++c) best[c] = perm[c];
         }
     } while (next_label_perm(K, seg, perm));
     cadj = bc;
-    canon_words<C>(K, lab, best, clab, inv);
+    canon_words(K, lab, best, clab, inv);
 }
 
 // Canonical code of a labeled K-vertex graph: the smallest (label sequence, adjacency
@@ -222,11 +215,11 @@ static __host__ __device__ __noinline__ void canonicalise(int K, const int *lab,
                                                           unsigned long long &clab, uint64_t &cadj, uint64_t &inv) {
     int perm[FSM_MAXK], seg[FSM_MAXK], best[FSM_MAXK];
     if (label_sort(K, lab, perm, seg) <= FSM_ENUM_MAX) {
-        canonicalise_enum<uint64_t>(K, lab, adj, clab, cadj, inv);
+        canonicalise_enum(K, lab, adj, clab, cadj, inv);
         return;
     }
     cadj = canon_search(K, lab, adj, -1, best);
-    canon_words<uint64_t>(K, lab, best, clab, inv);
+    canon_words(K, lab, best, clab, inv);
 }
 
 // The labeled graph a quick-pattern key denotes, in the key's local vertex order (the order the
@@ -276,14 +269,13 @@ static __host__ __device__ __noinline__ void key_graph(int V, int L, uint64_t ke
     join_graph(L, srows, i, tj0, tj1, txx, cross, adjH);
 }
 
-template <typename C>
-FSM_HD void decode_code(int K, unsigned long long clab, C cadj, int *lab, uint32_t *adj) {
+FSM_HD void decode_code(int K, unsigned long long clab, uint64_t cadj, int *lab, uint32_t *adj) {
     const int np = K * (K - 1) / 2;
     for (int c = 0; c < K; ++c) { lab[c] = clab_get(clab, c); adj[c] = 0; }
     int q = 0;
     for (int c1 = 0; c1 < K; ++c1)
         for (int c2 = c1 + 1; c2 < K; ++c2, ++q)
-            if ((cadj >> (np - 1 - q)) & (C)1) { adj[c1] |= 1u << c2; adj[c2] |= 1u << c1; }
+            if ((cadj >> (np - 1 - q)) & 1ull) { adj[c1] |= 1u << c2; adj[c2] |= 1u << c1; }
 }
 
 
@@ -304,20 +296,19 @@ static __host__ __device__ __noinline__ void orbit_reps_search(int K, const int 
 
 // Orbit representatives of a canonical pattern: rep[c] = the smallest canonical position that
 // an automorphism (a label-preserving order with the same adjacency sequence) maps c to.  With
-// few label-preserving orders they are enumerated (orbit_reps_enum: always for K <= 7),
-// otherwise found by marking.
-template <typename C, int N = FSM_MAXK>   // N >= K: scratch array size
-static __host__ __device__ __noinline__ void orbit_reps_enum(int K, unsigned long long clab, C cadj, int *rep) {
-    int lab[N], perm[N], seg[N];
-    uint32_t adj[N];
-    decode_code<C>(K, clab, cadj, lab, adj);
+// few label-preserving orders they are enumerated (orbit_reps_enum), otherwise found by
+// marking.
+static __host__ __device__ __noinline__ void orbit_reps_enum(int K, unsigned long long clab, uint64_t cadj, int *rep) {
+    int lab[FSM_MAXK], perm[FSM_MAXK], seg[FSM_MAXK];
+    uint32_t adj[FSM_MAXK];
+    decode_code(K, clab, cadj, lab, adj);
     for (int c = 0; c < K; ++c) {
         perm[c] = c;
         rep[c] = c;
         seg[c] = (c > 0 && lab[c] == lab[c - 1]) ? seg[c - 1] : c;
     }
     do {
-        if (adj_code_t<C>(K, adj, perm) == cadj)
+        if (adj_code(K, adj, perm) == cadj)
             for (int c = 0; c < K; ++c) if (perm[c] < rep[c]) rep[c] = perm[c];
     } while (next_label_perm(K, seg, perm));
 }
@@ -332,7 +323,7 @@ static __host__ __device__ __noinline__ void orbit_reps(int K, unsigned long lon
         orders *= (int64_t)(c - seg[c] + 1);
     }
     if (orders <= FSM_ENUM_MAX) {
-        orbit_reps_enum<uint64_t>(K, clab, cadj, rep);
+        orbit_reps_enum(K, clab, cadj, rep);
         return;
     }
     orbit_reps_search(K, lab, adj, seg, rep);
